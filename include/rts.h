@@ -1,0 +1,156 @@
+/*
+ * rts.h -- C ABI of the B300-native short-characteristics radiation transport
+ * solver (RTS).
+ *
+ * The operation (paper Sect. 2 "MURaM Routines" and Sect. 5.1 "Summary of the
+ * Radiation Transport Solver"): for every opacity band and every ray of a
+ * 3-rays-per-octant (24-ray) Carlson quadrature, integrate the transfer
+ * equation along short characteristics on a 3-D Cartesian grid that is
+ * periodic in x and y, iterating the periodic boundary intensities to a
+ * tolerance; then form the mean intensity J, the radiative flux F and the
+ * radiative heating/cooling Q_rad that is fed back to the MHD solver. The
+ * multi-band scheme (Sect. 1, Nordlund's opacity binning) runs the transfer
+ * once per band and sums over bands.
+ *
+ * Per point p, direction d and band b (one short characteristic):
+ *   I_up, chi_up, S_up = bilinear interpolation on the face the ray crosses
+ *   dtau = ds_d (chi_up + chi_p) / 2,  e = exp(-dtau)
+ *   I_p  = e I_up + w_up S_up + w_p S_p,
+ *   w_up = (1-e)/dtau - e,  w_p = 1 - (1-e)/dtau   (S linear in tau)
+ * Accumulation: J = sum_b sum_d w_d I,  F = 4 pi sum_b sum_d w_d n_d I,
+ * Q_rad = sum_b [om_b 4 pi chi_b (J_b - S_b) + (1 - om_b)(-div F_b)],
+ * om_b = exp(-chi_b min(dx,dy,dz) / tau_switch) (thin/thick blend).
+ * I_top[b][u] is the intensity of the u-th upward direction at k = Nz-1.
+ *
+ * Conventions
+ *  - Grid arrays are C-contiguous [B][Nz][Ny][Nx] (x fastest, k = 0 bottom);
+ *    F is [3][Nz][Ny][Nx]; J and Q_rad are [Nz][Ny][Nx].
+ *  - I_top and explicit bottom intensities are [B][n_up][Ny][Nx]; explicit
+ *    top intensities are [B][n_down][Ny][Nx]; up/down directions are counted
+ *    in quadrature-table order.
+ *  - Precision: chi, S, I_top and explicit boundary arrays are float64 for
+ *    RTS_FP64 and float32 for the FP32 modes. J, F and Q_rad are float64.
+ *  - Ownership: every array argument is a caller-owned DEVICE pointer
+ *    (unless stated otherwise), valid on the handle's stream. Inputs are
+ *    read-only. The handle owns all scratch, allocated in rts_create;
+ *    rts_solve and rts_adjoint allocate nothing and do not synchronise.
+ *  - Errors: every call returns an rts_status. Argument errors are returned
+ *    at once. Errors found on the device (a wait that timed out, a periodic
+ *    wrap that did not converge) are recorded in a device status word and
+ *    returned by the next rts_check or rts_get_stats. rts_last_error gives a
+ *    text. No C++ exception crosses the ABI.
+ */
+#ifndef RTS_H
+#define RTS_H
+#include <stddef.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RTS_OK = 0,
+    RTS_EINVAL = 1,      /* bad argument (NULL, size, band count, spacing) */
+    RTS_ENOMEM = 2,      /* device allocation failed in rts_create */
+    RTS_ECUDA = 3,       /* a CUDA runtime call failed */
+    RTS_ETIMEOUT = 4,    /* a device-side wait gave up (no hang) */
+    RTS_ENOCONV = 5,     /* the periodic wrap did not converge within the cap */
+    RTS_ENONFINITE = 6   /* reserved: non-finite input detected */
+} rts_status;
+
+typedef enum {
+    RTS_FP64 = 0,             /* FP64 sweep, FP64 accumulation and Q step */
+    RTS_FP32_MIXED = 1,       /* FP32 sweep; band/group accumulation and Q step in FP64 */
+    RTS_FP32_COMPENSATED = 2  /* FP32 sweep; accumulation and Q step in compensated
+                                 (double-float, two-FP32) arithmetic */
+} rts_precision;
+
+typedef enum { RTS_BC_ZERO = 0, RTS_BC_EQUAL_S = 1, RTS_BC_EXPLICIT = 2 } rts_bc_kind;
+
+typedef struct {
+    int nx, ny, nz;       /* nx, ny >= 1 (periodic), nz >= 2 */
+    double dx, dy, dz;    /* > 0 */
+} rts_grid;
+
+/* Angular quadrature (host pointers, copied in rts_create). NULL selects the
+ * default 24-direction level-symmetric S4 (Carlson) set. Every direction must
+ * have n_z != 0. */
+typedef struct {
+    int ndir;
+    const double *n;      /* [ndir][3] unit vectors */
+    const double *w;      /* [ndir] weights, sum 1 */
+} rts_quadrature;
+
+enum {
+    RTS_FLAG_HOST_IO = 1  /* allocate staging buffers for rts_solve_host */
+};
+
+typedef struct {
+    rts_precision prec;
+    double tau_switch;    /* thin/thick blend constant (default 0.1) */
+    double wrap_tol;      /* bound on the remaining seed error of the periodic
+                             wrap, relative to the seed error (default 1e-15
+                             for FP64, 1e-9 for FP32) */
+    int max_wrap_iters;   /* cap on the wrap warm-up, in periods (default 64) */
+    int tile_rows;        /* rows of a sweep tile (0 = automatic) */
+    int threads;          /* threads per CTA of the sweep (0 = automatic) */
+    int flags;            /* RTS_FLAG_* */
+    double timeout_s;     /* device-side wait limit in seconds (default 2) */
+    void *stream;         /* cudaStream_t to run on (NULL = legacy default stream) */
+} rts_options;
+
+typedef struct {
+    int n_units;          /* sweep units of the last solve (band x direction group) */
+    int n_tiles;          /* tiles of the last solve */
+    int max_warmup_steps; /* longest periodic-wrap warm-up of the last solve (planes) */
+    double mean_warmup_steps;
+    int device_status;    /* rts_status recorded on the device */
+} rts_stats;
+
+typedef struct {
+    rts_bc_kind bottom, top;
+    const void *bottom_I;  /* [B][n_up][Ny][Nx] when bottom == RTS_BC_EXPLICIT */
+    const void *top_I;     /* [B][n_down][Ny][Nx] when top == RTS_BC_EXPLICIT */
+} rts_boundary;
+
+typedef struct rts_handle rts_handle;
+
+/* Default options: RTS_FP64, tau_switch 0.1, automatic tiling, 2 s timeout. */
+void rts_default_options(rts_options *opt);
+
+/* Create a solver for one grid and band count. Allocates all device scratch.
+ * opt may be NULL (defaults). */
+rts_status rts_create(rts_handle **h, const rts_grid *g, int nbands,
+                      const rts_quadrature *q, const rts_options *opt);
+
+/* Forward solve (paper Sect. 5.1: integrate over all rays and bands, then
+ * flux). chi, S: [B][Nz][Ny][Nx]; bc may be NULL (bottom I = S, top I = 0).
+ * Any output may be NULL. Enqueued on the handle's stream; no sync. */
+rts_status rts_solve(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                     void *I_top, double *J, double *F, double *Q_rad);
+
+/* Same as rts_solve with HOST pointers: copies the inputs to the device,
+ * solves, copies the outputs back and synchronises the stream. Needs
+ * RTS_FLAG_HOST_IO at create time; explicit boundary arrays are not
+ * accepted here (bc kinds ZERO / EQUAL_S only). */
+rts_status rts_solve_host(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                          void *I_top, double *J, double *F, double *Q_rad);
+
+/* Wait for the handle's stream and return the device status of the last
+ * solve (RTS_OK, RTS_ETIMEOUT, RTS_ENOCONV). */
+rts_status rts_check(rts_handle *h);
+
+/* Statistics of the last solve (synchronises the stream). */
+rts_status rts_get_stats(rts_handle *h, rts_stats *out);
+
+/* Text of the last error on this handle (never NULL). */
+const char *rts_last_error(rts_handle *h);
+
+/* Number of upward directions of the handle's quadrature. */
+int rts_num_up(rts_handle *h);
+
+void rts_destroy(rts_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -199,4 +199,5 @@ def neg_divergence(F, dx=1.0, dy=1.0, dz=1.0):
 
 
 def default_threads():
-    return max(1, os.cpu_count() or 1)
+    """Threads for the oracle's OpenMP loop (capped: each holds one N-sized array)."""
+    return max(1, min(32, os.cpu_count() or 1))

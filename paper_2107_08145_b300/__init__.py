@@ -1,0 +1,232 @@
+"""B300-native short-characteristics radiation transport solver (RTS).
+
+A thin ctypes binding over the C ABI in include/rts.h (librts.so, built from
+csrc/ for sm_103a). Every step of the solve runs in the library's CUDA
+kernels; this module only marshals torch tensors (device memory, streams) into
+the ABI. If the library cannot be loaded, importing the solver raises: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB, build as _build
+
+RTS_OK, RTS_EINVAL, RTS_ENOMEM, RTS_ECUDA, RTS_ETIMEOUT, RTS_ENOCONV, RTS_ENONFINITE = range(7)
+FP64, FP32_MIXED, FP32_COMPENSATED = 0, 1, 2
+BC_ZERO, BC_EQUAL_S, BC_EXPLICIT = 0, 1, 2
+FLAG_HOST_IO = 1
+
+_PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED, "fp32_compensated": FP32_COMPENSATED}
+_BC = {"zero": BC_ZERO, "equal_s": BC_EQUAL_S}
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double)]
+
+
+class Quadrature(C.Structure):
+    _fields_ = [("ndir", C.c_int), ("n", C.POINTER(C.c_double)), ("w", C.POINTER(C.c_double))]
+
+
+class Options(C.Structure):
+    _fields_ = [("prec", C.c_int), ("tau_switch", C.c_double), ("wrap_tol", C.c_double),
+                ("max_wrap_iters", C.c_int), ("tile_rows", C.c_int), ("threads", C.c_int),
+                ("flags", C.c_int), ("timeout_s", C.c_double), ("stream", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_units", C.c_int), ("n_tiles", C.c_int), ("max_warmup_steps", C.c_int),
+                ("mean_warmup_steps", C.c_double), ("device_status", C.c_int)]
+
+
+class Boundary(C.Structure):
+    _fields_ = [("bottom", C.c_int), ("top", C.c_int), ("bottom_I", C.c_void_p), ("top_I", C.c_void_p)]
+
+
+_lib = None
+
+# every symbol include/rts.h declares
+EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "rts_check",
+           "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy")
+
+
+def library_path() -> str:
+    return LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load librts.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"CUDA library {path} is missing; run python -m paper_2107_08145_b300.build")
+        _build()
+    L = C.CDLL(path)
+    vp, dp = C.c_void_p, C.POINTER(C.c_double)
+    L.rts_default_options.argtypes = [C.POINTER(Options)]
+    L.rts_default_options.restype = None
+    L.rts_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Grid), C.c_int, C.POINTER(Quadrature), C.POINTER(Options)]
+    L.rts_create.restype = C.c_int
+    for f in ("rts_solve", "rts_solve_host"):
+        getattr(L, f).argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp]
+        getattr(L, f).restype = C.c_int
+    L.rts_check.argtypes = [vp]
+    L.rts_check.restype = C.c_int
+    L.rts_get_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.rts_get_stats.restype = C.c_int
+    L.rts_last_error.argtypes = [vp]
+    L.rts_last_error.restype = C.c_char_p
+    L.rts_num_up.argtypes = [vp]
+    L.rts_num_up.restype = C.c_int
+    L.rts_destroy.argtypes = [vp]
+    L.rts_destroy.restype = None
+    _ = dp
+    _lib = L
+    return L
+
+
+class RTSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rts status {code}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One grid + band count; owns the device scratch of the CUDA library.
+
+    precision: 'fp64', 'fp32' (FP32 sweep, FP64 accumulation and Q step) or
+    'fp32_compensated' (FP32 sweep, double-float accumulation and Q step).
+    """
+
+    def __init__(self, nx, ny, nz, nbands=1, dx=1.0, dy=1.0, dz=1.0, precision="fp64", n=None, w=None,
+                 tau_switch=0.1, wrap_tol=0.0, max_wrap_iters=64, tile_rows=0, timeout_s=2.0,
+                 host_io=False, stream=None):
+        import torch
+
+        L = load()
+        self.torch = torch
+        self.nx, self.ny, self.nz, self.nbands = nx, ny, nz, nbands
+        self.precision = precision
+        self.prec = _PREC[precision]
+        self.dtype = torch.float64 if self.prec == FP64 else torch.float32
+        o = Options()
+        L.rts_default_options(C.byref(o))
+        o.prec = self.prec
+        o.tau_switch = tau_switch
+        o.wrap_tol = wrap_tol
+        o.max_wrap_iters = max_wrap_iters
+        o.tile_rows = tile_rows
+        o.timeout_s = timeout_s
+        o.flags = FLAG_HOST_IO if host_io else 0
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o.stream = C.c_void_p(stream.cuda_stream)
+        g = Grid(nx, ny, nz, dx, dy, dz)
+        q = None
+        if n is not None:
+            import numpy as np
+
+            self._n = np.ascontiguousarray(n, dtype=np.float64).reshape(-1, 3)
+            self._w = np.ascontiguousarray(w, dtype=np.float64).reshape(-1)
+            q = Quadrature(len(self._w), self._n.ctypes.data_as(C.POINTER(C.c_double)),
+                           self._w.ctypes.data_as(C.POINTER(C.c_double)))
+        h = C.c_void_p()
+        rc = L.rts_create(C.byref(h), C.byref(g), nbands, C.byref(q) if q is not None else None, C.byref(o))
+        self._h = h
+        self._L = L
+        if rc != RTS_OK:
+            msg = L.rts_last_error(h).decode() if h.value else "rts_create failed"
+            L.rts_destroy(h)
+            self._h = C.c_void_p()
+            raise RTSError(rc, msg)
+        self.n_up = L.rts_num_up(h)
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                self._L.rts_destroy(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+    def _err(self, rc):
+        if rc != RTS_OK:
+            raise RTSError(rc, self._L.rts_last_error(self._h).decode())
+
+    def _bc(self, bottom, top):
+        b = Boundary()
+        keep = []
+        for side, v in (("bottom", bottom), ("top", top)):
+            if isinstance(v, str):
+                setattr(b, side, _BC[v])
+            else:
+                t = v.contiguous()
+                assert t.dtype == self.dtype and t.is_cuda
+                keep.append(t)
+                setattr(b, side, BC_EXPLICIT)
+                setattr(b, side + "_I", t.data_ptr())
+        return b, keep
+
+    def solve(self, chi, S, bottom="equal_s", top="zero", check=True, out=None):
+        """chi, S: CUDA tensors [B, nz, ny, nx] in the solver's dtype.
+
+        Returns dict(I_top [B,n_up,ny,nx], J [nz,ny,nx], F [3,nz,ny,nx], Q [nz,ny,nx])."""
+        torch = self.torch
+        shape = (self.nbands, self.nz, self.ny, self.nx)
+        assert tuple(chi.shape) == shape and tuple(S.shape) == shape, (chi.shape, shape)
+        assert chi.dtype == self.dtype and S.dtype == self.dtype and chi.is_cuda and S.is_cuda
+        chi = chi.contiguous()
+        S = S.contiguous()
+        if out is None:
+            dev = chi.device
+            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=self.dtype, device=dev),
+                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        b, keep = self._bc(bottom, top)
+        rc = self._L.rts_solve(self._h, _ptr(chi), _ptr(S), C.byref(b), _ptr(out.get("I_top")), _ptr(out.get("J")),
+                               _ptr(out.get("F")), _ptr(out.get("Q")))
+        self._err(rc)
+        if check:
+            self.check()
+        del keep
+        return out
+
+    def solve_host(self, chi, S, bottom="equal_s", top="zero", out=None):
+        """Host (numpy) inputs and outputs; the library copies both ways."""
+        import numpy as np
+
+        npdt = np.float64 if self.prec == FP64 else np.float32
+        chi = np.ascontiguousarray(chi, dtype=npdt)
+        S = np.ascontiguousarray(S, dtype=npdt)
+        if out is None:
+            out = dict(I_top=np.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=npdt),
+                       J=np.empty((self.nz, self.ny, self.nx)), F=np.empty((3, self.nz, self.ny, self.nx)),
+                       Q=np.empty((self.nz, self.ny, self.nx)))
+        b = Boundary(_BC[bottom], _BC[top], None, None)
+        p = lambda a: None if a is None else C.c_void_p(a.ctypes.data)  # noqa: E731
+        rc = self._L.rts_solve_host(self._h, p(chi), p(S), C.byref(b), p(out.get("I_top")), p(out.get("J")),
+                                    p(out.get("F")), p(out.get("Q")))
+        self._err(rc)
+        return out
+
+    def check(self):
+        self._err(self._L.rts_check(self._h))
+
+    def stats(self):
+        s = Stats()
+        rc = self._L.rts_get_stats(self._h, C.byref(s))
+        self._err(rc)
+        return dict(n_units=s.n_units, n_tiles=s.n_tiles, max_warmup_steps=s.max_warmup_steps,
+                    mean_warmup_steps=s.mean_warmup_steps)

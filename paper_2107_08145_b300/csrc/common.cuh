@@ -1,0 +1,76 @@
+// common.cuh -- device helpers shared by the RTS kernels: memory-order
+// primitives for the tile ready flags, bounded waits and the device status
+// word. Every wait has a time limit; on expiry it records RTS_ETIMEOUT in the
+// status word and returns false so the kernel can unwind (no trap, no hang).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rts {
+
+// Device status bits (mapped to rts_status on the host).
+enum : int { ST_TIMEOUT = 1, ST_NOCONV = 2, ST_BADARG = 4 };
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_relaxed(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait until *flag >= want. Returns false (and records why) if the device
+// status already carries an error or the time limit expires.
+__device__ __forceinline__ bool wait_flag_geq(const int *flag, int want, int *status, uint64_t limit_ns)
+{
+    if (ld_acquire(flag) >= want) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        __nanosleep(64);
+        if (ld_acquire(flag) >= want) return true;
+        if (ld_relaxed(status) != 0) return false;
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Loads that bypass L1 (data written by other CTAs during this kernel).
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T *p)
+{
+    return __ldcg(p);
+}
+
+}  // namespace rts

@@ -1,0 +1,107 @@
+// df32.cuh -- double-float ("two-FP32") arithmetic for the compensated
+// accumulation mode. A value is the unevaluated sum hi + lo of two floats
+// with |lo| <= ulp(hi)/2, giving about 44-48 significant bits.
+//
+// Built from the error-free transformations of Knuth (TwoSum) and Dekker
+// (FastTwoSum; TwoProd via a fused multiply-add), the standard basis of
+// double-float and double-double libraries. B300's FP64 rate is a small
+// fraction of its FP32 rate, so the compensated mode keeps the cancelling
+// J - S and flux-divergence steps on the FP32 pipes.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace rts {
+
+struct df32 {
+    float hi, lo;
+};
+
+// s + e = a + b exactly (no ordering requirement)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// s + e = a + b exactly when |a| >= |b|
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// p + e = a * b exactly
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+__device__ __forceinline__ df32 df_make(float a) { return {a, 0.f}; }
+
+__device__ __forceinline__ df32 df_add(df32 a, df32 b)
+{
+    float s, e, t, f;
+    two_sum(a.hi, b.hi, s, e);
+    two_sum(a.lo, b.lo, t, f);
+    e = __fadd_rn(e, t);
+    fast_two_sum(s, e, s, e);
+    e = __fadd_rn(e, f);
+    fast_two_sum(s, e, s, e);
+    return {s, e};
+}
+
+__device__ __forceinline__ df32 df_add(df32 a, float b)
+{
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    e = __fadd_rn(e, a.lo);
+    fast_two_sum(s, e, s, e);
+    return {s, e};
+}
+
+__device__ __forceinline__ df32 df_neg(df32 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df32 df_sub(df32 a, df32 b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df32 df_mul(df32 a, float b)
+{
+    float p, e;
+    two_prod(a.hi, b, p, e);
+    e = __fmaf_rn(a.lo, b, e);
+    fast_two_sum(p, e, p, e);
+    return {p, e};
+}
+
+__device__ __forceinline__ df32 df_mul(df32 a, df32 b)
+{
+    float p, e;
+    two_prod(a.hi, b.hi, p, e);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    fast_two_sum(p, e, p, e);
+    return {p, e};
+}
+
+__device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
+
+// Arithmetic-type shims so the Q step is written once for double and df32.
+__device__ __forceinline__ double acc_zero(double *) { return 0.0; }
+__device__ __forceinline__ df32 acc_zero(df32 *) { return {0.f, 0.f}; }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ df32 acc_add(df32 a, df32 b) { return df_add(a, b); }
+__device__ __forceinline__ double acc_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ df32 acc_sub(df32 a, df32 b) { return df_sub(a, b); }
+__device__ __forceinline__ double acc_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ df32 acc_mul(df32 a, df32 b) { return df_mul(a, b); }
+__device__ __forceinline__ double acc_to_double(double a) { return a; }
+__device__ __forceinline__ double acc_to_double(df32 a) { return df_to_double(a); }
+__device__ __forceinline__ double acc_from(double *, double v) { return v; }
+__device__ __forceinline__ df32 acc_from(df32 *, float v) { return df_make(v); }
+__device__ __forceinline__ df32 acc_from(df32 *, double v)
+{
+    float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+
+}  // namespace rts

@@ -1,0 +1,156 @@
+// qstep.cuh -- the paper's flux() step (Sect. 5.1: "from the specific
+// intensity calculate the average intensity and radiative fluxes", and the
+// radiative heating/cooling fed back to the MHD), plus the transpose that
+// lets x-dominant sweeps read unit-stride planes (Sect. 5.3.1).
+//
+//   J_b  = sum over the band's sweep units of their partial sums (w_d I_d)
+//   F_b  = same for the 4 pi w_d n_d I_d partials
+//   Q_b  = om_b 4 pi chi_b (J_b - S_b) + (1 - om_b)(-div F_b)
+//   om_b = exp(-chi_b min(dx,dy,dz) / tau_switch)
+//   J = sum_b J_b, F = sum_b F_b, Q_rad = sum_b Q_b
+// The divergence uses central differences, periodic in x and y, first-order
+// one-sided at k = 0 and k = Nz-1. The arithmetic type Acc is double (FP64)
+// or df32 (compensated two-FP32); outputs are written as double.
+#pragma once
+#include "df32.cuh"
+
+namespace rts {
+
+// out[b][i][k][j] = in[b][k][j][i]
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_x_kernel(const T *__restrict__ in, T *__restrict__ out,
+                                                            int nx, int ny, int nz)
+{
+    __shared__ T tile[32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const long long bk = blockIdx.z;
+    const long long b = bk / nz, k = bk % nz;
+    const T *src = in + (b * nz + k) * (long long)ny * nx;
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int i = i0 + tx, j = j0 + jj;
+        if (i < nx && j < ny) tile[jj][tx] = src[(long long)j * nx + i];
+    }
+    __syncthreads();
+    for (int ii = ty; ii < 32; ii += 8) {
+        const int i = i0 + ii, j = j0 + tx;
+        if (i < nx && j < ny) out[((b * nx + i) * nz + k) * (long long)ny + j] = tile[tx][ii];
+    }
+}
+
+struct RedUnit {
+    const void *partial;  // [4][N] in the unit's layout
+    int axis;             // 0: transposed layout [i][k][j]; else natural
+};
+
+template <typename T, typename Acc>
+__device__ __forceinline__ Acc acc_addT(Acc a, T v);
+template <>
+__device__ __forceinline__ double acc_addT<double, double>(double a, double v) { return a + v; }
+template <>
+__device__ __forceinline__ double acc_addT<float, double>(double a, float v) { return a + (double)v; }
+template <>
+__device__ __forceinline__ df32 acc_addT<float, df32>(df32 a, float v) { return df_add(a, v); }
+
+// JF[b][c][N] (c = J, Fx, Fy, Fz) from the band's sweep-unit partials.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) reduce_units_kernel(const RedUnit *__restrict__ ru,
+                                                            const int *__restrict__ ru_begin,
+                                                            Acc *__restrict__ JF, int nx, int ny, int nz)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int b = blockIdx.z / nz, k = blockIdx.z % nz;
+    if (i >= nx || j >= ny) return;
+    const long long N = (long long)nx * ny * nz;
+    const long long noff = ((long long)k * ny + j) * nx + i;
+    const long long toff = ((long long)i * nz + k) * ny + j;
+    Acc s[4];
+    for (int c = 0; c < 4; ++c) s[c] = acc_zero((Acc *)nullptr);
+    for (int u = ru_begin[b]; u < ru_begin[b + 1]; ++u) {
+        const T *p = (const T *)ru[u].partial;
+        const long long off = ru[u].axis == 0 ? toff : noff;
+        for (int c = 0; c < 4; ++c) s[c] = acc_addT<T, Acc>(s[c], p[c * N + off]);
+    }
+    for (int c = 0; c < 4; ++c) JF[((long long)b * 4 + c) * N + noff] = s[c];
+}
+
+struct QParams {
+    int nx, ny, nz, nbands;
+    double inv2dx, inv2dy, inv2dz, invdz;   // stencil coefficients
+    double thin;                            // min(dx,dy,dz) / tau_switch
+};
+
+__device__ __forceinline__ void blend_weights(double chi, double thin, double &om, double &omc)
+{
+    const double x = chi * thin;
+    om = exp(-x);
+    omc = -expm1(-x);
+}
+__device__ __forceinline__ void blend_weights(float chi, float thin, float &om, float &omc)
+{
+    const float x = chi * thin;
+    om = expf(-x);
+    omc = -expm1f(-x);
+}
+
+__device__ __forceinline__ double accT(double *, double v) { return v; }
+__device__ __forceinline__ double accT(double *, float v) { return (double)v; }
+__device__ __forceinline__ df32 accT(df32 *, float v) { return df_make(v); }
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) qstep_kernel(const Acc *__restrict__ JF, const T *__restrict__ chi,
+                                                     const T *__restrict__ S, QParams P,
+                                                     double *__restrict__ J, double *__restrict__ F,
+                                                     double *__restrict__ Q)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= P.nx || j >= P.ny) return;
+    const long long nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long N = nx * ny * nz;
+    const long long p = ((long long)k * ny + j) * nx + i;
+    const long long xp = p - i + (i + 1 == nx ? 0 : i + 1), xm = p - i + (i == 0 ? nx - 1 : i - 1);
+    const long long yp = p + ((j + 1 == ny ? 0 : j + 1) - j) * nx, ym = p + ((j == 0 ? ny - 1 : j - 1) - j) * nx;
+    long long zp, zm;
+    Acc cz;
+    Acc *tag = nullptr;
+    if (nz == 1) { zp = zm = p; cz = acc_zero(tag); }
+    else if (k == 0) { zp = p + nx * ny; zm = p; cz = acc_from(tag, P.invdz); }
+    else if (k == nz - 1) { zp = p; zm = p - nx * ny; cz = acc_from(tag, P.invdz); }
+    else { zp = p + nx * ny; zm = p - nx * ny; cz = acc_from(tag, P.inv2dz); }
+    const Acc cx = acc_from(tag, P.inv2dx), cy = acc_from(tag, P.inv2dy);
+    const Acc four_pi = acc_from(tag, 12.566370614359172953850573533118);
+
+    Acc Jt = acc_zero(tag), Fx = acc_zero(tag), Fy = acc_zero(tag), Fz = acc_zero(tag), Qt = acc_zero(tag);
+    for (int b = 0; b < P.nbands; ++b) {
+        const Acc *jf = JF + (long long)b * 4 * N;
+        const Acc Jb = jf[p];
+        const Acc fx = jf[N + p], fy = jf[2 * N + p], fz = jf[3 * N + p];
+        // -div F_b
+        const Acc dvx = acc_mul(acc_sub(jf[N + xp], jf[N + xm]), cx);
+        const Acc dvy = acc_mul(acc_sub(jf[2 * N + yp], jf[2 * N + ym]), cy);
+        const Acc dvz = acc_mul(acc_sub(jf[3 * N + zp], jf[3 * N + zm]), cz);
+        const Acc negdiv = acc_sub(acc_zero(tag), acc_add(acc_add(dvx, dvy), dvz));
+        const T c = chi[(long long)b * N + p], s = S[(long long)b * N + p];
+        const Acc qj = acc_mul(acc_mul(four_pi, accT(tag, c)), acc_sub(Jb, accT(tag, s)));
+        T om, omc;
+        blend_weights(c, (T)P.thin, om, omc);
+        const Acc qb = acc_add(acc_mul(accT(tag, om), qj), acc_mul(accT(tag, omc), negdiv));
+        Jt = acc_add(Jt, Jb);
+        Fx = acc_add(Fx, fx);
+        Fy = acc_add(Fy, fy);
+        Fz = acc_add(Fz, fz);
+        Qt = acc_add(Qt, qb);
+    }
+    if (J) J[p] = acc_to_double(Jt);
+    if (F) {
+        F[p] = acc_to_double(Fx);
+        F[N + p] = acc_to_double(Fy);
+        F[2 * N + p] = acc_to_double(Fz);
+    }
+    if (Q) Q[p] = acc_to_double(Qt);
+}
+
+}  // namespace rts

@@ -1,0 +1,593 @@
+// rts_api.cu -- C ABI of the B300 radiation transport solver (include/rts.h).
+//
+// rts_create plans the solve once per grid: the angular set, the geometry of
+// every short characteristic, the sweep units (band x direction group, up to
+// 4 directions each), their tiling, and all device scratch. rts_solve then
+// only enqueues kernels on the handle's stream:
+//   1. transpose of chi and S for the x-dominant groups (paper Sect. 5.3.1)
+//   2. one persistent sweep launch over every band and group (Sect. 5.1
+//      integrate(); Sect. 5.2 launch overhead removed by construction)
+//   3. per-band reduction of the sweep-unit partial sums, and
+//   4. the Q step (flux(): J, F and the thin/thick Q_rad blend).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "rts.h"
+#include "qstep.cuh"
+#include "sweep.cuh"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kLag = 2;  // planes between posting the seed-error bound and using it
+
+struct DirGeo {
+    int axis, sa, b1, b2, s1, s2, up;
+    double ds, d1, d2, beta[4];
+};
+
+// Geometry of the short characteristic of direction n on spacing h: the
+// upwind point r - ds n lies on the nearest grid plane perpendicular to the
+// dominant axis; its position on that plane gives bilinear corner weights.
+bool direction_geometry(const double h[3], const double n[3], DirGeo &g)
+{
+    const int order[3] = {2, 1, 0};  // ties resolved towards z, then y
+    int a = -1;
+    double best = 0;
+    for (int t = 0; t < 3; ++t) {
+        const int ax = order[t];
+        if (n[ax] == 0.0) continue;
+        const double s = h[ax] / std::fabs(n[ax]);
+        if (a < 0 || s < best) { a = ax; best = s; }
+    }
+    if (a < 0 || n[2] == 0.0) return false;
+    g.axis = a;
+    g.sa = n[a] > 0 ? 1 : -1;
+    g.b1 = a == 0 ? 1 : 0;
+    g.b2 = a == 2 ? 1 : 2;
+    g.s1 = n[g.b1] < 0 ? -1 : 1;
+    g.s2 = n[g.b2] < 0 ? -1 : 1;
+    g.ds = best;
+    g.d1 = std::min(1.0, best * std::fabs(n[g.b1]) / h[g.b1]);
+    g.d2 = std::min(1.0, best * std::fabs(n[g.b2]) / h[g.b2]);
+    g.beta[0] = (1 - g.d1) * (1 - g.d2);
+    g.beta[1] = g.d1 * (1 - g.d2);
+    g.beta[2] = (1 - g.d1) * g.d2;
+    g.beta[3] = g.d1 * g.d2;
+    g.up = n[2] > 0;
+    return true;
+}
+
+// Default angular set: 3 directions per octant, each with two components
+// mu1 and one component mu2 = sqrt(1 - 2 mu1^2); mu1^2 = (1 - sqrt(2/5))/3
+// makes the set integrate the 4th moment of each axis exactly (S4 level
+// symmetric). Order: groups +z, -z, +x, -x, +y, -y, minor signs (+,+),(-,+),(+,-),(-,-).
+void default_quadrature(std::vector<double> &n, std::vector<double> &w)
+{
+    const double m1 = std::sqrt((1.0 - std::sqrt(0.4)) / 3.0);
+    const double m2 = std::sqrt(1.0 - 2.0 * m1 * m1);
+    const int axis_of[6] = {2, 2, 0, 0, 1, 1};
+    n.clear();
+    w.clear();
+    for (int grp = 0; grp < 6; ++grp) {
+        const int ax = axis_of[grp];
+        const double sa = grp % 2 == 0 ? 1.0 : -1.0;
+        const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+        for (int m = 0; m < 4; ++m) {
+            double v[3];
+            v[ax] = sa * m2;
+            v[b1] = (m & 1) ? -m1 : m1;
+            v[b2] = (m & 2) ? -m1 : m1;
+            n.insert(n.end(), v, v + 3);
+            w.push_back(1.0 / 24.0);
+        }
+    }
+}
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct rts_handle {
+    rts_grid g{};
+    int B = 0, ndir = 0, n_up = 0, n_dn = 0;
+    std::vector<double> n, w;
+    rts_options opt{};
+    cudaStream_t stream = nullptr;
+    int esize = 8;  // bytes of the sweep precision
+
+    std::vector<rts::SweepUnit> units;
+    std::vector<int> unit_of_tile;
+    int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, ppt = 4, tq = 0;
+    size_t smem = 0;
+    bool has_x = false;
+    long long N = 0;
+
+    // device memory (one allocation, carved)
+    void *dmem = nullptr;
+    rts::SweepUnit *d_units = nullptr;
+    int *d_unit_of_tile = nullptr;
+    void *d_partial = nullptr, *d_chiT = nullptr, *d_ST = nullptr, *d_JF = nullptr, *d_halo = nullptr;
+    int *d_flags = nullptr, *d_ticket = nullptr, *d_status = nullptr, *d_unit_tacc = nullptr;
+    unsigned long long *d_gsync = nullptr;
+    rts::RedUnit *d_ru = nullptr;
+    int *d_ru_begin = nullptr;
+    // host-IO staging
+    void *d_in_chi = nullptr, *d_in_S = nullptr, *d_out_itop = nullptr;
+    double *d_out_J = nullptr, *d_out_F = nullptr, *d_out_Q = nullptr;
+
+    char err[512] = {0};
+};
+
+static rts_status fail(rts_handle *h, rts_status s, const char *fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CUDA_TRY(h, call)                                                                      \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(h, RTS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T, int PPT>
+static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a)
+{
+    auto kern = rts::sweep_kernel<T, PPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(h->grid);
+    cfg.blockDim = dim3(rts::SWEEP_NT);
+    cfg.dynamicSmemBytes = h->smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+template <typename T, int PPT>
+static cudaError_t occupancy(rts_handle *h, int *blocks)
+{
+    auto kern = rts::sweep_kernel<T, PPT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, rts::SWEEP_NT, h->smem);
+}
+
+template <typename T>
+static cudaError_t dispatch_occupancy(rts_handle *h, int *blocks)
+{
+    switch (h->ppt) {
+    case 2: return occupancy<T, 2>(h, blocks);
+    case 4: return occupancy<T, 4>(h, blocks);
+    default: return occupancy<T, 8>(h, blocks);
+    }
+}
+
+template <typename T>
+static cudaError_t dispatch_sweep(rts_handle *h, const rts::SweepArgs<T> &a)
+{
+    switch (h->ppt) {
+    case 2: return launch_sweep<T, 2>(h, a);
+    case 4: return launch_sweep<T, 4>(h, a);
+    default: return launch_sweep<T, 8>(h, a);
+    }
+}
+
+extern "C" {
+
+void rts_default_options(rts_options *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->prec = RTS_FP64;
+    o->tau_switch = 0.1;
+    o->wrap_tol = 0.0;  // 0 = precision default
+    o->max_wrap_iters = 64;
+    o->timeout_s = 2.0;
+}
+
+const char *rts_last_error(rts_handle *h) { return h ? h->err : "null handle"; }
+
+int rts_num_up(rts_handle *h) { return h ? h->n_up : 0; }
+
+static void free_all(rts_handle *h)
+{
+    if (h->dmem) cudaFree(h->dmem);
+    h->dmem = nullptr;
+}
+
+void rts_destroy(rts_handle *h)
+{
+    if (!h) return;
+    free_all(h);
+    delete h;
+}
+
+rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts_quadrature *q,
+                      const rts_options *opt)
+{
+    if (!out) return RTS_EINVAL;
+    *out = nullptr;
+    rts_handle *h = new (std::nothrow) rts_handle();
+    if (!h) return RTS_ENOMEM;
+    if (opt) h->opt = *opt;
+    else rts_default_options(&h->opt);
+    rts_options &o = h->opt;
+    auto bail = [&](rts_status s) {
+        // keep the handle so the caller can read the error text
+        *out = h;
+        return s;
+    };
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 2 || nbands < 1)
+        return bail(fail(h, RTS_EINVAL, "grid must have nx, ny >= 1, nz >= 2 and nbands >= 1"));
+    if (!(g->dx > 0 && g->dy > 0 && g->dz > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dy) ||
+        !std::isfinite(g->dz))
+        return bail(fail(h, RTS_EINVAL, "grid spacing must be finite and positive"));
+    if (o.prec != RTS_FP64 && o.prec != RTS_FP32_MIXED && o.prec != RTS_FP32_COMPENSATED)
+        return bail(fail(h, RTS_EINVAL, "unknown precision %d", (int)o.prec));
+    if (!(o.tau_switch > 0)) return bail(fail(h, RTS_EINVAL, "tau_switch must be > 0"));
+    if (o.max_wrap_iters < 1) o.max_wrap_iters = 64;
+    if (!(o.timeout_s > 0)) o.timeout_s = 2.0;
+    if (!(o.wrap_tol > 0)) o.wrap_tol = o.prec == RTS_FP64 ? 1e-15 : 1e-9;
+    h->g = *g;
+    h->B = nbands;
+    h->stream = (cudaStream_t)o.stream;
+    h->esize = o.prec == RTS_FP64 ? 8 : 4;
+
+    if (q && q->ndir > 0) {
+        if (!q->n || !q->w) return bail(fail(h, RTS_EINVAL, "quadrature arrays are NULL"));
+        h->n.assign(q->n, q->n + 3 * q->ndir);
+        h->w.assign(q->w, q->w + q->ndir);
+    } else {
+        default_quadrature(h->n, h->w);
+    }
+    h->ndir = (int)h->w.size();
+    const double hsp[3] = {g->dx, g->dy, g->dz};
+    std::vector<DirGeo> geo(h->ndir);
+    std::vector<int> udx(h->ndir);
+    for (int d = 0; d < h->ndir; ++d) {
+        if (!direction_geometry(hsp, &h->n[3 * d], geo[d]))
+            return bail(fail(h, RTS_EINVAL, "direction %d has n_z == 0 or is zero", d));
+        udx[d] = geo[d].up ? h->n_up++ : h->n_dn++;
+    }
+
+    const long long nx = g->nx, ny = g->ny, nz = g->nz;
+    h->N = nx * ny * nz;
+
+    // ---- sweep units: band x (axis, sign) group, chunks of up to 4 directions ----
+    struct GroupKey { int axis, sa; };
+    // wrap groups (x, y) first: they run longer (warm-up), then z
+    const GroupKey keys[6] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}, {2, 1}, {2, -1}};
+    std::vector<std::vector<int>> chunks;
+    std::vector<GroupKey> chunk_key;
+    for (const GroupKey &k : keys) {
+        std::vector<int> ds;
+        for (int d = 0; d < h->ndir; ++d)
+            if (geo[d].axis == k.axis && geo[d].sa == k.sa) ds.push_back(d);
+        for (size_t c = 0; c < ds.size(); c += rts::MAXD) {
+            chunks.emplace_back(ds.begin() + c, ds.begin() + std::min(ds.size(), c + rts::MAXD));
+            chunk_key.push_back(k);
+        }
+    }
+    // tiling: TQ rows x the full periodic P extent per CTA
+    auto extents = [&](int axis, int &NP, int &NQ, int &NM) {
+        if (axis == 2) { NP = (int)nx; NQ = (int)ny; NM = (int)nz; }
+        else if (axis == 1) { NP = (int)nx; NQ = (int)nz; NM = (int)ny; }
+        else { NP = (int)ny; NQ = (int)nz; NM = (int)nx; }
+    };
+    int npmax = 0;
+    for (const GroupKey &k : chunk_key) {
+        int NP, NQ, NM;
+        extents(k.axis, NP, NQ, NM);
+        npmax = std::max(npmax, NP);
+    }
+    if (npmax > 1024) return bail(fail(h, RTS_EINVAL, "plane extent %d > 1024 is not supported", npmax));
+    int tq = o.tile_rows > 0 ? o.tile_rows : std::max(1, 1024 / npmax);
+    while (tq > 1 && (long long)tq * npmax > 8 * rts::SWEEP_NT) --tq;
+    h->tq = tq;
+    const int npts_max = tq * npmax;
+    h->ppt = npts_max <= 2 * rts::SWEEP_NT ? 2 : (npts_max <= 4 * rts::SWEEP_NT ? 4 : 8);
+    const int RW = tq + 2;
+    h->smem = (size_t)(rts::MAXD + 2) * RW * npmax * h->esize + (size_t)rts::MAXD * RW * npmax * sizeof(float);
+    if (h->smem > 227 * 1024) return bail(fail(h, RTS_EINVAL, "tile of %d rows needs %zu B shared memory", tq, h->smem));
+
+    long long halo_elems = 0;
+    int tile0 = 0;
+    for (int b = 0; b < nbands; ++b) {
+        for (size_t c = 0; c < chunks.size(); ++c) {
+            const GroupKey k = chunk_key[c];
+            rts::SweepUnit U;
+            std::memset(&U, 0, sizeof(U));
+            U.N = h->N;
+            U.band = b;
+            U.axis = k.axis;
+            U.sa = k.sa;
+            extents(k.axis, U.NP, U.NQ, U.NM);
+            if (k.axis == 2) { U.sQ = nx; U.sM = nx * ny; U.transposed = 0; U.qper = 1; U.wrap = 0; }
+            else if (k.axis == 1) { U.sQ = nx * ny; U.sM = nx; U.transposed = 0; U.qper = 0; U.wrap = 1; }
+            else { U.sQ = ny; U.sM = nz * ny; U.transposed = 1; U.qper = 0; U.wrap = 1; h->has_x = true; }
+            U.nd = (int)chunks[c].size();
+            U.TQ = std::min(tq, U.NQ);
+            U.ntiles = (U.NQ + U.TQ - 1) / U.TQ;
+            U.tile0 = tile0;
+            U.nx = (int)nx;
+            U.ny = (int)ny;
+            U.halo_off = halo_elems;
+            for (int i = 0; i < U.nd; ++i) {
+                const int d = chunks[c][i];
+                const DirGeo &G = geo[d];
+                for (int cc = 0; cc < 4; ++cc) U.beta[i][cc] = G.beta[cc];
+                U.ds[i] = G.ds;
+                U.cJ[i] = h->w[d];
+                for (int cc = 0; cc < 3; ++cc) U.cF[cc][i] = 4.0 * kPi * h->w[d] * h->n[3 * d + cc];
+                U.sP[i] = G.s1;
+                U.sQd[i] = G.s2;
+                U.up[i] = G.up;
+                U.udx[i] = udx[d];
+            }
+            halo_elems += (long long)U.ntiles * 8 * rts::MAXD * U.NP;
+            for (int t = 0; t < U.ntiles; ++t) h->unit_of_tile.push_back((int)h->units.size());
+            tile0 += U.ntiles;
+            h->max_ntiles = std::max(h->max_ntiles, U.ntiles);
+            h->units.push_back(U);
+        }
+    }
+    h->total_tiles = tile0;
+    int R = 8;
+    while (R < 2 * (h->max_ntiles + kLag + 2)) R *= 2;
+    h->R = R;
+
+    // ---- residency of the persistent launch ----
+    int dev = 0, nsm = 0, blocks = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    cudaError_t oe = o.prec == RTS_FP64 ? dispatch_occupancy<double>(h, &blocks) : dispatch_occupancy<float>(h, &blocks);
+    if (oe != cudaSuccess) return bail(fail(h, RTS_ECUDA, "occupancy query: %s", cudaGetErrorString(oe)));
+    h->grid = std::min(h->total_tiles, blocks * nsm);
+    if (blocks < 1 || h->grid < h->max_ntiles)
+        return bail(fail(h, RTS_EINVAL, "a sweep unit has %d tiles but only %d CTAs fit on the GPU", h->max_ntiles,
+                         blocks * nsm));
+
+    // ---- device memory ----
+    const size_t es = h->esize;
+    const size_t accsz = 8;  // double or df32
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = round_up(off + bytes, 256); return at; };
+    const size_t o_units = take(sizeof(rts::SweepUnit) * h->units.size());
+    const size_t o_uot = take(sizeof(int) * h->unit_of_tile.size());
+    const size_t o_part = take((size_t)h->units.size() * 4 * h->N * es);
+    const size_t o_chiT = h->has_x ? take((size_t)nbands * h->N * es) : 0;
+    const size_t o_ST = h->has_x ? take((size_t)nbands * h->N * es) : 0;
+    const size_t o_JF = take((size_t)nbands * 4 * h->N * accsz);
+    const size_t o_halo = take((size_t)halo_elems * es);
+    const size_t o_flags = take(sizeof(int) * h->total_tiles);
+    const size_t o_gsync = take(sizeof(unsigned long long) * (size_t)h->total_tiles * R);
+    const size_t o_ticket = take(sizeof(int) * 4);
+    const size_t o_status = take(sizeof(int) * 4);
+    const size_t o_tacc = take(sizeof(int) * h->units.size());
+    const size_t o_ru = take(sizeof(rts::RedUnit) * h->units.size());
+    const size_t o_rub = take(sizeof(int) * (nbands + 1));
+    size_t o_io[6] = {0};
+    const bool hostio = (o.flags & RTS_FLAG_HOST_IO) != 0;
+    if (hostio) {
+        o_io[0] = take((size_t)nbands * h->N * es);
+        o_io[1] = take((size_t)nbands * h->N * es);
+        o_io[2] = take((size_t)nbands * h->n_up * nx * ny * es);
+        o_io[3] = take((size_t)h->N * 8);
+        o_io[4] = take((size_t)3 * h->N * 8);
+        o_io[5] = take((size_t)h->N * 8);
+    }
+    cudaError_t ae = cudaMalloc(&h->dmem, off);
+    if (ae != cudaSuccess) {
+        h->dmem = nullptr;
+        return bail(fail(h, RTS_ENOMEM, "cudaMalloc of %zu bytes: %s", off, cudaGetErrorString(ae)));
+    }
+    char *base = (char *)h->dmem;
+    h->d_units = (rts::SweepUnit *)(base + o_units);
+    h->d_unit_of_tile = (int *)(base + o_uot);
+    h->d_partial = base + o_part;
+    h->d_chiT = h->has_x ? base + o_chiT : nullptr;
+    h->d_ST = h->has_x ? base + o_ST : nullptr;
+    h->d_JF = base + o_JF;
+    h->d_halo = base + o_halo;
+    h->d_flags = (int *)(base + o_flags);
+    h->d_gsync = (unsigned long long *)(base + o_gsync);
+    h->d_ticket = (int *)(base + o_ticket);
+    h->d_status = (int *)(base + o_status);
+    h->d_unit_tacc = (int *)(base + o_tacc);
+    h->d_ru = (rts::RedUnit *)(base + o_ru);
+    h->d_ru_begin = (int *)(base + o_rub);
+    if (hostio) {
+        h->d_in_chi = base + o_io[0];
+        h->d_in_S = base + o_io[1];
+        h->d_out_itop = base + o_io[2];
+        h->d_out_J = (double *)(base + o_io[3]);
+        h->d_out_F = (double *)(base + o_io[4]);
+        h->d_out_Q = (double *)(base + o_io[5]);
+    }
+    // partial pointers and the reduction table (units are band-major)
+    std::vector<rts::RedUnit> ru(h->units.size());
+    std::vector<int> rub(nbands + 1, 0);
+    for (size_t u = 0; u < h->units.size(); ++u) {
+        h->units[u].partial = (char *)h->d_partial + u * 4 * h->N * es;
+        ru[u].partial = h->units[u].partial;
+        ru[u].axis = h->units[u].axis;
+        rub[h->units[u].band + 1]++;
+    }
+    for (int b = 0; b < nbands; ++b) rub[b + 1] += rub[b];
+    CUDA_TRY(h, cudaMemcpy(h->d_units, h->units.data(), sizeof(rts::SweepUnit) * h->units.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_unit_of_tile, h->unit_of_tile.data(), sizeof(int) * h->unit_of_tile.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * ru.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, rub.data(), sizeof(int) * rub.size(), cudaMemcpyHostToDevice));
+    *out = h;
+    return RTS_OK;
+}
+
+}  // extern "C"
+
+template <typename T, typename Acc>
+static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top,
+                             double *J, double *F, double *Q)
+{
+    const rts_grid &g = h->g;
+    const int B = h->B;
+    cudaStream_t st = h->stream;
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->total_tiles, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gsync, 0, sizeof(unsigned long long) * (size_t)h->total_tiles * h->R, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
+    if (h->has_x) {
+        dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
+        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)h->d_chiT, g.nx, g.ny, g.nz);
+        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)h->d_ST, g.nx, g.ny, g.nz);
+        CUDA_TRY(h, cudaGetLastError());
+    }
+    rts::SweepArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.units = h->d_units;
+    a.unit_of_tile = h->d_unit_of_tile;
+    a.total_tiles = h->total_tiles;
+    a.chi = (const T *)chi;
+    a.S = (const T *)S;
+    a.chiT = (const T *)h->d_chiT;
+    a.ST = (const T *)h->d_ST;
+    a.itop = (T *)I_top;
+    a.bc_bottom = bc ? bc->bottom : RTS_BC_EQUAL_S;
+    a.bc_top = bc ? bc->top : RTS_BC_ZERO;
+    a.bc_up = bc ? (const T *)bc->bottom_I : nullptr;
+    a.bc_dn = bc ? (const T *)bc->top_I : nullptr;
+    a.n_up = h->n_up;
+    a.n_dn = h->n_dn;
+    a.ticket = h->d_ticket;
+    a.flags = h->d_flags;
+    a.halo = (T *)h->d_halo;
+    a.gsync = h->d_gsync;
+    a.R = h->R;
+    a.L = kLag;
+    a.status = h->d_status;
+    a.unit_tacc = h->d_unit_tacc;
+    a.tol = (float)h->opt.wrap_tol;
+    a.max_periods = h->opt.max_wrap_iters;
+    a.timeout_ns = (unsigned long long)(h->opt.timeout_s * 1e9);
+    cudaError_t e = dispatch_sweep<T>(h, a);
+    if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+    if (J || F || Q) {
+        dim3 rb(32, 8), rg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)(g.nz * B));
+        rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
+        rts::QParams P;
+        P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
+        P.inv2dx = 0.5 / g.dx; P.inv2dy = 0.5 / g.dy; P.inv2dz = 0.5 / g.dz; P.invdz = 1.0 / g.dz;
+        P.thin = std::min(g.dx, std::min(g.dy, g.dz)) / h->opt.tau_switch;
+        dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
+        rts::qstep_kernel<T, Acc><<<qg, rb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, P, J, F, Q);
+        CUDA_TRY(h, cudaGetLastError());
+    }
+    return RTS_OK;
+}
+
+static rts_status check_bc(rts_handle *h, const rts_boundary *bc)
+{
+    if (!bc) return RTS_OK;
+    if (bc->bottom < RTS_BC_ZERO || bc->bottom > RTS_BC_EXPLICIT || bc->top < RTS_BC_ZERO || bc->top > RTS_BC_EXPLICIT)
+        return fail(h, RTS_EINVAL, "unknown boundary kind");
+    if (bc->bottom == RTS_BC_EXPLICIT && !bc->bottom_I) return fail(h, RTS_EINVAL, "bottom_I is NULL");
+    if (bc->top == RTS_BC_EXPLICIT && !bc->top_I) return fail(h, RTS_EINVAL, "top_I is NULL");
+    return RTS_OK;
+}
+
+extern "C" {
+
+rts_status rts_solve(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top, double *J,
+                     double *F, double *Q)
+{
+    if (!h || !h->dmem) return h ? fail(h, RTS_EINVAL, "handle was not created successfully") : RTS_EINVAL;
+    if (!chi || !S) return fail(h, RTS_EINVAL, "chi and S must not be NULL");
+    rts_status s = check_bc(h, bc);
+    if (s) return s;
+    switch (h->opt.prec) {
+    case RTS_FP64: return solve_impl<double, double>(h, chi, S, bc, I_top, J, F, Q);
+    case RTS_FP32_MIXED: return solve_impl<float, double>(h, chi, S, bc, I_top, J, F, Q);
+    default: return solve_impl<float, rts::df32>(h, chi, S, bc, I_top, J, F, Q);
+    }
+}
+
+rts_status rts_solve_host(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top,
+                          double *J, double *F, double *Q)
+{
+    if (!h || !h->dmem) return h ? fail(h, RTS_EINVAL, "handle was not created successfully") : RTS_EINVAL;
+    if (!h->d_in_chi) return fail(h, RTS_EINVAL, "rts_solve_host needs RTS_FLAG_HOST_IO at create time");
+    if (!chi || !S) return fail(h, RTS_EINVAL, "chi and S must not be NULL");
+    if (bc && (bc->bottom == RTS_BC_EXPLICIT || bc->top == RTS_BC_EXPLICIT))
+        return fail(h, RTS_EINVAL, "rts_solve_host does not take explicit boundary arrays");
+    rts_status s = check_bc(h, bc);
+    if (s) return s;
+    cudaStream_t st = h->stream;
+    const size_t in_bytes = (size_t)h->B * h->N * h->esize;
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_in_chi, chi, in_bytes, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->d_in_S, S, in_bytes, cudaMemcpyHostToDevice, st));
+    s = rts_solve(h, h->d_in_chi, h->d_in_S, bc, I_top ? h->d_out_itop : nullptr, J ? h->d_out_J : nullptr,
+                  F ? h->d_out_F : nullptr, Q ? h->d_out_Q : nullptr);
+    if (s) return s;
+    const size_t plane = (size_t)h->g.nx * h->g.ny;
+    if (I_top)
+        CUDA_TRY(h, cudaMemcpyAsync(I_top, h->d_out_itop, (size_t)h->B * h->n_up * plane * h->esize, cudaMemcpyDeviceToHost, st));
+    if (J) CUDA_TRY(h, cudaMemcpyAsync(J, h->d_out_J, h->N * 8, cudaMemcpyDeviceToHost, st));
+    if (F) CUDA_TRY(h, cudaMemcpyAsync(F, h->d_out_F, 3 * h->N * 8, cudaMemcpyDeviceToHost, st));
+    if (Q) CUDA_TRY(h, cudaMemcpyAsync(Q, h->d_out_Q, h->N * 8, cudaMemcpyDeviceToHost, st));
+    return rts_check(h);
+}
+
+rts_status rts_check(rts_handle *h)
+{
+    if (!h || !h->dmem) return RTS_EINVAL;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int st = 0;
+    CUDA_TRY(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & rts::ST_TIMEOUT) return fail(h, RTS_ETIMEOUT, "a device-side wait exceeded %.3g s", h->opt.timeout_s);
+    if (st & rts::ST_NOCONV)
+        return fail(h, RTS_ENOCONV, "periodic wrap not converged within %d periods", h->opt.max_wrap_iters);
+    return RTS_OK;
+}
+
+rts_status rts_get_stats(rts_handle *h, rts_stats *out)
+{
+    if (!h || !h->dmem || !out) return RTS_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->n_units = (int)h->units.size();
+    out->n_tiles = h->total_tiles;
+    rts_status s = rts_check(h);
+    out->device_status = s;
+    std::vector<int> tacc(h->units.size());
+    CUDA_TRY(h, cudaMemcpy(tacc.data(), h->d_unit_tacc, sizeof(int) * tacc.size(), cudaMemcpyDeviceToHost));
+    int nw = 0;
+    double sum = 0;
+    for (size_t u = 0; u < tacc.size(); ++u) {
+        if (!h->units[u].wrap) continue;
+        out->max_warmup_steps = std::max(out->max_warmup_steps, tacc[u]);
+        sum += tacc[u];
+        ++nw;
+    }
+    out->mean_warmup_steps = nw ? sum / nw : 0.0;
+    return s;
+}
+
+}  // extern "C"
