@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the B300 RTS solve on the paper's 288^3 test size, 4 bands.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+A step is one forward solve (rts_solve: transpose, persistent sweep over all
+bands and direction groups, per-band reduction, Q step) of the synthetic
+288^3 x 4-band stratified atmosphere with the FP32 sweep and FP64 Q step,
+inputs resident in HBM (764 MB of chi/S, larger than L2, so no flush is
+needed between steps). The metric is point x direction x band updates per
+second (Gupd/s = 288^3 * 24 * 4 / t). One JSON line is printed by rank 0.
+
+Extra keys: roofline of the sweep kernel (timed live with CUDA events on its
+own stream through the library's phase timer), the FP64 solve, the end-to-end
+number through rts_solve_host (host buffers, copies inside the timed region),
+the CPU oracle timed on this host, and SM clocks sampled during the timed
+region. Under torchrun (N > 1) every rank solves its own replica (no data-path
+collective); timing is the max over ranks.
+
+--impl reference times the CPU oracle (the paper has no code to run) on a
+bounded sample of the same workload and prints the same kind of line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gupd/s (pts×dirs×bands) 288³×4 bands FP32 vs FP64, %HBM; adjoint/fwd ratio"
+WORKLOAD = "rts288x4"
+NX = NY = NZ = 288
+NB = 4
+NDIR = 24
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def _config(prec):
+    return {
+        "grid": [NX, NY, NZ],
+        "workload": f"rts288x4: {NX}x{NY}x{NZ} periodic grid, 4 opacity bands (chi x {{1,10,100,1000}}, "
+                    "S = T^4 x {0.4,0.3,0.2,0.1}), 24 rays (S4 Carlson), bottom I=S, top I=0",
+        "precision": prec,
+        "sweep": "FP32 sweep" if prec != "fp64" else "FP64 sweep",
+        "q_step": {"fp32": "FP64", "fp32_compensated": "double-float (2xFP32)", "fp64": "FP64"}[prec],
+        "l2": "inputs (764 MB chi+S FP32) larger than the 126 MB L2; no flush between steps",
+        "step": "one rts_solve over all 4 bands and 24 rays",
+    }
+
+
+# ----------------------------------------------------------------------------
+# SM clocks and throttle reasons during the timed region (NVML, read only)
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    """Samples SM clock and clock-event reasons while the timed region runs:
+    NVML when its library loads, else `nvidia-smi -lms` (both read only)."""
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+               0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+               0x100: "display_clock_setting"}
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.reasons = 0
+        self.max_mhz = None
+        self._stop = threading.Event()
+        self.mode = None
+        self.err = None
+        try:
+            import pynvml
+
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.mode = "nvml"
+        except Exception as e:
+            self.err = f"nvml: {e}"
+            self.mode = "nvidia-smi"
+
+    def _reason_bits(self):
+        for name in ("nvmlDeviceGetCurrentClocksEventReasons", "nvmlDeviceGetCurrentClocksThrottleReasons"):
+            f = getattr(self.nv, name, None)
+            if f is not None:
+                try:
+                    return f(self.h)
+                except Exception:
+                    continue
+        return 0
+
+    def _run_nvml(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self.nv.nvmlDeviceGetClockInfo(self.h, self.nv.NVML_CLOCK_SM))
+                self.reasons |= self._reason_bits()
+            except Exception as e:
+                self.err = f"nvml sample: {e}"
+            time.sleep(0.005)
+
+    def __enter__(self):
+        if self.mode == "nvml":
+            self.t = threading.Thread(target=self._run_nvml, daemon=True)
+            self.t.start()
+        else:
+            import subprocess
+
+            q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active")
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                              "--format=csv,noheader,nounits", "-lms", "20"],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception as e:
+                self.proc = None
+                self.err = (self.err or "") + f"; nvidia-smi: {e}"
+        return self
+
+    def __exit__(self, *a):
+        if self.mode == "nvml":
+            self._stop.set()
+            self.t.join()
+        elif self.proc is not None:
+            self.proc.terminate()
+            out, _ = self.proc.communicate()
+            for line in out.splitlines():
+                f = [x.strip() for x in line.split(",")]
+                try:
+                    self.samples.append(float(f[0]))
+                    self.max_mhz = float(f[1])
+                    self.reasons |= int(f[2], 16)
+                except Exception:
+                    continue
+
+    def summary(self):
+        names = [n for b, n in self.REASONS.items() if self.reasons & b and n != "gpu_idle"]
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(self.samples), "source": self.mode, "error": self.err}
+
+
+# ----------------------------------------------------------------------------
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _traffic_from_profile(prec):
+    """DRAM bytes per sweep launch from the committed ncu summary, or None if
+    the sweep source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "sweep_rts288x4_dram.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2107_08145_b300", "csrc", "sweep.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("sweep_source_sha256_16") != digest or rec.get("precision") != prec:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def sweep_algorithmic_bytes(prec, nb=NB, ndir=NDIR):
+    """Per launch: every sweep unit (band x group of 4 rays) reads its band's
+    chi and S once and writes its 4 partial sums (J, Fx, Fy, Fz) once; plus
+    the upward intensities at the top."""
+    es = 8 if prec == "fp64" else 4
+    n = NX * NY * NZ
+    units = nb * (ndir // 4)
+    return units * n * (2 * es + 4 * es) + nb * (ndir // 2) * NX * NY * es
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2107_08145_b300 as rts
+    from workloads import workload
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = args.precision
+    chi64, S64 = workload(WORKLOAD, nx=NX, ny=NY, nz=NZ)
+    upd = NX * NY * NZ * NDIR * NB
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if ws == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    s = rts.Solver(NX, NY, NZ, NB, precision=prec, timing=True, stream=stream)
+    chi = torch.as_tensor(chi64, dtype=s.dtype, device=dev)
+    S = torch.as_tensor(S64, dtype=s.dtype, device=dev)
+    out = s.solve(chi, S)
+    for _ in range(args.warmup):
+        s.solve(chi, S, out=out, check=False)
+    s.check()
+    s.stats()  # resets the phase timer
+    clk = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            s.solve(chi, S, out=out, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms)
+    s.check()
+    st = s.stats()
+    value = ws * upd / (ms * 1e-3) / 1e9
+
+    peaks = _peaks()
+    hbm = peaks.get("hbm_gbs")
+    sweep_ms = st["ms_sweep"]
+    alg = sweep_algorithmic_bytes(prec)
+    achieved = alg / (sweep_ms * 1e-3) / 1e9
+    roofline = {"kernel": "sweep_kernel (persistent tile-DAG sweep, all bands and groups)",
+                "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm if hbm else 6400.0,
+                "unit": "GB/s", "frac": round(achieved / (hbm if hbm else 6400.0), 5),
+                "peak_source": "of measured" if hbm else "of fallback",
+                "traffic": _traffic_from_profile(prec), "algorithmic_bytes_per_launch": alg,
+                "sweep_ms_mean": round(sweep_ms, 4), "launches_timed": st["timed_solves"]}
+    phases = {k: round(st[k], 4) for k in ("ms_transpose", "ms_sweep", "ms_reduce", "ms_qstep")}
+
+    extra = {}
+    # FP64 solve of the same workload (the plain FP64 reference form)
+    if not args.skip_fp64 and prec != "fp64":
+        s64 = rts.Solver(NX, NY, NZ, NB, precision="fp64", timing=True, stream=stream)
+        c64 = torch.as_tensor(chi64, dtype=torch.float64, device=dev)
+        S64d = torch.as_tensor(S64, dtype=torch.float64, device=dev)
+        o64 = s64.solve(c64, S64d)
+        s64.stats()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        n64 = 2
+        for _ in range(n64):
+            s64.solve(c64, S64d, out=o64, check=False)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        s64.check()
+        ms64 = max_over_ranks(f0.elapsed_time(f1) / n64)
+        st64 = s64.stats()
+        extra["fp64"] = {"value": round(ws * upd / (ms64 * 1e-3) / 1e9, 4), "unit": "Gupd/s",
+                         "ms_per_step": round(ms64, 3), "sweep_ms": round(st64["ms_sweep"], 3)}
+        extra["fp32_over_fp64"] = round(ms64 / ms, 2)
+        del s64, c64, S64d, o64
+
+    # end to end through the public C API with host buffers
+    e2e = None
+    if not args.skip_e2e:
+        sh = rts.Solver(NX, NY, NZ, NB, precision=prec, host_io=True, stream=stream)
+        npdt = np.float64 if prec == "fp64" else np.float32
+        hc = torch.from_numpy(chi64.astype(npdt)).pin_memory().numpy()
+        hS = torch.from_numpy(S64.astype(npdt)).pin_memory().numpy()
+        pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()  # noqa: E731
+        tdt = torch.float64 if prec == "fp64" else torch.float32
+        hout = dict(I_top=pin((NB, 12, NY, NX), tdt), J=pin((NZ, NY, NX), torch.float64),
+                    F=pin((3, NZ, NY, NX), torch.float64), Q=pin((NZ, NY, NX), torch.float64))
+        sh.solve_host(hc, hS, out=hout)
+        ke = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            sh.solve_host(hc, hS, out=hout)
+        dt = max_over_ranks((time.perf_counter() - t0) / ke)
+        h2d = hc.nbytes + hS.nbytes
+        d2h = sum(v.nbytes for v in hout.values())
+        e2e = {"value": round(ws * upd / dt / 1e9, 4), "unit": "Gupd/s", "ms_per_step": round(dt * 1e3, 3),
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "api": "rts_solve_host (pinned host buffers; copies and sync inside the timed region)"}
+        del sh
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    line = {"metric": METRIC, "value": round(value, 4), "unit": "Gupd/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
+            "config": _config(prec), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clk.summary(), "gpu_launches": st["kernels_per_solve"] * args.steps,
+            "phases_ms": phases,
+            "wrap": {"max_warmup_planes": st["max_warmup_steps"], "mean_warmup_planes": st["mean_warmup_steps"]},
+            "adjoint_over_forward": None}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle
+# ----------------------------------------------------------------------------
+def _oracle_sample(oracle, chi, S, bands, dirs, threads):
+    """Oracle solve of a sample: the given bands, a subset of the 24 rays."""
+    n, w = oracle.a4_quadrature()
+    P = oracle.Problem(NX, NY, NZ, len(bands), n=n[dirs], w=w[dirs] * (NDIR / len(dirs)), max_wrap_iters=100000)
+    t0 = time.perf_counter()
+    P.solve(chi[bands], S[bands], nthreads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(budget_s):
+    """The oracle as it stands on this host's cores, on a bounded sample of
+    the workload: bands taken one at a time (all 24 rays) until the budget is
+    used; Gupd/s over what was solved."""
+    import oracle
+    from workloads import workload
+
+    chi, S = workload(WORKLOAD, nx=NX, ny=NY, nz=NZ)
+    threads = oracle.default_threads()
+    done, t = 0, 0.0
+    for b in range(NB):
+        t += _oracle_sample(oracle, chi, S, [b], list(range(NDIR)), threads)
+        done += 1
+        if t >= budget_s:
+            break
+    return {"value": round(NX * NY * NZ * NDIR * done / t / 1e9, 5), "unit": "Gupd/s", "cores": threads,
+            "kind": "oracle", "seconds": round(t, 2),
+            "sample": f"bands 0..{done - 1} of rts288x4 (all 24 rays, full 288^3 grid), FP64 C oracle, "
+                      f"OpenMP over rays on {threads} threads"}
+
+
+def run_reference(args):
+    """CPU oracle arm: each step solves a bounded sample of the workload."""
+    import oracle
+    from workloads import workload
+
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    chi, S = workload(WORKLOAD, nx=NX, ny=NY, nz=NZ)
+    threads = oracle.default_threads()
+    # one step: one band, a chunk of rays (one per thread), cycling through
+    # bands and rays so the whole run covers the workload evenly
+    chunk = min(NDIR, max(4, threads))
+    times, work = [], 0
+    for it in range(args.warmup + args.steps):
+        b = it % NB
+        d0 = (it * chunk) % NDIR
+        dirs = [(d0 + k) % NDIR for k in range(chunk)]
+        dt = _oracle_sample(oracle, chi, S, [b], dirs, threads)
+        if it >= args.warmup:
+            times.append(dt)
+            work += NX * NY * NZ * len(dirs)
+    tot = sum(times)
+    value = work / tot / 1e9
+    ms = tot / args.steps * 1e3
+    sample = (f"per step: one band x {chunk} of the 24 rays of rts288x4 (full 288^3 grid), FP64 C oracle, "
+              f"OpenMP over rays on {threads} threads")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gupd/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(args.precision),
+            "cpu_baseline": {"value": round(value, 5), "unit": "Gupd/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "Gupd/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("fp32", "fp32_compensated", "fp64"), default="fp32")
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--grid", default="288,288,288",
+                    help="NX,NY,NZ override (profiling of smaller cases); the metric is quoted at 288^3")
+    args = ap.parse_args()
+    global NX, NY, NZ
+    NX, NY, NZ = (int(v) for v in args.grid.split(","))
+    if args.warmup < 3 and args.impl == "ours":
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -81,7 +81,11 @@ typedef struct {
 } rts_quadrature;
 
 enum {
-    RTS_FLAG_HOST_IO = 1  /* allocate staging buffers for rts_solve_host */
+    RTS_FLAG_HOST_IO = 1, /* allocate staging buffers for rts_solve_host */
+    RTS_FLAG_TIMING = 2   /* record CUDA events around each phase of every
+                             solve (on the handle's stream); rts_get_stats
+                             reports their mean over the solves since the
+                             previous rts_get_stats call */
 };
 
 typedef struct {
@@ -104,6 +108,13 @@ typedef struct {
     int max_warmup_steps; /* longest periodic-wrap warm-up of the last solve (planes) */
     double mean_warmup_steps;
     int device_status;    /* rts_status recorded on the device */
+    int grid;             /* CTAs of the persistent sweep launch */
+    int tile_rows;        /* rows per sweep tile */
+    int kernels_per_solve;/* kernels one rts_solve launches */
+    /* with RTS_FLAG_TIMING: mean milliseconds per solve of each phase over the
+     * timed_solves solves since the previous call (else 0) */
+    int timed_solves;
+    float ms_transpose, ms_sweep, ms_reduce, ms_qstep;
 } rts_stats;
 
 typedef struct {
@@ -139,7 +150,8 @@ rts_status rts_solve_host(rts_handle *h, const void *chi, const void *S, const r
  * solve (RTS_OK, RTS_ETIMEOUT, RTS_ENOCONV). */
 rts_status rts_check(rts_handle *h);
 
-/* Statistics of the last solve (synchronises the stream). */
+/* Statistics of the last solve and, with RTS_FLAG_TIMING, mean phase times
+ * of the solves since the previous call (synchronises the stream). */
 rts_status rts_get_stats(rts_handle *h, rts_stats *out);
 
 /* Text of the last error on this handle (never NULL). */

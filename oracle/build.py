@@ -6,6 +6,7 @@ links against it.
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import subprocess
 
@@ -16,11 +17,17 @@ SRC = [os.path.join(HERE, "rts_oracle.c")]
 HDR = [os.path.join(HERE, "rts_oracle.h")]
 
 
+def _digest() -> str:
+    h = hashlib.sha256()
+    for f in SRC + HDR:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB + ".srchash"):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in SRC + HDR)
+    return open(LIB + ".srchash").read().strip() != _digest()
 
 
 def build_oracle(force: bool = False) -> str:
@@ -32,8 +39,11 @@ def build_oracle(force: bool = False) -> str:
     # -O2 without -ffast-math: IEEE double arithmetic in program order.
     cmd = ["gcc", "-std=c11", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wextra",
            "-o", tmp] + SRC + ["-lm"]
+    digest = _digest()
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
+    with open(LIB + ".srchash", "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

@@ -17,6 +17,7 @@ RTS_OK, RTS_EINVAL, RTS_ENOMEM, RTS_ECUDA, RTS_ETIMEOUT, RTS_ENOCONV, RTS_ENONFI
 FP64, FP32_MIXED, FP32_COMPENSATED = 0, 1, 2
 BC_ZERO, BC_EQUAL_S, BC_EXPLICIT = 0, 1, 2
 FLAG_HOST_IO = 1
+FLAG_TIMING = 2
 
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED, "fp32_compensated": FP32_COMPENSATED}
 _BC = {"zero": BC_ZERO, "equal_s": BC_EQUAL_S}
@@ -39,7 +40,10 @@ class Options(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("n_units", C.c_int), ("n_tiles", C.c_int), ("max_warmup_steps", C.c_int),
-                ("mean_warmup_steps", C.c_double), ("device_status", C.c_int)]
+                ("mean_warmup_steps", C.c_double), ("device_status", C.c_int), ("grid", C.c_int),
+                ("tile_rows", C.c_int), ("kernels_per_solve", C.c_int), ("timed_solves", C.c_int),
+                ("ms_transpose", C.c_float), ("ms_sweep", C.c_float), ("ms_reduce", C.c_float),
+                ("ms_qstep", C.c_float)]
 
 
 class Boundary(C.Structure):
@@ -110,7 +114,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, nbands=1, dx=1.0, dy=1.0, dz=1.0, precision="fp64", n=None, w=None,
                  tau_switch=0.1, wrap_tol=0.0, max_wrap_iters=64, tile_rows=0, timeout_s=2.0,
-                 host_io=False, stream=None):
+                 host_io=False, timing=False, stream=None):
         import torch
 
         L = load()
@@ -127,7 +131,7 @@ class Solver:
         o.max_wrap_iters = max_wrap_iters
         o.tile_rows = tile_rows
         o.timeout_s = timeout_s
-        o.flags = FLAG_HOST_IO if host_io else 0
+        o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -228,5 +232,4 @@ class Solver:
         s = Stats()
         rc = self._L.rts_get_stats(self._h, C.byref(s))
         self._err(rc)
-        return dict(n_units=s.n_units, n_tiles=s.n_tiles, max_warmup_steps=s.max_warmup_steps,
-                    mean_warmup_steps=s.mean_warmup_steps)
+        return {k: getattr(s, k) for k, _ in Stats._fields_ if k != "device_status"}

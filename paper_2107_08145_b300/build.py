@@ -8,6 +8,7 @@ package loads it with ctypes.
 from __future__ import annotations
 
 import glob
+import hashlib
 import os
 import subprocess
 import sys
@@ -24,11 +25,19 @@ def _inputs():
     return sorted(glob.glob(os.path.join(HERE, "csrc", "*.cu*")) + [os.path.join(ROOT, "include", "rts.h")])
 
 
+def source_hash() -> str:
+    """Hash of every source the library is built from (and of the command)."""
+    h = hashlib.sha256(" ".join(nvcc_command("out")).encode())
+    for f in _inputs():
+        h.update(f.encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(LIB + ".srchash"):
         return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(f) > t for f in _inputs())
+    return open(LIB + ".srchash").read().strip() != source_hash()
 
 
 def nvcc_command(out: str, extra=()):
@@ -42,8 +51,11 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     tmp = LIB + ".tmp.%d" % os.getpid()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    digest = source_hash()
     subprocess.run(nvcc_command(tmp, extra), check=True)
     os.replace(tmp, LIB)
+    with open(LIB + ".srchash", "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

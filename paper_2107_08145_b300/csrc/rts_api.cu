@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -123,6 +124,12 @@ struct rts_handle {
     void *d_in_chi = nullptr, *d_in_S = nullptr, *d_out_itop = nullptr;
     double *d_out_J = nullptr, *d_out_F = nullptr, *d_out_Q = nullptr;
 
+    // RTS_FLAG_TIMING: one set of phase events per solve since the last stats call
+    bool timing = false;
+    std::vector<std::array<cudaEvent_t, 5>> evs;
+    size_t nrec = 0;
+    int kernels_last = 0;
+
     char err[512] = {0};
 };
 
@@ -212,6 +219,10 @@ static void free_all(rts_handle *h)
 {
     if (h->dmem) cudaFree(h->dmem);
     h->dmem = nullptr;
+    for (auto &set : h->evs)
+        for (cudaEvent_t e : set)
+            if (e) cudaEventDestroy(e);
+    h->evs.clear();
 }
 
 void rts_destroy(rts_handle *h)
@@ -437,6 +448,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     CUDA_TRY(h, cudaMemcpy(h->d_unit_of_tile, h->unit_of_tile.data(), sizeof(int) * h->unit_of_tile.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * ru.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, rub.data(), sizeof(int) * rub.size(), cudaMemcpyHostToDevice));
+    h->timing = (o.flags & RTS_FLAG_TIMING) != 0;
     *out = h;
     return RTS_OK;
 }
@@ -455,12 +467,25 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->total_tiles, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gsync, 0, sizeof(unsigned long long) * (size_t)h->total_tiles * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
+    cudaEvent_t *ev = nullptr;
+    if (h->timing) {
+        if (h->nrec == h->evs.size()) {
+            std::array<cudaEvent_t, 5> set{};
+            for (cudaEvent_t &e : set) CUDA_TRY(h, cudaEventCreate(&e));
+            h->evs.push_back(set);
+        }
+        ev = h->evs[h->nrec++].data();
+        CUDA_TRY(h, cudaEventRecord(ev[0], st));
+    }
+    int kernels = 0;
     if (h->has_x) {
         dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
         rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)h->d_chiT, g.nx, g.ny, g.nz);
         rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)h->d_ST, g.nx, g.ny, g.nz);
         CUDA_TRY(h, cudaGetLastError());
+        kernels += 2;
     }
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev[1], st));
     rts::SweepArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     a.units = h->d_units;
@@ -490,9 +515,12 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     a.timeout_ns = (unsigned long long)(h->opt.timeout_s * 1e9);
     cudaError_t e = dispatch_sweep<T>(h, a);
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+    kernels += 1;
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
     if (J || F || Q) {
         dim3 rb(32, 8), rg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)(g.nz * B));
         rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
+        if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
         rts::QParams P;
         P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
         P.inv2dx = 0.5 / g.dx; P.inv2dy = 0.5 / g.dy; P.inv2dz = 0.5 / g.dz; P.invdz = 1.0 / g.dz;
@@ -500,7 +528,12 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
         dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
         rts::qstep_kernel<T, Acc><<<qg, rb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, P, J, F, Q);
         CUDA_TRY(h, cudaGetLastError());
+        kernels += 2;
+    } else if (ev) {
+        CUDA_TRY(h, cudaEventRecord(ev[3], st));
     }
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev[4], st));
+    h->kernels_last = kernels;
     return RTS_OK;
 }
 
@@ -587,6 +620,24 @@ rts_status rts_get_stats(rts_handle *h, rts_stats *out)
         ++nw;
     }
     out->mean_warmup_steps = nw ? sum / nw : 0.0;
+    out->grid = h->grid;
+    out->tile_rows = h->tq;
+    out->kernels_per_solve = h->kernels_last;
+    if (h->timing && h->nrec > 0) {
+        double acc[4] = {0, 0, 0, 0};
+        for (size_t r = 0; r < h->nrec; ++r)
+            for (int i = 0; i < 4; ++i) {
+                float ms = 0.f;
+                CUDA_TRY(h, cudaEventElapsedTime(&ms, h->evs[r][i], h->evs[r][i + 1]));
+                acc[i] += ms;
+            }
+        out->timed_solves = (int)h->nrec;
+        out->ms_transpose = (float)(acc[0] / h->nrec);
+        out->ms_sweep = (float)(acc[1] / h->nrec);
+        out->ms_reduce = (float)(acc[2] / h->nrec);
+        out->ms_qstep = (float)(acc[3] / h->nrec);
+        h->nrec = 0;
+    }
     return s;
 }
 
