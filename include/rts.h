@@ -162,6 +162,35 @@ int rts_num_up(rts_handle *h);
 
 void rts_destroy(rts_handle *h);
 
+/* ---------------------------------------------------------------------------
+ * Forward solve without any memory allocation. The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory --
+ * code that runs while an enclosing application is capturing a CUDA graph,
+ * or an embedding code that hands the solver a fixed memory budget and does
+ * not allow cudaMalloc outside its own pool. It runs the same kernels as
+ * rts_solve on the same inputs and outputs (caller-owned device pointers,
+ * layouts as above), with the default quadrature, bottom I = S, top I = 0 and
+ * default options, and takes all its scratch from one static device array of
+ * RTS_NOALLOC_SCRATCH_BYTES that the CUDA runtime sets up when the library is
+ * loaded on a GPU (every GPU that loads the library keeps it until exit).
+ *  - It calls no cudaMalloc/cudaFree and allocates no host memory.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture of your own.
+ *  - Problems whose scratch would not fit (about 64^3 x 2 bands in FP32) are
+ *    rejected with RTS_EINVAL and a message in err.
+ *  - All calls share the one array and it keeps the previous call's contents;
+ *    the control words are cleared on every call. Calls that overlap on the
+ *    GPU (other streams, other host threads) race: serialise them.
+ *  - The call waits for its stream and returns the device status (RTS_OK,
+ *    RTS_ETIMEOUT, RTS_ENOCONV). err (may be NULL) receives a text.
+ *  - nbands <= 16; nx, ny <= 1024. */
+#define RTS_NOALLOC_SCRATCH_BYTES (64u << 20)
+rts_status rts_solve_noalloc(const rts_grid *g, int nbands, rts_precision prec,
+                             const void *chi, const void *S,
+                             void *I_top, double *J, double *F, double *Q_rad,
+                             void *stream, char *err, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,7 +54,7 @@ _lib = None
 
 # every symbol include/rts.h declares
 EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "rts_check",
-           "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy")
+           "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc")
 
 
 def library_path() -> str:
@@ -90,6 +90,9 @@ def load(build_if_missing: bool = True):
     L.rts_num_up.restype = C.c_int
     L.rts_destroy.argtypes = [vp]
     L.rts_destroy.restype = None
+    L.rts_solve_noalloc.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp,
+                                    C.c_char_p, C.c_size_t]
+    L.rts_solve_noalloc.restype = C.c_int
     _ = dp
     _lib = L
     return L
@@ -233,3 +236,36 @@ class Solver:
         rc = self._L.rts_get_stats(self._h, C.byref(s))
         self._err(rc)
         return {k: getattr(s, k) for k, _ in Stats._fields_ if k != "device_status"}
+
+
+def solve_noalloc(chi, S, precision="fp32", dx=1.0, dy=1.0, dz=1.0, out=None, stream=None):
+    """Forward solve through rts_solve_noalloc: no device (or host) memory is
+    allocated by the library; its scratch is a fixed static device array.
+    For callers that must not allocate (inside someone else's graph capture,
+    or under a fixed memory budget). Defaults only: S4 quadrature, bottom
+    I = S, top I = 0. Outputs must be given or are made here with torch.
+    Returns the outputs dict; raises RTSError (with the library's message)
+    on failure, e.g. when the grid is too large for the fixed array."""
+    import torch
+
+    L = load()
+    B, nz, ny, nx = chi.shape
+    prec = _PREC[precision]
+    dt = torch.float64 if prec == FP64 else torch.float32
+    assert chi.dtype == dt and S.dtype == dt and chi.is_cuda and S.is_cuda
+    if out is None:
+        dev = chi.device
+        out = dict(I_top=torch.empty((B, 12, ny, nx), dtype=dt, device=dev),
+                   J=torch.empty((nz, ny, nx), dtype=torch.float64, device=dev),
+                   F=torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
+                   Q=torch.empty((nz, ny, nx), dtype=torch.float64, device=dev))
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    err = C.create_string_buffer(512)
+    g = Grid(nx, ny, nz, dx, dy, dz)
+    rc = L.rts_solve_noalloc(C.byref(g), B, prec, _ptr(chi.contiguous()), _ptr(S.contiguous()),
+                             _ptr(out.get("I_top")), _ptr(out.get("J")), _ptr(out.get("F")), _ptr(out.get("Q")),
+                             C.c_void_p(stream.cuda_stream), err, 512)
+    if rc != RTS_OK:
+        raise RTSError(rc, err.value.decode())
+    return out

@@ -17,6 +17,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -642,3 +643,315 @@ rts_status rts_get_stats(rts_handle *h, rts_stats *out)
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// rts_solve_noalloc: a forward solve for callers that cannot allocate device
+// memory (for example code running inside a caller's CUDA graph capture, or
+// an embedding application that owns a fixed device-memory budget and forbids
+// cudaMalloc outside its own pool). It runs the same kernels as rts_solve, but
+// every piece of scratch comes from one file-scope device array of fixed size
+// that the CUDA runtime creates when the library's module is loaded on a GPU
+// (every GPU that loads the library keeps it until the process exits).
+// ===========================================================================
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RTS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoallocMaxDevices = 64;
+constexpr int kNoallocMaxUnits = 6 * 16;  // 6 direction groups x 16 bands
+constexpr int kNoallocMaxTiles = 4096;
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+void noalloc_msg(char *err, size_t n, const char *fmt, ...)
+{
+    if (!err || n == 0) return;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(err, n, fmt, ap);
+    va_end(ap);
+}
+
+template <typename T, typename Acc>
+rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *S, void *I_top, double *J,
+                         double *F, double *Q, cudaStream_t st, char *err, size_t errlen)
+{
+    // device address of the scratch array on the current device, looked up once
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) {
+        noalloc_msg(err, errlen, "no usable current CUDA device");
+        return RTS_ECUDA;
+    }
+    unsigned char *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                noalloc_msg(err, errlen, "cudaGetSymbolAddress of the scratch array: %s", cudaGetErrorString(e));
+                return RTS_ECUDA;
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        base = (unsigned char *)g_noalloc_ptr[dev];
+    }
+
+    // plan: default quadrature, bottom I = S, top I = 0, default options
+    // (fixed-size host arrays: nothing is allocated, on the host or the device)
+    double n[72], w[24];
+    {
+        const double m1 = std::sqrt((1.0 - std::sqrt(0.4)) / 3.0);
+        const double m2 = std::sqrt(1.0 - 2.0 * m1 * m1);
+        const int axis_of[6] = {2, 2, 0, 0, 1, 1};
+        for (int grp = 0, d = 0; grp < 6; ++grp) {
+            const int ax = axis_of[grp];
+            const int b1 = ax == 0 ? 1 : 0, b2 = ax == 2 ? 1 : 2;
+            for (int m = 0; m < 4; ++m, ++d) {
+                n[3 * d + ax] = (grp % 2 == 0 ? 1.0 : -1.0) * m2;
+                n[3 * d + b1] = (m & 1) ? -m1 : m1;
+                n[3 * d + b2] = (m & 2) ? -m1 : m1;
+                w[d] = 1.0 / 24.0;
+            }
+        }
+    }
+    const double hsp[3] = {g->dx, g->dy, g->dz};
+    DirGeo geo[24];
+    int udx[24], nup = 0, ndn = 0;
+    for (int d = 0; d < 24; ++d) {
+        if (!direction_geometry(hsp, &n[3 * d], geo[d])) {
+            noalloc_msg(err, errlen, "direction %d has no valid geometry", d);
+            return RTS_EINVAL;
+        }
+        udx[d] = geo[d].up ? nup++ : ndn++;
+    }
+    const long long nx = g->nx, ny = g->ny, nz = g->nz, N = nx * ny * nz;
+    const int npmax = (int)std::max(nx, ny);
+    if (npmax > 1024) {
+        noalloc_msg(err, errlen, "plane extent %d > 1024 is not supported", npmax);
+        return RTS_EINVAL;
+    }
+    int tq = std::max(1, 1024 / npmax);
+    const int npts_max = tq * npmax;
+    const int ppt = npts_max <= 2 * rts::SWEEP_NT ? 2 : (npts_max <= 4 * rts::SWEEP_NT ? 4 : 8);
+    const size_t es = sizeof(T);
+    const size_t smem = (size_t)(rts::MAXD + 2) * (tq + 2) * npmax * es + (size_t)rts::MAXD * (tq + 2) * npmax * 4;
+
+    rts::SweepUnit units[kNoallocMaxUnits];
+    int unit_of_tile[kNoallocMaxTiles];
+    rts::RedUnit ru[kNoallocMaxUnits];
+    int rub[17] = {0};
+    const int keys[6][2] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}, {2, 1}, {2, -1}};
+    int nunits = 0, ntile = 0, maxnt = 0;
+    long long halo_elems = 0;
+    bool has_x = false;
+    for (int b = 0; b < B; ++b) {
+        for (const auto &k : keys) {
+            int ds[24], nd = 0;
+            for (int d = 0; d < 24; ++d)
+                if (geo[d].axis == k[0] && geo[d].sa == k[1]) ds[nd++] = d;
+            for (int c0 = 0; c0 < nd; c0 += rts::MAXD) {
+                rts::SweepUnit &U = units[nunits];
+                std::memset(&U, 0, sizeof(U));
+                U.N = N;
+                U.band = b;
+                U.axis = k[0];
+                U.sa = k[1];
+                if (U.axis == 2) { U.NP = (int)nx; U.NQ = (int)ny; U.NM = (int)nz; U.sQ = nx; U.sM = nx * ny; U.qper = 1; }
+                else if (U.axis == 1) { U.NP = (int)nx; U.NQ = (int)nz; U.NM = (int)ny; U.sQ = nx * ny; U.sM = nx; U.wrap = 1; }
+                else { U.NP = (int)ny; U.NQ = (int)nz; U.NM = (int)nx; U.sQ = ny; U.sM = nz * ny; U.wrap = 1; U.transposed = 1; has_x = true; }
+                U.nd = std::min(rts::MAXD, nd - c0);
+                U.TQ = std::min(tq, U.NQ);
+                U.ntiles = (U.NQ + U.TQ - 1) / U.TQ;
+                U.tile0 = ntile;
+                U.nx = (int)nx;
+                U.ny = (int)ny;
+                U.halo_off = halo_elems;
+                for (int i = 0; i < U.nd; ++i) {
+                    const int d = ds[c0 + i];
+                    for (int c = 0; c < 4; ++c) U.beta[i][c] = geo[d].beta[c];
+                    U.ds[i] = geo[d].ds;
+                    U.cJ[i] = w[d];
+                    for (int c = 0; c < 3; ++c) U.cF[c][i] = 4.0 * kPi * w[d] * n[3 * d + c];
+                    U.sP[i] = geo[d].s1;
+                    U.sQd[i] = geo[d].s2;
+                    U.up[i] = geo[d].up;
+                    U.udx[i] = udx[d];
+                }
+                if (ntile + U.ntiles > kNoallocMaxTiles) {
+                    noalloc_msg(err, errlen, "more than %d sweep tiles", kNoallocMaxTiles);
+                    return RTS_EINVAL;
+                }
+                for (int t = 0; t < U.ntiles; ++t) unit_of_tile[ntile + t] = nunits;
+                ntile += U.ntiles;
+                maxnt = std::max(maxnt, U.ntiles);
+                halo_elems += (long long)U.ntiles * 8 * rts::MAXD * U.NP;
+                rub[b + 1]++;
+                ++nunits;
+            }
+        }
+    }
+    for (int b = 0; b < B; ++b) rub[b + 1] += rub[b];
+    int R = 8;
+    while (R < 2 * (maxnt + kLag + 2)) R *= 2;
+
+    // carve the scratch array
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = round_up(off + bytes, 256); return at; };
+    const size_t o_units = take(sizeof(rts::SweepUnit) * nunits);
+    const size_t o_uot = take(sizeof(int) * ntile);
+    const size_t o_ru = take(sizeof(rts::RedUnit) * nunits);
+    const size_t o_rub = take(sizeof(int) * (B + 1));
+    const size_t o_flags = take(sizeof(int) * ntile);
+    const size_t o_gsync = take(sizeof(unsigned long long) * (size_t)ntile * R);
+    const size_t o_ctl = take(sizeof(int) * 8);  // ticket, status
+    const size_t o_tacc = take(sizeof(int) * nunits);
+    const size_t o_halo = take((size_t)halo_elems * es);
+    const size_t o_part = take((size_t)nunits * 4 * N * es);
+    const size_t o_chiT = has_x ? take((size_t)B * N * es) : 0;
+    const size_t o_ST = has_x ? take((size_t)B * N * es) : 0;
+    const size_t o_JF = take((size_t)B * 4 * N * sizeof(Acc));
+    if (off > (size_t)RTS_NOALLOC_SCRATCH_BYTES) {
+        noalloc_msg(err, errlen, "grid %lldx%lldx%lld with %d bands needs %zu bytes of scratch; the fixed array has %zu",
+                    nx, ny, nz, B, off, (size_t)RTS_NOALLOC_SCRATCH_BYTES);
+        return RTS_EINVAL;
+    }
+    for (int u = 0; u < nunits; ++u) {
+        units[u].partial = base + o_part + (size_t)u * 4 * N * es;
+        ru[u].partial = units[u].partial;
+        ru[u].axis = units[u].axis;
+    }
+
+    // residency of the persistent launch
+    auto kern = ppt == 2 ? rts::sweep_kernel<T, 2> : (ppt == 4 ? rts::sweep_kernel<T, 4> : rts::sweep_kernel<T, 8>);
+    int nsm = 0, blocks = 0;
+#define NA_TRY(call)                                                                              \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            noalloc_msg(err, errlen, "%s: %s", #call, cudaGetErrorString(e_));                    \
+            return RTS_ECUDA;                                                                     \
+        }                                                                                         \
+    } while (0)
+    NA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    NA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, rts::SWEEP_NT, smem));
+    const int grid = std::min(ntile, blocks * nsm);
+    if (blocks < 1 || grid < maxnt) {
+        noalloc_msg(err, errlen, "a sweep unit has %d tiles but only %d CTAs fit", maxnt, blocks * nsm);
+        return RTS_EINVAL;
+    }
+
+    // tables in, control words cleared (the array keeps the previous call's contents)
+    NA_TRY(cudaMemcpyAsync(base + o_units, units, sizeof(rts::SweepUnit) * nunits, cudaMemcpyHostToDevice, st));
+    NA_TRY(cudaMemcpyAsync(base + o_uot, unit_of_tile, sizeof(int) * ntile, cudaMemcpyHostToDevice, st));
+    NA_TRY(cudaMemcpyAsync(base + o_ru, ru, sizeof(rts::RedUnit) * nunits, cudaMemcpyHostToDevice, st));
+    NA_TRY(cudaMemcpyAsync(base + o_rub, rub, sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
+    NA_TRY(cudaMemsetAsync(base + o_flags, 0, sizeof(int) * ntile, st));
+    NA_TRY(cudaMemsetAsync(base + o_gsync, 0, sizeof(unsigned long long) * (size_t)ntile * R, st));
+    NA_TRY(cudaMemsetAsync(base + o_ctl, 0, sizeof(int) * 8, st));
+    NA_TRY(cudaMemsetAsync(base + o_tacc, 0, sizeof(int) * nunits, st));
+
+    if (has_x) {
+        dim3 tb(32, 8), tg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)(g->nz * B));
+        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)(base + o_chiT), g->nx, g->ny, g->nz);
+        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)(base + o_ST), g->nx, g->ny, g->nz);
+        NA_TRY(cudaGetLastError());
+    }
+    rts::SweepArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.units = (const rts::SweepUnit *)(base + o_units);
+    a.unit_of_tile = (const int *)(base + o_uot);
+    a.total_tiles = ntile;
+    a.chi = (const T *)chi;
+    a.S = (const T *)S;
+    a.chiT = has_x ? (const T *)(base + o_chiT) : nullptr;
+    a.ST = has_x ? (const T *)(base + o_ST) : nullptr;
+    a.itop = (T *)I_top;
+    a.bc_bottom = RTS_BC_EQUAL_S;
+    a.bc_top = RTS_BC_ZERO;
+    a.n_up = nup;
+    a.n_dn = ndn;
+    a.ticket = (int *)(base + o_ctl);
+    a.status = (int *)(base + o_ctl) + 4;
+    a.flags = (int *)(base + o_flags);
+    a.halo = (T *)(base + o_halo);
+    a.gsync = (unsigned long long *)(base + o_gsync);
+    a.R = R;
+    a.L = kLag;
+    a.unit_tacc = (int *)(base + o_tacc);
+    a.tol = sizeof(T) == 8 ? 1e-15f : 1e-9f;
+    a.max_periods = 64;
+    a.timeout_ns = 2000000000ull;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(rts::SWEEP_NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    NA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
+    if (J || F || Q) {
+        dim3 rb(32, 8), rg((g->nx + 31) / 32, (g->ny + 7) / 8, (unsigned)(g->nz * B));
+        rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>((const rts::RedUnit *)(base + o_ru),
+                                                             (const int *)(base + o_rub), (Acc *)(base + o_JF),
+                                                             g->nx, g->ny, g->nz);
+        rts::QParams P;
+        P.nx = g->nx; P.ny = g->ny; P.nz = g->nz; P.nbands = B;
+        P.inv2dx = 0.5 / g->dx; P.inv2dy = 0.5 / g->dy; P.inv2dz = 0.5 / g->dz; P.invdz = 1.0 / g->dz;
+        P.thin = std::min(g->dx, std::min(g->dy, g->dz)) / 0.1;
+        dim3 qg((g->nx + 31) / 32, (g->ny + 7) / 8, (unsigned)g->nz);
+        rts::qstep_kernel<T, Acc><<<qg, rb, 0, st>>>((const Acc *)(base + o_JF), (const T *)chi, (const T *)S, P,
+                                                      J, F, Q);
+        NA_TRY(cudaGetLastError());
+    }
+    // wait for the solve and report what the device recorded
+    NA_TRY(cudaStreamSynchronize(st));
+    int status = 0;
+    NA_TRY(cudaMemcpy(&status, base + o_ctl + 4 * sizeof(int), sizeof(int), cudaMemcpyDeviceToHost));
+#undef NA_TRY
+    if (status & rts::ST_TIMEOUT) {
+        noalloc_msg(err, errlen, "a device-side wait exceeded 2 s");
+        return RTS_ETIMEOUT;
+    }
+    if (status & rts::ST_NOCONV) {
+        noalloc_msg(err, errlen, "periodic wrap not converged within 64 periods");
+        return RTS_ENOCONV;
+    }
+    noalloc_msg(err, errlen, "ok");
+    return RTS_OK;
+}
+
+}  // namespace
+
+extern "C" rts_status rts_solve_noalloc(const rts_grid *g, int nbands, rts_precision prec, const void *chi,
+                                        const void *S, void *I_top, double *J, double *F, double *Q_rad,
+                                        void *stream, char *err, size_t errlen)
+{
+    if (!g || g->nx < 1 || g->ny < 1 || g->nz < 2 || nbands < 1 || nbands > 16) {
+        noalloc_msg(err, errlen, "grid must have nx, ny >= 1, nz >= 2 and 1 <= nbands <= 16");
+        return RTS_EINVAL;
+    }
+    if (!(g->dx > 0 && g->dy > 0 && g->dz > 0) || !std::isfinite(g->dx) || !std::isfinite(g->dy) ||
+        !std::isfinite(g->dz)) {
+        noalloc_msg(err, errlen, "grid spacing must be finite and positive");
+        return RTS_EINVAL;
+    }
+    if (!chi || !S) {
+        noalloc_msg(err, errlen, "chi and S must not be NULL");
+        return RTS_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (prec) {
+    case RTS_FP64: return noalloc_solve<double, double>(g, nbands, chi, S, I_top, J, F, Q_rad, st, err, errlen);
+    case RTS_FP32_MIXED: return noalloc_solve<float, double>(g, nbands, chi, S, I_top, J, F, Q_rad, st, err, errlen);
+    case RTS_FP32_COMPENSATED:
+        return noalloc_solve<float, rts::df32>(g, nbands, chi, S, I_top, J, F, Q_rad, st, err, errlen);
+    default: noalloc_msg(err, errlen, "unknown precision %d", (int)prec); return RTS_EINVAL;
+    }
+}
