@@ -66,6 +66,40 @@ __device__ __forceinline__ bool wait_flag_geq(const int *flag, int want, int *st
     }
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until *cnt >= want (same limits as wait_flag_geq).
+__device__ __forceinline__ bool wait_count_geq(const unsigned *cnt, unsigned want, int *status, uint64_t limit_ns)
+{
+    if (ld_acquire_u32(cnt) >= want) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        __nanosleep(64);
+        if (ld_acquire_u32(cnt) >= want) return true;
+        if (ld_relaxed(status) != 0) return false;
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Asynchronous global -> shared copies of one element (4 or 8 bytes).
+template <typename T>
+__device__ __forceinline__ void cp_async(T *smem_dst, const T *gmem_src)
+{
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "element size");
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(gmem_src), "n"(sizeof(T)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Loads that bypass L1 (data written by other CTAs during this kernel).
 template <typename T>
 __device__ __forceinline__ T ld_cg(const T *p)

@@ -107,7 +107,7 @@ struct rts_handle {
 
     std::vector<rts::SweepUnit> units;
     std::vector<int> unit_of_tile;
-    int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, ppt = 4, tq = 0;
+    int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, nt = 32, tq = 0;
     size_t smem = 0;
     bool has_x = false;
     long long N = 0;
@@ -118,7 +118,8 @@ struct rts_handle {
     int *d_unit_of_tile = nullptr;
     void *d_partial = nullptr, *d_chiT = nullptr, *d_ST = nullptr, *d_JF = nullptr, *d_halo = nullptr;
     int *d_flags = nullptr, *d_ticket = nullptr, *d_status = nullptr, *d_unit_tacc = nullptr;
-    unsigned long long *d_gsync = nullptr;
+    unsigned int *d_gcnt = nullptr;
+    unsigned long long *d_gmax = nullptr;
     rts::RedUnit *d_ru = nullptr;
     int *d_ru_begin = nullptr;
     // host-IO staging
@@ -151,15 +152,54 @@ static rts_status fail(rts_handle *h, rts_status s, const char *fmt, ...)
         if (e_ != cudaSuccess) return fail(h, RTS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
     } while (0)
 
-template <typename T, int PPT>
+template <typename T>
+using SweepFn = void (*)(rts::SweepArgs<T>);
+
+// the sweep kernel instantiated for tq rows per tile
+template <typename T>
+static SweepFn<T> sweep_fn(int tq)
+{
+    switch (tq) {
+    case 1: return rts::sweep_kernel<T, 1>;
+    case 2: return rts::sweep_kernel<T, 2>;
+    case 3: return rts::sweep_kernel<T, 3>;
+    case 4: return rts::sweep_kernel<T, 4>;
+    case 6: return rts::sweep_kernel<T, 6>;
+    default: return rts::sweep_kernel<T, 8>;
+    }
+}
+
+static const int kTileRows[6] = {8, 6, 4, 3, 2, 1};
+
+// shared memory of one sweep CTA: I (4 rays) + chi/S ring (2 slots x 2) in
+// the sweep precision, seed-error bounds (2) in FP32, each (tq+2) x np
+static size_t sweep_smem(int tq, int np, int esize)
+{
+    return (size_t)(rts::MAXD + 4) * (tq + 2) * np * esize + (size_t)2 * (tq + 2) * np * sizeof(float);
+}
+
+// rows per tile: the option if given (rounded down to an instantiated size),
+// else the largest size whose CTA fits in ~75 KB (FP32) / ~110 KB (FP64) of
+// shared memory so that two or three CTAs share an SM
+static int pick_tile_rows(int requested, int np, int esize)
+{
+    const size_t budget = esize == 4 ? 76 * 1024 : 112 * 1024;
+    for (int tq : kTileRows) {
+        if (requested > 0 && tq > requested) continue;
+        if (requested > 0 || sweep_smem(tq, np, esize) <= budget) return tq;
+    }
+    return 1;
+}
+
+template <typename T>
 static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a)
 {
-    auto kern = rts::sweep_kernel<T, PPT>;
+    SweepFn<T> kern = sweep_fn<T>(h->tq);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(h->grid);
-    cfg.blockDim = dim3(rts::SWEEP_NT);
+    cfg.blockDim = dim3(h->nt);
     cfg.dynamicSmemBytes = h->smem;
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
@@ -170,33 +210,13 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a)
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <typename T, int PPT>
+template <typename T>
 static cudaError_t occupancy(rts_handle *h, int *blocks)
 {
-    auto kern = rts::sweep_kernel<T, PPT>;
+    SweepFn<T> kern = sweep_fn<T>(h->tq);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, rts::SWEEP_NT, h->smem);
-}
-
-template <typename T>
-static cudaError_t dispatch_occupancy(rts_handle *h, int *blocks)
-{
-    switch (h->ppt) {
-    case 2: return occupancy<T, 2>(h, blocks);
-    case 4: return occupancy<T, 4>(h, blocks);
-    default: return occupancy<T, 8>(h, blocks);
-    }
-}
-
-template <typename T>
-static cudaError_t dispatch_sweep(rts_handle *h, const rts::SweepArgs<T> &a)
-{
-    switch (h->ppt) {
-    case 2: return launch_sweep<T, 2>(h, a);
-    case 4: return launch_sweep<T, 4>(h, a);
-    default: return launch_sweep<T, 8>(h, a);
-    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, h->nt, h->smem);
 }
 
 extern "C" {
@@ -312,13 +332,10 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         npmax = std::max(npmax, NP);
     }
     if (npmax > 1024) return bail(fail(h, RTS_EINVAL, "plane extent %d > 1024 is not supported", npmax));
-    int tq = o.tile_rows > 0 ? o.tile_rows : std::max(1, 1024 / npmax);
-    while (tq > 1 && (long long)tq * npmax > 8 * rts::SWEEP_NT) --tq;
+    const int tq = pick_tile_rows(o.tile_rows, npmax, h->esize);
     h->tq = tq;
-    const int npts_max = tq * npmax;
-    h->ppt = npts_max <= 2 * rts::SWEEP_NT ? 2 : (npts_max <= 4 * rts::SWEEP_NT ? 4 : 8);
-    const int RW = tq + 2;
-    h->smem = (size_t)(rts::MAXD + 2) * RW * npmax * h->esize + (size_t)rts::MAXD * RW * npmax * sizeof(float);
+    h->nt = 32 * ((npmax + 31) / 32);
+    h->smem = sweep_smem(tq, npmax, h->esize);
     if (h->smem > 227 * 1024) return bail(fail(h, RTS_EINVAL, "tile of %d rows needs %zu B shared memory", tq, h->smem));
 
     long long halo_elems = 0;
@@ -337,7 +354,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
             else if (k.axis == 1) { U.sQ = nx * ny; U.sM = nx; U.transposed = 0; U.qper = 0; U.wrap = 1; }
             else { U.sQ = ny; U.sM = nz * ny; U.transposed = 1; U.qper = 0; U.wrap = 1; h->has_x = true; }
             U.nd = (int)chunks[c].size();
-            U.TQ = std::min(tq, U.NQ);
+            U.TQ = tq;
             U.ntiles = (U.NQ + U.TQ - 1) / U.TQ;
             U.tile0 = tile0;
             U.nx = (int)nx;
@@ -355,7 +372,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
                 U.up[i] = G.up;
                 U.udx[i] = udx[d];
             }
-            halo_elems += (long long)U.ntiles * 8 * rts::MAXD * U.NP;
+            halo_elems += (long long)U.ntiles * 4 * rts::HALO_CH * U.NP;
             for (int t = 0; t < U.ntiles; ++t) h->unit_of_tile.push_back((int)h->units.size());
             tile0 += U.ntiles;
             h->max_ntiles = std::max(h->max_ntiles, U.ntiles);
@@ -371,7 +388,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     int dev = 0, nsm = 0, blocks = 0;
     CUDA_TRY(h, cudaGetDevice(&dev));
     CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    cudaError_t oe = o.prec == RTS_FP64 ? dispatch_occupancy<double>(h, &blocks) : dispatch_occupancy<float>(h, &blocks);
+    cudaError_t oe = o.prec == RTS_FP64 ? occupancy<double>(h, &blocks) : occupancy<float>(h, &blocks);
     if (oe != cudaSuccess) return bail(fail(h, RTS_ECUDA, "occupancy query: %s", cudaGetErrorString(oe)));
     h->grid = std::min(h->total_tiles, blocks * nsm);
     if (blocks < 1 || h->grid < h->max_ntiles)
@@ -391,7 +408,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_JF = take((size_t)nbands * 4 * h->N * accsz);
     const size_t o_halo = take((size_t)halo_elems * es);
     const size_t o_flags = take(sizeof(int) * h->total_tiles);
-    const size_t o_gsync = take(sizeof(unsigned long long) * (size_t)h->total_tiles * R);
+    const size_t o_gcnt = take(sizeof(unsigned int) * h->units.size() * R);
+    const size_t o_gmax = take(sizeof(unsigned long long) * h->units.size() * R);
     const size_t o_ticket = take(sizeof(int) * 4);
     const size_t o_status = take(sizeof(int) * 4);
     const size_t o_tacc = take(sizeof(int) * h->units.size());
@@ -421,7 +439,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->d_JF = base + o_JF;
     h->d_halo = base + o_halo;
     h->d_flags = (int *)(base + o_flags);
-    h->d_gsync = (unsigned long long *)(base + o_gsync);
+    h->d_gcnt = (unsigned int *)(base + o_gcnt);
+    h->d_gmax = (unsigned long long *)(base + o_gmax);
     h->d_ticket = (int *)(base + o_ticket);
     h->d_status = (int *)(base + o_status);
     h->d_unit_tacc = (int *)(base + o_tacc);
@@ -466,7 +485,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->total_tiles, st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_gsync, 0, sizeof(unsigned long long) * (size_t)h->total_tiles * h->R, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
     cudaEvent_t *ev = nullptr;
     if (h->timing) {
@@ -506,7 +526,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     a.ticket = h->d_ticket;
     a.flags = h->d_flags;
     a.halo = (T *)h->d_halo;
-    a.gsync = h->d_gsync;
+    a.gcnt = h->d_gcnt;
+    a.gmax = h->d_gmax;
     a.R = h->R;
     a.L = kLag;
     a.status = h->d_status;
@@ -514,7 +535,7 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     a.tol = (float)h->opt.wrap_tol;
     a.max_periods = h->opt.max_wrap_iters;
     a.timeout_ns = (unsigned long long)(h->opt.timeout_s * 1e9);
-    cudaError_t e = dispatch_sweep<T>(h, a);
+    cudaError_t e = launch_sweep<T>(h, a);
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     kernels += 1;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
@@ -733,11 +754,10 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
         noalloc_msg(err, errlen, "plane extent %d > 1024 is not supported", npmax);
         return RTS_EINVAL;
     }
-    int tq = std::max(1, 1024 / npmax);
-    const int npts_max = tq * npmax;
-    const int ppt = npts_max <= 2 * rts::SWEEP_NT ? 2 : (npts_max <= 4 * rts::SWEEP_NT ? 4 : 8);
     const size_t es = sizeof(T);
-    const size_t smem = (size_t)(rts::MAXD + 2) * (tq + 2) * npmax * es + (size_t)rts::MAXD * (tq + 2) * npmax * 4;
+    const int tq = pick_tile_rows(0, npmax, (int)es);
+    const int nt = 32 * ((npmax + 31) / 32);
+    const size_t smem = sweep_smem(tq, npmax, (int)es);
 
     rts::SweepUnit units[kNoallocMaxUnits];
     int unit_of_tile[kNoallocMaxTiles];
@@ -763,7 +783,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
                 else if (U.axis == 1) { U.NP = (int)nx; U.NQ = (int)nz; U.NM = (int)ny; U.sQ = nx * ny; U.sM = nx; U.wrap = 1; }
                 else { U.NP = (int)ny; U.NQ = (int)nz; U.NM = (int)nx; U.sQ = ny; U.sM = nz * ny; U.wrap = 1; U.transposed = 1; has_x = true; }
                 U.nd = std::min(rts::MAXD, nd - c0);
-                U.TQ = std::min(tq, U.NQ);
+                U.TQ = tq;
                 U.ntiles = (U.NQ + U.TQ - 1) / U.TQ;
                 U.tile0 = ntile;
                 U.nx = (int)nx;
@@ -787,7 +807,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
                 for (int t = 0; t < U.ntiles; ++t) unit_of_tile[ntile + t] = nunits;
                 ntile += U.ntiles;
                 maxnt = std::max(maxnt, U.ntiles);
-                halo_elems += (long long)U.ntiles * 8 * rts::MAXD * U.NP;
+                halo_elems += (long long)U.ntiles * 4 * rts::HALO_CH * U.NP;
                 rub[b + 1]++;
                 ++nunits;
             }
@@ -805,7 +825,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     const size_t o_ru = take(sizeof(rts::RedUnit) * nunits);
     const size_t o_rub = take(sizeof(int) * (B + 1));
     const size_t o_flags = take(sizeof(int) * ntile);
-    const size_t o_gsync = take(sizeof(unsigned long long) * (size_t)ntile * R);
+    const size_t o_gcnt = take(sizeof(unsigned int) * nunits * R);
+    const size_t o_gmax = take(sizeof(unsigned long long) * nunits * R);
     const size_t o_ctl = take(sizeof(int) * 8);  // ticket, status
     const size_t o_tacc = take(sizeof(int) * nunits);
     const size_t o_halo = take((size_t)halo_elems * es);
@@ -825,7 +846,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     }
 
     // residency of the persistent launch
-    auto kern = ppt == 2 ? rts::sweep_kernel<T, 2> : (ppt == 4 ? rts::sweep_kernel<T, 4> : rts::sweep_kernel<T, 8>);
+    SweepFn<T> kern = sweep_fn<T>(tq);
     int nsm = 0, blocks = 0;
 #define NA_TRY(call)                                                                              \
     do {                                                                                          \
@@ -837,7 +858,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     } while (0)
     NA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     NA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    NA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, rts::SWEEP_NT, smem));
+    NA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, nt, smem));
     const int grid = std::min(ntile, blocks * nsm);
     if (blocks < 1 || grid < maxnt) {
         noalloc_msg(err, errlen, "a sweep unit has %d tiles but only %d CTAs fit", maxnt, blocks * nsm);
@@ -850,7 +871,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     NA_TRY(cudaMemcpyAsync(base + o_ru, ru, sizeof(rts::RedUnit) * nunits, cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemcpyAsync(base + o_rub, rub, sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemsetAsync(base + o_flags, 0, sizeof(int) * ntile, st));
-    NA_TRY(cudaMemsetAsync(base + o_gsync, 0, sizeof(unsigned long long) * (size_t)ntile * R, st));
+    NA_TRY(cudaMemsetAsync(base + o_gcnt, 0, sizeof(unsigned int) * nunits * R, st));
+    NA_TRY(cudaMemsetAsync(base + o_gmax, 0, sizeof(unsigned long long) * nunits * R, st));
     NA_TRY(cudaMemsetAsync(base + o_ctl, 0, sizeof(int) * 8, st));
     NA_TRY(cudaMemsetAsync(base + o_tacc, 0, sizeof(int) * nunits, st));
 
@@ -878,7 +900,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     a.status = (int *)(base + o_ctl) + 4;
     a.flags = (int *)(base + o_flags);
     a.halo = (T *)(base + o_halo);
-    a.gsync = (unsigned long long *)(base + o_gsync);
+    a.gcnt = (unsigned int *)(base + o_gcnt);
+    a.gmax = (unsigned long long *)(base + o_gmax);
     a.R = R;
     a.L = kLag;
     a.unit_tacc = (int *)(base + o_tacc);
@@ -887,7 +910,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     a.timeout_ns = 2000000000ull;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(rts::SWEEP_NT);
+    cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
