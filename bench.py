@@ -40,6 +40,7 @@ WORKLOAD = "rts288x4"
 NX = NY = NZ = 288
 NB = 4
 NDIR = 24
+TILE_ROWS = None
 
 
 def _peaks():
@@ -59,6 +60,7 @@ def _config(prec):
         "q_step": {"fp32": "FP64", "fp32_compensated": "double-float (2xFP32)", "fp64": "FP64"}[prec],
         "l2": "inputs (764 MB chi+S FP32) larger than the 126 MB L2; no flush between steps",
         "step": "one rts_solve over all 4 bands and 24 rays",
+        "tile_rows": TILE_ROWS,
     }
 
 
@@ -213,7 +215,7 @@ def run_ours(args):
         return float(t.item())
 
     stream = torch.cuda.current_stream()
-    s = rts.Solver(NX, NY, NZ, NB, precision=prec, timing=True, stream=stream)
+    s = rts.Solver(NX, NY, NZ, NB, precision=prec, timing=True, stream=stream, tile_rows=args.tile_rows)
     chi = torch.as_tensor(chi64, dtype=s.dtype, device=dev)
     S = torch.as_tensor(S64, dtype=s.dtype, device=dev)
     out = s.solve(chi, S)
@@ -236,6 +238,8 @@ def run_ours(args):
     ms = max_over_ranks(ms)
     s.check()
     st = s.stats()
+    global TILE_ROWS
+    TILE_ROWS = st["tile_rows"]
     value = ws * upd / (ms * 1e-3) / 1e9
 
     peaks = _peaks()
@@ -395,6 +399,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--precision", choices=("fp32", "fp32_compensated", "fp64"), default="fp32")
+    ap.add_argument("--tile-rows", type=int, default=0, help="rows per sweep tile (0 = library default)")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")

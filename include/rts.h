@@ -93,7 +93,7 @@ typedef struct {
     double tau_switch;    /* thin/thick blend constant (default 0.1) */
     double wrap_tol;      /* bound on the remaining seed error of the periodic
                              wrap, relative to the seed error (default 1e-15
-                             for FP64, 1e-9 for FP32) */
+                             for FP64, 2^-24 for FP32) */
     int max_wrap_iters;   /* cap on the wrap warm-up, in periods (default 64) */
     int tile_rows;        /* rows of a sweep tile (0 = automatic) */
     int threads;          /* threads per CTA of the sweep (0 = automatic) */

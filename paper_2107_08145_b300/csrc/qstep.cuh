@@ -43,36 +43,75 @@ struct RedUnit {
     int axis;             // 0: transposed layout [i][k][j]; else natural
 };
 
-template <typename T, typename Acc>
-__device__ __forceinline__ Acc acc_addT(Acc a, T v);
+// Sums of sweep-unit partials. FP32 partials are summed in double-float
+// arithmetic (error-free TwoSum), which for a handful of terms is exact to
+// ~2^-48 relative; the FP64 form of that sum is then taken once. This keeps
+// the FP64 pipe (a small fraction of the FP32 rate on B300) out of the loop.
+template <typename T>
+struct PartSum;
 template <>
-__device__ __forceinline__ double acc_addT<double, double>(double a, double v) { return a + v; }
+struct PartSum<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ double as_double() const { return v; }
+    __device__ __forceinline__ df32 as_df32() const { return {(float)v, (float)(v - (double)(float)v)}; }
+};
 template <>
-__device__ __forceinline__ double acc_addT<float, double>(double a, float v) { return a + (double)v; }
-template <>
-__device__ __forceinline__ df32 acc_addT<float, df32>(df32 a, float v) { return df_add(a, v); }
+struct PartSum<float> {
+    df32 v = {0.f, 0.f};
+    __device__ __forceinline__ void add(float x) { v = df_add(v, x); }
+    __device__ __forceinline__ void add(df32 x) { v = df_add(v, x); }
+    __device__ __forceinline__ double as_double() const { return df_to_double(v); }
+    __device__ __forceinline__ df32 as_df32() const { return v; }
+};
+__device__ __forceinline__ double part_out(const PartSum<double> &s, double *) { return s.as_double(); }
+__device__ __forceinline__ double part_out(const PartSum<float> &s, double *) { return s.as_double(); }
+__device__ __forceinline__ df32 part_out(const PartSum<float> &s, df32 *) { return s.as_df32(); }
 
-// JF[b][c][N] (c = J, Fx, Fy, Fz) from the band's sweep-unit partials.
+// JF[b][c][N] (c = J, Fx, Fy, Fz) from the band's sweep-unit partials. A CTA
+// covers a 32 x 32 (i, j) tile of one level k of one band. Units in natural
+// layout are read along i; units of the x groups, stored [i][k][j], are read
+// along j into a shared tile and summed transposed, so every global read is
+// coalesced.
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) reduce_units_kernel(const RedUnit *__restrict__ ru,
                                                             const int *__restrict__ ru_begin,
                                                             Acc *__restrict__ JF, int nx, int ny, int nz)
 {
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
+    __shared__ PartSum<T> tile[4][32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
     const int b = blockIdx.z / nz, k = blockIdx.z % nz;
-    if (i >= nx || j >= ny) return;
     const long long N = (long long)nx * ny * nz;
-    const long long noff = ((long long)k * ny + j) * nx + i;
-    const long long toff = ((long long)i * nz + k) * ny + j;
-    Acc s[4];
-    for (int c = 0; c < 4; ++c) s[c] = acc_zero((Acc *)nullptr);
-    for (int u = ru_begin[b]; u < ru_begin[b + 1]; ++u) {
-        const T *p = (const T *)ru[u].partial;
-        const long long off = ru[u].axis == 0 ? toff : noff;
-        for (int c = 0; c < 4; ++c) s[c] = acc_addT<T, Acc>(s[c], p[c * N + off]);
+    const int u0 = ru_begin[b], u1 = ru_begin[b + 1];
+    // transposed units: tile[c][i - i0][j - j0]
+    for (int c = 0; c < 4; ++c)
+        for (int jj = ty; jj < 32; jj += 8) tile[c][jj][tx] = PartSum<T>();
+    __syncthreads();
+    for (int u = u0; u < u1; ++u) {
+        if (ru[u].axis != 0) continue;
+        const T *pt = (const T *)ru[u].partial;
+        for (int ii = ty; ii < 32; ii += 8) {
+            const int i = i0 + ii, j = j0 + tx;
+            if (i >= nx || j >= ny) continue;
+            const long long off = ((long long)i * nz + k) * ny + j;
+            for (int c = 0; c < 4; ++c) tile[c][ii][tx].add(pt[c * N + off]);
+        }
     }
-    for (int c = 0; c < 4; ++c) JF[((long long)b * 4 + c) * N + noff] = s[c];
+    __syncthreads();
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int i = i0 + tx, j = j0 + jj;
+        if (i >= nx || j >= ny) continue;
+        const long long noff = ((long long)k * ny + j) * nx + i;
+        PartSum<T> s[4];
+        for (int c = 0; c < 4; ++c) s[c] = tile[c][tx][jj];
+        for (int u = u0; u < u1; ++u) {
+            if (ru[u].axis == 0) continue;
+            const T *pn = (const T *)ru[u].partial;
+            for (int c = 0; c < 4; ++c) s[c].add(pn[c * N + noff]);
+        }
+        for (int c = 0; c < 4; ++c) JF[((long long)b * 4 + c) * N + noff] = part_out(s[c], (Acc *)nullptr);
+    }
 }
 
 struct QParams {

@@ -28,7 +28,7 @@
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kLag = 2;  // planes between posting the seed-error bound and using it
+constexpr int kLag = 8;  // planes between posting the seed-error bound and using it
 
 struct DirGeo {
     int axis, sa, b1, b2, s1, s2, up;
@@ -94,6 +94,86 @@ void default_quadrature(std::vector<double> &n, std::vector<double> &w)
 }
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// extents of a group's plane (P, Q) and sweep axis (M)
+void unit_extents(int axis, long long nx, long long ny, long long nz, int &NP, int &NQ, int &NM)
+{
+    if (axis == 2) { NP = (int)nx; NQ = (int)ny; NM = (int)nz; }
+    else if (axis == 1) { NP = (int)nx; NQ = (int)nz; NM = (int)ny; }
+    else { NP = (int)ny; NQ = (int)nz; NM = (int)nx; }
+}
+
+struct PlanOut {
+    int nunits = 0, ntiles = 0, max_ntiles = 0;
+    long long halo_elems = 0;
+    bool has_x = false;
+};
+
+// Sweep units of B bands. Per band and per (dominant axis, sign) group --
+// the x and y groups first, as their periodic warm-up makes them run longer --
+// the group's rays are bucketed by sign slot (sign along P, sign along Q);
+// unit u of the group takes the u-th ray of every slot. Writes at most
+// max_units units and max_tiles tile -> unit entries (fixed arrays, no
+// allocation); returns false if either would overflow.
+bool plan_units(const DirGeo *geo, const int *udx, const double *n, const double *w, int ndir, long long nx,
+                long long ny, long long nz, int B, int tq, rts::SweepUnit *units, int max_units, int *unit_of_tile,
+                int max_tiles, PlanOut &po)
+{
+    const int keys[6][2] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}, {2, 1}, {2, -1}};
+    const long long N = nx * ny * nz;
+    po = PlanOut();
+    for (int b = 0; b < B; ++b) {
+        for (const auto &k : keys) {
+            // rays of this group by slot, in table order
+            int cnt[rts::MAXD] = {0, 0, 0, 0}, nunit = 0;
+            for (int d = 0; d < ndir; ++d) {
+                if (geo[d].axis != k[0] || geo[d].sa != k[1]) continue;
+                const int sl = (geo[d].s1 < 0 ? 1 : 0) + (geo[d].s2 < 0 ? 2 : 0);
+                nunit = std::max(nunit, ++cnt[sl]);
+            }
+            for (int u = 0; u < nunit; ++u) {
+                if (po.nunits >= max_units) return false;
+                rts::SweepUnit &U = units[po.nunits];
+                std::memset(&U, 0, sizeof(U));
+                U.N = N;
+                U.band = b;
+                U.axis = k[0];
+                U.sa = k[1];
+                unit_extents(U.axis, nx, ny, nz, U.NP, U.NQ, U.NM);
+                if (U.axis == 2) { U.sQ = nx; U.sM = nx * ny; U.qper = 1; }
+                else if (U.axis == 1) { U.sQ = nx * ny; U.sM = nx; U.wrap = 1; }
+                else { U.sQ = ny; U.sM = nz * ny; U.wrap = 1; U.transposed = 1; po.has_x = true; }
+                U.TQ = tq;
+                U.ntiles = (U.NQ + tq - 1) / tq;
+                U.tile0 = po.ntiles;
+                U.nx = (int)nx;
+                U.ny = (int)ny;
+                U.halo_off = po.halo_elems;
+                int seen[rts::MAXD] = {0, 0, 0, 0};
+                for (int sl = 0; sl < rts::MAXD; ++sl) U.up[sl] = U.axis == 2 ? (U.sa > 0) : (sl < 2);
+                for (int d = 0; d < ndir; ++d) {
+                    if (geo[d].axis != k[0] || geo[d].sa != k[1]) continue;
+                    const int sl = (geo[d].s1 < 0 ? 1 : 0) + (geo[d].s2 < 0 ? 2 : 0);
+                    if (seen[sl]++ != u) continue;
+                    U.active[sl] = 1;
+                    for (int cc = 0; cc < 4; ++cc) U.beta[sl][cc] = geo[d].beta[cc];
+                    U.ds[sl] = geo[d].ds;
+                    U.cJ[sl] = w[d];
+                    for (int cc = 0; cc < 3; ++cc) U.cF[cc][sl] = 4.0 * kPi * w[d] * n[3 * d + cc];
+                    U.up[sl] = geo[d].up;
+                    U.udx[sl] = udx[d];
+                }
+                if (po.ntiles + U.ntiles > max_tiles) return false;
+                for (int t = 0; t < U.ntiles; ++t) unit_of_tile[po.ntiles + t] = po.nunits;
+                po.ntiles += U.ntiles;
+                po.max_ntiles = std::max(po.max_ntiles, U.ntiles);
+                po.halo_elems += (long long)U.ntiles * 4 * rts::HALO_CH * U.NP;
+                ++po.nunits;
+            }
+        }
+    }
+    return true;
+}
 
 }  // namespace
 
@@ -164,18 +244,18 @@ static SweepFn<T> sweep_fn(int tq)
     case 2: return rts::sweep_kernel<T, 2>;
     case 3: return rts::sweep_kernel<T, 3>;
     case 4: return rts::sweep_kernel<T, 4>;
-    case 6: return rts::sweep_kernel<T, 6>;
-    default: return rts::sweep_kernel<T, 8>;
+    default: return rts::sweep_kernel<T, 4>;
     }
 }
 
-static const int kTileRows[6] = {8, 6, 4, 3, 2, 1};
+static const int kTileRows[4] = {4, 3, 2, 1};
 
-// shared memory of one sweep CTA: I (4 rays) + chi/S ring (2 slots x 2) in
-// the sweep precision, seed-error bounds (2) in FP32, each (tq+2) x np
+// shared memory of one sweep CTA: per plane parity I of 4 slots and the two
+// seed-error bounds, per chi/S slot (3) chi and S: 18 fields of (tq+2) rows x
+// (np+2) columns in the sweep precision
 static size_t sweep_smem(int tq, int np, int esize)
 {
-    return (size_t)(rts::MAXD + 4) * (tq + 2) * np * esize + (size_t)2 * (tq + 2) * np * sizeof(float);
+    return (size_t)rts::NFIELD * (tq + 2) * (np + 2) * esize;
 }
 
 // rows per tile: the option if given (rounded down to an instantiated size),
@@ -183,7 +263,7 @@ static size_t sweep_smem(int tq, int np, int esize)
 // shared memory so that two or three CTAs share an SM
 static int pick_tile_rows(int requested, int np, int esize)
 {
-    const size_t budget = esize == 4 ? 76 * 1024 : 112 * 1024;
+    const size_t budget = esize == 4 ? 110 * 1024 : 112 * 1024;
     for (int tq : kTileRows) {
         if (requested > 0 && tq > requested) continue;
         if (requested > 0 || sweep_smem(tq, np, esize) <= budget) return tq;
@@ -278,7 +358,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     if (!(o.tau_switch > 0)) return bail(fail(h, RTS_EINVAL, "tau_switch must be > 0"));
     if (o.max_wrap_iters < 1) o.max_wrap_iters = 64;
     if (!(o.timeout_s > 0)) o.timeout_s = 2.0;
-    if (!(o.wrap_tol > 0)) o.wrap_tol = o.prec == RTS_FP64 ? 1e-15 : 1e-9;
+    if (!(o.wrap_tol > 0)) o.wrap_tol = o.prec == RTS_FP64 ? 1e-15 : 0x1p-24;
     h->g = *g;
     h->B = nbands;
     h->stream = (cudaStream_t)o.stream;
@@ -304,31 +384,11 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const long long nx = g->nx, ny = g->ny, nz = g->nz;
     h->N = nx * ny * nz;
 
-    // ---- sweep units: band x (axis, sign) group, chunks of up to 4 directions ----
-    struct GroupKey { int axis, sa; };
-    // wrap groups (x, y) first: they run longer (warm-up), then z
-    const GroupKey keys[6] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}, {2, 1}, {2, -1}};
-    std::vector<std::vector<int>> chunks;
-    std::vector<GroupKey> chunk_key;
-    for (const GroupKey &k : keys) {
-        std::vector<int> ds;
-        for (int d = 0; d < h->ndir; ++d)
-            if (geo[d].axis == k.axis && geo[d].sa == k.sa) ds.push_back(d);
-        for (size_t c = 0; c < ds.size(); c += rts::MAXD) {
-            chunks.emplace_back(ds.begin() + c, ds.begin() + std::min(ds.size(), c + rts::MAXD));
-            chunk_key.push_back(k);
-        }
-    }
-    // tiling: TQ rows x the full periodic P extent per CTA
-    auto extents = [&](int axis, int &NP, int &NQ, int &NM) {
-        if (axis == 2) { NP = (int)nx; NQ = (int)ny; NM = (int)nz; }
-        else if (axis == 1) { NP = (int)nx; NQ = (int)nz; NM = (int)ny; }
-        else { NP = (int)ny; NQ = (int)nz; NM = (int)nx; }
-    };
+    // ---- sweep units and tiling ----
     int npmax = 0;
-    for (const GroupKey &k : chunk_key) {
+    for (int d = 0; d < h->ndir; ++d) {
         int NP, NQ, NM;
-        extents(k.axis, NP, NQ, NM);
+        unit_extents(geo[d].axis, nx, ny, nz, NP, NQ, NM);
         npmax = std::max(npmax, NP);
     }
     if (npmax > 1024) return bail(fail(h, RTS_EINVAL, "plane extent %d > 1024 is not supported", npmax));
@@ -337,48 +397,20 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->nt = 32 * ((npmax + 31) / 32);
     h->smem = sweep_smem(tq, npmax, h->esize);
     if (h->smem > 227 * 1024) return bail(fail(h, RTS_EINVAL, "tile of %d rows needs %zu B shared memory", tq, h->smem));
-
-    long long halo_elems = 0;
-    int tile0 = 0;
-    for (int b = 0; b < nbands; ++b) {
-        for (size_t c = 0; c < chunks.size(); ++c) {
-            const GroupKey k = chunk_key[c];
-            rts::SweepUnit U;
-            std::memset(&U, 0, sizeof(U));
-            U.N = h->N;
-            U.band = b;
-            U.axis = k.axis;
-            U.sa = k.sa;
-            extents(k.axis, U.NP, U.NQ, U.NM);
-            if (k.axis == 2) { U.sQ = nx; U.sM = nx * ny; U.transposed = 0; U.qper = 1; U.wrap = 0; }
-            else if (k.axis == 1) { U.sQ = nx * ny; U.sM = nx; U.transposed = 0; U.qper = 0; U.wrap = 1; }
-            else { U.sQ = ny; U.sM = nz * ny; U.transposed = 1; U.qper = 0; U.wrap = 1; h->has_x = true; }
-            U.nd = (int)chunks[c].size();
-            U.TQ = tq;
-            U.ntiles = (U.NQ + U.TQ - 1) / U.TQ;
-            U.tile0 = tile0;
-            U.nx = (int)nx;
-            U.ny = (int)ny;
-            U.halo_off = halo_elems;
-            for (int i = 0; i < U.nd; ++i) {
-                const int d = chunks[c][i];
-                const DirGeo &G = geo[d];
-                for (int cc = 0; cc < 4; ++cc) U.beta[i][cc] = G.beta[cc];
-                U.ds[i] = G.ds;
-                U.cJ[i] = h->w[d];
-                for (int cc = 0; cc < 3; ++cc) U.cF[cc][i] = 4.0 * kPi * h->w[d] * h->n[3 * d + cc];
-                U.sP[i] = G.s1;
-                U.sQd[i] = G.s2;
-                U.up[i] = G.up;
-                U.udx[i] = udx[d];
-            }
-            halo_elems += (long long)U.ntiles * 4 * rts::HALO_CH * U.NP;
-            for (int t = 0; t < U.ntiles; ++t) h->unit_of_tile.push_back((int)h->units.size());
-            tile0 += U.ntiles;
-            h->max_ntiles = std::max(h->max_ntiles, U.ntiles);
-            h->units.push_back(U);
-        }
-    }
+    const int max_units = nbands * 6 * h->ndir;
+    const long long max_tiles = (long long)max_units * ((std::max(nx, std::max(ny, nz)) + tq - 1) / tq);
+    h->units.resize(max_units);
+    h->unit_of_tile.resize(max_tiles);
+    PlanOut po;
+    if (!plan_units(geo.data(), udx.data(), h->n.data(), h->w.data(), h->ndir, nx, ny, nz, nbands, tq,
+                    h->units.data(), max_units, h->unit_of_tile.data(), (int)max_tiles, po))
+        return bail(fail(h, RTS_EINVAL, "too many sweep units or tiles"));
+    h->units.resize(po.nunits);
+    h->unit_of_tile.resize(po.ntiles);
+    h->has_x = po.has_x;
+    h->max_ntiles = po.max_ntiles;
+    const long long halo_elems = po.halo_elems;
+    const int tile0 = po.ntiles;
     h->total_tiles = tile0;
     int R = 8;
     while (R < 2 * (h->max_ntiles + kLag + 2)) R *= 2;
@@ -540,7 +572,7 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     kernels += 1;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
     if (J || F || Q) {
-        dim3 rb(32, 8), rg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)(g.nz * B));
+        dim3 rb(32, 8), rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
         rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
         if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
         rts::QParams P;
@@ -763,56 +795,16 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     int unit_of_tile[kNoallocMaxTiles];
     rts::RedUnit ru[kNoallocMaxUnits];
     int rub[17] = {0};
-    const int keys[6][2] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}, {2, 1}, {2, -1}};
-    int nunits = 0, ntile = 0, maxnt = 0;
-    long long halo_elems = 0;
-    bool has_x = false;
-    for (int b = 0; b < B; ++b) {
-        for (const auto &k : keys) {
-            int ds[24], nd = 0;
-            for (int d = 0; d < 24; ++d)
-                if (geo[d].axis == k[0] && geo[d].sa == k[1]) ds[nd++] = d;
-            for (int c0 = 0; c0 < nd; c0 += rts::MAXD) {
-                rts::SweepUnit &U = units[nunits];
-                std::memset(&U, 0, sizeof(U));
-                U.N = N;
-                U.band = b;
-                U.axis = k[0];
-                U.sa = k[1];
-                if (U.axis == 2) { U.NP = (int)nx; U.NQ = (int)ny; U.NM = (int)nz; U.sQ = nx; U.sM = nx * ny; U.qper = 1; }
-                else if (U.axis == 1) { U.NP = (int)nx; U.NQ = (int)nz; U.NM = (int)ny; U.sQ = nx * ny; U.sM = nx; U.wrap = 1; }
-                else { U.NP = (int)ny; U.NQ = (int)nz; U.NM = (int)nx; U.sQ = ny; U.sM = nz * ny; U.wrap = 1; U.transposed = 1; has_x = true; }
-                U.nd = std::min(rts::MAXD, nd - c0);
-                U.TQ = tq;
-                U.ntiles = (U.NQ + U.TQ - 1) / U.TQ;
-                U.tile0 = ntile;
-                U.nx = (int)nx;
-                U.ny = (int)ny;
-                U.halo_off = halo_elems;
-                for (int i = 0; i < U.nd; ++i) {
-                    const int d = ds[c0 + i];
-                    for (int c = 0; c < 4; ++c) U.beta[i][c] = geo[d].beta[c];
-                    U.ds[i] = geo[d].ds;
-                    U.cJ[i] = w[d];
-                    for (int c = 0; c < 3; ++c) U.cF[c][i] = 4.0 * kPi * w[d] * n[3 * d + c];
-                    U.sP[i] = geo[d].s1;
-                    U.sQd[i] = geo[d].s2;
-                    U.up[i] = geo[d].up;
-                    U.udx[i] = udx[d];
-                }
-                if (ntile + U.ntiles > kNoallocMaxTiles) {
-                    noalloc_msg(err, errlen, "more than %d sweep tiles", kNoallocMaxTiles);
-                    return RTS_EINVAL;
-                }
-                for (int t = 0; t < U.ntiles; ++t) unit_of_tile[ntile + t] = nunits;
-                ntile += U.ntiles;
-                maxnt = std::max(maxnt, U.ntiles);
-                halo_elems += (long long)U.ntiles * 4 * rts::HALO_CH * U.NP;
-                rub[b + 1]++;
-                ++nunits;
-            }
-        }
+    PlanOut po;
+    if (!plan_units(geo, udx, n, w, 24, nx, ny, nz, B, tq, units, kNoallocMaxUnits, unit_of_tile, kNoallocMaxTiles,
+                    po)) {
+        noalloc_msg(err, errlen, "more than %d sweep units or %d tiles", kNoallocMaxUnits, kNoallocMaxTiles);
+        return RTS_EINVAL;
     }
+    const int nunits = po.nunits, ntile = po.ntiles, maxnt = po.max_ntiles;
+    const long long halo_elems = po.halo_elems;
+    const bool has_x = po.has_x;
+    for (int u = 0; u < nunits; ++u) rub[units[u].band + 1]++;
     for (int b = 0; b < B; ++b) rub[b + 1] += rub[b];
     int R = 8;
     while (R < 2 * (maxnt + kLag + 2)) R *= 2;
@@ -905,7 +897,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     a.R = R;
     a.L = kLag;
     a.unit_tacc = (int *)(base + o_tacc);
-    a.tol = sizeof(T) == 8 ? 1e-15f : 1e-9f;
+    a.tol = sizeof(T) == 8 ? 1e-15f : 0x1p-24f;
     a.max_periods = 64;
     a.timeout_ns = 2000000000ull;
     cudaLaunchConfig_t cfg = {};
@@ -920,7 +912,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     cfg.numAttrs = 1;
     NA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
     if (J || F || Q) {
-        dim3 rb(32, 8), rg((g->nx + 31) / 32, (g->ny + 7) / 8, (unsigned)(g->nz * B));
+        dim3 rb(32, 8), rg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)(g->nz * B));
         rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>((const rts::RedUnit *)(base + o_ru),
                                                              (const int *)(base + o_rub), (Acc *)(base + o_JF),
                                                              g->nx, g->ny, g->nz);

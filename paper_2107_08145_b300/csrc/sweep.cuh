@@ -9,9 +9,14 @@
 //    (the wavefront of Sect. 5.1).
 //  * A unit's plane is cut into tiles of TQ rows along Q spanning the whole
 //    (periodic) P extent; thread p of the CTA owns column p of the tile. A
-//    CTA owns one tile for the whole sweep and keeps the previous plane
-//    (I, chi, S and the seed-error bound g) in shared memory; chi and S of the
-//    next plane are prefetched with cp.async into a two-slot ring. Only the
+//    CTA owns one tile for the whole sweep and keeps the previous plane (I
+//    and the seed-error bound g, by plane parity) and three planes of chi
+//    and S (the next one prefetched a whole plane ahead with cp.async) in
+//    shared memory. Each plane: integrate the interior rows; each thread
+//    acquires the neighbours' flags and loads its column of their edge rows
+//    into the halo rows; barrier; integrate the edge rows and write them to
+//    the ring; barrier; release the tile's flag; only then store the
+//    plane's partial sums, so the release never waits for those stores. Only the
 //    first and last row of a tile cross CTAs: they are published to a small
 //    global ring with a release flag per tile, and the neighbouring tiles
 //    wait on that flag (bounded) before their next plane.
@@ -45,21 +50,25 @@ namespace rts {
 constexpr int MAXD = 4;     // directions per sweep unit
 constexpr int HALO_CH = MAXD + 2;  // ring channels: I of each ray, g of up / down rays
 
+// Rays of a unit sit in "sign slots": slot s holds the ray whose components
+// along P and Q have signs sP = (s & 1 ? -1 : +1), sQ = (s & 2 ? -1 : +1), so
+// its upwind corners are the compile-time offsets (0,0), (-sP,0), (0,-sQ),
+// (-sP,-sQ). A slot without a ray is inactive (zero weights, not exported).
 struct SweepUnit {
     void *partial;              // [4][N] J, Fx, Fy, Fz of this unit, unit layout
     long long sQ, sM, N;        // strides of Q and M (elements), points
     long long halo_off;         // element offset of tile 0's halo block
     int band, transposed;       // band index; reads the x-transposed copy
     int NP, NQ, NM;
-    int axis, sa, wrap, qper, nd;
+    int axis, sa, wrap, qper;
     int TQ, ntiles, tile0;
     int nx, ny;
+    int active[MAXD];           // slot holds a ray
+    int up[MAXD], udx[MAXD];    // upward?; index among up (or down) rays
     double beta[MAXD][4];       // bilinear weights of corners (0,0),(1,0),(0,1),(1,1)
     double ds[MAXD];            // path length to the upwind plane
     double cJ[MAXD];            // w_d
     double cF[3][MAXD];         // 4 pi w_d n_d
-    int sP[MAXD], sQd[MAXD];    // corner step along P and Q is -sP, -sQ
-    int up[MAXD], udx[MAXD];    // upward?; index among up (or down) directions
 };
 
 template <typename T>
@@ -137,13 +146,13 @@ __device__ __forceinline__ void natural_ij(int axis, int p, int q, int m, int &i
     else { i = m; j = p; }
 }
 
-// Direction constants of the unit in shared memory.
+// Ray constants of the unit's slots in shared memory.
 template <typename T>
 struct DirConst {
     T beta[MAXD][4];
     T hds[MAXD];           // ds / 2
     T cJ[MAXD], cF[3][MAXD];
-    int sP[MAXD], sQ[MAXD], up[MAXD], bck[MAXD], udx[MAXD];
+    int up[MAXD], bck[MAXD], udx[MAXD], active[MAXD];
 };
 
 template <typename T>
@@ -161,78 +170,120 @@ __device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U,
     return arr[(long long)D.udx[d] * plane + (long long)j * U.nx + i];
 }
 
+// Shared memory of a tile, NPP = NP + 2 columns per row: column c = p + 1,
+// columns 0 and NP+1 repeat p = NP-1 and p = 0 (periodic padding), so a P
+// neighbour is always the next column. Fields per plane parity: I of the 4
+// slots, the up/down seed-error bounds, chi and S; each field RW = TQ+2 rows
+// (halo row, TQ own rows, halo row).
+enum { F_I0 = 0, F_GU = 4, F_GD = 5, NPARF = 6, NXSF = 2, NFIELD = 2 * NPARF + 2 * NXSF };
+
+// I of slot (SP, SQ) at one point from the previous plane: pointers at the
+// point, row stride npp; e = exp(-dtau) for the seed-error bound
+template <typename T, int SP, int SQ>
+__device__ __forceinline__ T slot_update(const T *__restrict__ Ip, const T *__restrict__ Xp,
+                                         const T *__restrict__ Sp, int npp, T b0, T b1, T b2, T b3, T hds,
+                                         T xp, T sp, T &e)
+{
+    const int oq = -SQ * npp;
+    const T Iup = b0 * Ip[0] + b1 * Ip[-SP] + b2 * Ip[oq] + b3 * Ip[oq - SP];
+    const T xup = b0 * Xp[0] + b1 * Xp[-SP] + b2 * Xp[oq] + b3 * Xp[oq - SP];
+    const T sup = b0 * Sp[0] + b1 * Sp[-SP] + b2 * Sp[oq] + b3 * Sp[oq - SP];
+    T wu, wp;
+    seg_weights(hds * (xup + xp), e, wu, wp);
+    return Iup + wu * (sup - Iup) + wp * (sp - Iup);
+}
+
+template <typename T, int SP, int SQ>
+__device__ __forceinline__ float slot_bound(const T *__restrict__ Gp, int npp, T b0, T b1, T b2, T b3, T e)
+{
+    const int oq = -SQ * npp;
+    return (float)(e * (b0 * Gp[0] + b1 * Gp[-SP] + b2 * Gp[oq] + b3 * Gp[oq - SP]));
+}
+
 // One tile of one sweep unit, from its first plane to the last. Thread p
 // owns column p (p < NP) of rows q0 .. q0+nrows-1.
 template <typename T, int TQ>
-__device__ void run_tile(const SweepArgs<T> &a, const SweepUnit &U, int uidx, int r, int gt,
+__device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug, int uidx, int r, int gt,
                          unsigned char *smem)
 {
-    constexpr int RW = TQ + 2;                  // rows in shared memory incl. halo rows
+    constexpr int RW = TQ + 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, NT = blockDim.x;
-    const int NP = U.NP, NQ = U.NQ, NM = U.NM, nd = U.nd;
+    // unit description in registers (the struct lives in global memory)
+    const int NP = Ug->NP, NQ = Ug->NQ, NM = Ug->NM;
+    const int axis = Ug->axis, sa = Ug->sa, ntl = Ug->ntiles, tile0 = Ug->tile0;
+    const bool wrap = Ug->wrap != 0, qper = Ug->qper != 0;
+    const int band = Ug->band, unx = Ug->nx, uny = Ug->ny;
+    const long long sQ = Ug->sQ, sM = Ug->sM, N = Ug->N;
+    const T *__restrict__ chi = (Ug->transposed ? a.chiT : a.chi) + (long long)band * N;
+    const T *__restrict__ Sg = (Ug->transposed ? a.ST : a.S) + (long long)band * N;
+    T *const itop = a.itop ? a.itop + (long long)band * a.n_up * uny * unx : nullptr;
+    T *const part = (T *)Ug->partial;
+    const long long tile_stride = (long long)2 * 2 * HALO_CH * NP;
+    T *const halo_base = a.halo + Ug->halo_off;
+    T *const myhalo = halo_base + (long long)r * tile_stride;
+
     const int q0 = r * TQ;
     const int nrows = min(TQ, NQ - q0);
     const int p = tid;
     const bool act = p < NP;
-    const int pm = p == 0 ? NP - 1 : p - 1;
-    const int pn = p >= NP - 1 ? 0 : p + 1;
-    const T *__restrict__ chi = (U.transposed ? a.chiT : a.chi) + (long long)U.band * U.N;
-    const T *__restrict__ Sg = (U.transposed ? a.ST : a.S) + (long long)U.band * U.N;
-    T *const itop = a.itop ? a.itop + (long long)U.band * a.n_up * U.ny * U.nx : nullptr;
-    T *const part = (T *)U.partial;
+    const int c = p + 1;                        // smem column
+    const int npp = NP + 2;
+    const int FL = RW * npp;                    // one field
+    T *const sm = (T *)smem;
+    auto fI = [&](int par, int f) -> T * { return sm + (par * NPARF + f) * FL; };
+    auto fX = [&](int t) -> T * { return sm + (2 * NPARF + (t & 1) * NXSF) * FL; };
+    auto fS = [&](int t) -> T * { return sm + (2 * NPARF + (t & 1) * NXSF + 1) * FL; };
 
-    const int PL = RW * NP;                     // one smem plane
-    T *sI = (T *)smem;                          // [MAXD][RW][NP] previous plane
-    T *sX = sI + MAXD * PL;                     // [2][RW][NP] chi ring (slot = plane & 1)
-    T *sS = sX + 2 * PL;                        // [2][RW][NP] S ring
-    float *sG = (float *)(sS + 2 * PL);         // [2][RW][NP] seed-error bound (up, down)
     __shared__ DirConst<T> D;
     __shared__ float s_wmax[32];
-    __shared__ int s_ctl[4];                    // 0 abort, 2 decision
+    __shared__ int s_ctl[4];                    // 0 abort, 1 decision for the next plane
+    __shared__ int s_q[RW];                     // global row of smem row k, -1 outside
 
     if (tid < MAXD) {
         const int d = tid;
-        for (int c = 0; c < 4; ++c) D.beta[d][c] = (T)U.beta[d][c];
-        D.hds[d] = (T)(0.5 * U.ds[d]);
-        D.cJ[d] = (T)U.cJ[d];
-        for (int c = 0; c < 3; ++c) D.cF[c][d] = (T)U.cF[c][d];
-        D.sP[d] = U.sP[d];
-        D.sQ[d] = U.sQd[d];
-        D.up[d] = U.up[d];
-        D.bck[d] = U.up[d] ? a.bc_bottom : a.bc_top;
-        D.udx[d] = U.udx[d];
+        for (int cc = 0; cc < 4; ++cc) D.beta[d][cc] = (T)Ug->beta[d][cc];
+        D.hds[d] = (T)(0.5 * Ug->ds[d]);
+        D.cJ[d] = (T)Ug->cJ[d];
+        for (int cc = 0; cc < 3; ++cc) D.cF[cc][d] = (T)Ug->cF[cc][d];
+        D.up[d] = Ug->up[d];
+        D.bck[d] = Ug->up[d] ? a.bc_bottom : a.bc_top;
+        D.udx[d] = Ug->udx[d];
+        D.active[d] = Ug->active[d];
     }
-    if (tid == 0) { s_ctl[0] = 0; s_ctl[2] = 0; }
+    if (tid < RW) {
+        int q = q0 - 1 + tid;
+        if (qper) q = (q % NQ + NQ) % NQ;
+        else if (q < 0 || q >= NQ) q = -1;
+        s_q[tid] = tid <= nrows + 1 ? q : -1;
+    }
+    if (tid == 0) { s_ctl[0] = 0; s_ctl[1] = 0; }
 
-    // global row of smem row k (0 .. nrows+1), or -1 outside a non-periodic Q
-    auto grow = [&](int k) -> int {
-        int q = q0 - 1 + k;
-        if (U.qper) return (q % NQ + NQ) % NQ;
-        return (q >= 0 && q < NQ) ? q : -1;
+    const int t_first = wrap ? 0 : 1;
+    const int lower = qper ? (r + ntl - 1) % ntl : r - 1;
+    const int upper = qper ? (r + 1) % ntl : r + 1;
+    const bool has_lower = qper || r > 0;
+    const bool has_upper = qper || r < ntl - 1;
+
+    // store v at column p + 1 of row k of field f, and its periodic copy
+    auto put = [&](T *f, int k, T v) {
+        f[k * npp + c] = v;
+        if (p == 0) f[k * npp + NP + 1] = v;
+        if (p == NP - 1) f[k * npp] = v;
     };
-    const int t_first = U.wrap ? 0 : 1;
-    const int ntl = U.ntiles;
-    const int lower = U.qper ? (r + ntl - 1) % ntl : r - 1;
-    const int upper = U.qper ? (r + 1) % ntl : r + 1;
-    const bool has_lower = U.qper || r > 0;
-    const bool has_upper = U.qper || r < ntl - 1;
-    const long long tile_stride = (long long)2 * 2 * HALO_CH * NP;
-    T *__restrict__ myhalo = a.halo + U.halo_off + (long long)r * tile_stride;
-
-    // asynchronous copy of the chi/S rows of plane t into ring slot t & 1
+    // asynchronous copy of this thread's column of the chi/S rows of plane t
+    // into slot t & 1
     auto prefetch = [&](int t) {
-        const int m = plane_of(t, NM, U.sa);
-        const long long mo = (long long)m * U.sM;
-        const int slot = t & 1;
         if (act) {
+            const long long mo = (long long)plane_of(t, NM, sa) * sM + p;
+            T *dx = fX(t), *ds = fS(t);
             for (int k = 0; k < nrows + 2; ++k) {
-                const int q = grow(k);
-                T *dx = sX + slot * PL + k * NP + p;
-                T *ds = sS + slot * PL + k * NP + p;
-                if (q < 0) { *dx = T(0); *ds = T(0); continue; }
-                const long long off = mo + (long long)q * U.sQ + p;
-                cp_async(dx, chi + off);
-                cp_async(ds, Sg + off);
+                const int q = s_q[k];
+                if (q < 0) { put(dx, k, T(0)); put(ds, k, T(0)); continue; }
+                const T *gx = chi + mo + (long long)q * sQ, *gs = Sg + mo + (long long)q * sQ;
+                cp_async(dx + k * npp + c, gx);
+                cp_async(ds + k * npp + c, gs);
+                if (p == 0) { cp_async(dx + k * npp + NP + 1, gx); cp_async(ds + k * npp + NP + 1, gs); }
+                if (p == NP - 1) { cp_async(dx + k * npp, gx); cp_async(ds + k * npp, gs); }
             }
         }
         cp_async_commit();
@@ -241,226 +292,241 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit &U, int uidx, in
     __syncthreads();
 
     // ---------------- prologue: the plane before the first integrated one ----
-    {
-        const int tp = t_first - 1;
-        const int m = plane_of(tp, NM, U.sa);
-        const long long mo = (long long)m * U.sM;
-        const int slot = tp & 1;
-        if (act) {
-            for (int k = 0; k < nrows + 2; ++k) {
-                const int q = grow(k);
-                const bool ok = q >= 0;
-                const long long off = mo + (long long)(ok ? q : 0) * U.sQ + p;
-                const T x = ok ? chi[off] : T(0);
-                const T s = ok ? Sg[off] : T(0);
-                sX[slot * PL + k * NP + p] = x;
-                sS[slot * PL + k * NP + p] = s;
-                float gu = 0.f, gd = 0.f;
-                for (int d = 0; d < nd; ++d) {
-                    T v;
-                    const bool bcrow = U.wrap ? ((D.up[d] && q == 0) || (!D.up[d] && q == NQ - 1)) : true;
-                    if (!ok) v = T(0);
-                    else if (bcrow) v = bc_value(a, U, D, d, p, q, m, s);
+    const int tp = t_first - 1;
+    prefetch(t_first);
+    if (act) {
+        const int m = plane_of(tp, NM, sa);
+        const int par = tp & 1;
+        const long long mo = (long long)m * sM + p;
+        for (int k = 0; k < nrows + 2; ++k) {
+            const int q = s_q[k];
+            const bool ok = q >= 0;
+            const long long off = mo + (long long)(ok ? q : 0) * sQ;
+            const T x = ok ? chi[off] : T(0);
+            const T s = ok ? Sg[off] : T(0);
+            put(fX(tp), k, x);
+            put(fS(tp), k, s);
+            T gu = 0, gd = 0;
+            for (int d = 0; d < MAXD; ++d) {
+                T v = T(0);
+                const bool bcrow = wrap ? ((D.up[d] && q == 0) || (!D.up[d] && q == NQ - 1)) : true;
+                if (ok && D.active[d]) {
+                    if (bcrow) v = bc_value(a, *Ug, D, d, p, q, m, s);
                     else {  // seed: I = S, unit seed-error bound
                         v = s;
-                        if (D.up[d]) gu = 1.f; else gd = 1.f;
+                        if (D.up[d]) gu = 1; else gd = 1;
                     }
-                    sI[d * PL + k * NP + p] = v;
                 }
-                sG[k * NP + p] = gu;
-                sG[PL + k * NP + p] = gd;
+                put(fI(par, F_I0 + d), k, v);
             }
+            put(fI(par, F_GU), k, gu);
+            put(fI(par, F_GD), k, gd);
         }
-        __syncthreads();
         // z groups: the boundary plane is the first of the NM accumulated planes
-        if (!U.wrap && act) {
+        if (!wrap) {
             for (int k = 1; k <= nrows; ++k) {
-                const int q = q0 + k - 1;
                 T aJ = 0, aX = 0, aY = 0, aZ = 0;
-                for (int d = 0; d < nd; ++d) {
-                    const T v = sI[d * PL + k * NP + p];
+                for (int d = 0; d < MAXD; ++d) {
+                    const T v = fI(par, F_I0 + d)[k * npp + c];
                     aJ += D.cJ[d] * v; aX += D.cF[0][d] * v; aY += D.cF[1][d] * v; aZ += D.cF[2][d] * v;
                 }
-                const long long off = (long long)m * U.sM + (long long)q * U.sQ + p;
-                part[off] = aJ; part[U.N + off] = aX; part[2 * U.N + off] = aY; part[3 * U.N + off] = aZ;
+                const long long off = (long long)m * sM + (long long)s_q[k] * sQ + p;
+                part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
             }
         }
     }
-    prefetch(t_first);
+    cp_async_wait_all();
+    __syncthreads();
 
-    int t_acc = U.wrap ? -1 : 0;
-    const int warm_cap = a.max_periods * NM;
+    int t_acc = wrap ? -1 : 0;
+    // warm-up cap in planes whose bound was examined (the decision lags by L)
+    const int warm_cap = a.max_periods * NM + a.L;
     const int dec_thread = NT > 32 ? 32 : 0;
 
     for (int t = t_first;; ++t) {
-        const int m = plane_of(t, NM, U.sa);
-        const bool acc_before = t_acc >= 0;  // same in every thread
-        const bool need_decision = !acc_before && t - a.L >= 0;
-        // ---- (A) plane t's chi/S landed; neighbours published plane t-1; wrap decision ----
-        if (tid == 0 && t > t_first) {
-            bool ok = true;
-            if (has_lower) ok = wait_flag_geq(a.flags + U.tile0 + lower, t, a.status, a.timeout_ns);
-            if (ok && has_upper) ok = wait_flag_geq(a.flags + U.tile0 + upper, t, a.status, a.timeout_ns);
-            if (!ok) s_ctl[0] = 1;
+        const int m = plane_of(t, NM, sa);
+        const int cur = t & 1, prv = cur ^ 1;
+        // decision taken during the previous plane
+        if (t_acc < 0 && s_ctl[1]) {
+            t_acc = t;
+            if (r == 0 && tid == 0) a.unit_tacc[uidx] = t;
         }
-        if (tid == dec_thread && need_decision) {
-            const int ts = t - a.L;
+        if (wrap && t_acc < 0 && t >= warm_cap) {
+            if (tid == 0) atomicOr(a.status, ST_NOCONV);
+            return;  // every tile of the unit stops at the same plane; nothing in flight
+        }
+        const bool acc = t_acc >= 0;
+        const bool last = acc && (t - t_acc == NM - 1);
+        cp_async_wait_all();  // this thread's chi/S of plane t (read only by this thread until B1)
+
+        T b[MAXD][4], hds[MAXD];
+#pragma unroll
+        for (int d = 0; d < MAXD; ++d) {
+            hds[d] = D.hds[d];
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) b[d][cc] = D.beta[d][cc];
+        }
+        const T *Xp = fX(t + 1), *Sp = fS(t + 1), *Xc = fX(t), *Sc = fS(t);  // (t+1) & 1 == (t-1) & 1
+        const bool top_plane = axis == 2 && t == NM - 1 && sa > 0;
+        float gmax = 0.f;
+        T ps[TQ][4];  // partial sums of the own rows, stored after the release
+
+        // integrate row k (1..nrows) of plane t from the previous plane
+        auto do_row = [&](int k) {
+            const int q = q0 + k - 1;
+            const int o = k * npp + c;
+            const T xp = Xc[o], sp = Sc[o];
+            T v[MAXD], e[MAXD];
+            v[0] = slot_update<T, 1, 1>(fI(prv, F_I0 + 0) + o, Xp + o, Sp + o, npp, b[0][0], b[0][1], b[0][2], b[0][3], hds[0], xp, sp, e[0]);
+            v[1] = slot_update<T, -1, 1>(fI(prv, F_I0 + 1) + o, Xp + o, Sp + o, npp, b[1][0], b[1][1], b[1][2], b[1][3], hds[1], xp, sp, e[1]);
+            v[2] = slot_update<T, 1, -1>(fI(prv, F_I0 + 2) + o, Xp + o, Sp + o, npp, b[2][0], b[2][1], b[2][2], b[2][3], hds[2], xp, sp, e[2]);
+            v[3] = slot_update<T, -1, -1>(fI(prv, F_I0 + 3) + o, Xp + o, Sp + o, npp, b[3][0], b[3][1], b[3][2], b[3][3], hds[3], xp, sp, e[3]);
+            float gu = 0.f, gd = 0.f;
+            if (!acc) {
+                // seed-error bound of the up and the down rays
+                const float g0 = slot_bound<T, 1, 1>(fI(prv, D.up[0] ? F_GU : F_GD) + o, npp, b[0][0], b[0][1], b[0][2], b[0][3], e[0]);
+                const float g1 = slot_bound<T, -1, 1>(fI(prv, D.up[1] ? F_GU : F_GD) + o, npp, b[1][0], b[1][1], b[1][2], b[1][3], e[1]);
+                const float g2 = slot_bound<T, 1, -1>(fI(prv, D.up[2] ? F_GU : F_GD) + o, npp, b[2][0], b[2][1], b[2][2], b[2][3], e[2]);
+                const float g3 = slot_bound<T, -1, -1>(fI(prv, D.up[3] ? F_GU : F_GD) + o, npp, b[3][0], b[3][1], b[3][2], b[3][3], e[3]);
+                gu = fmaxf(fmaxf(D.up[0] ? g0 : 0.f, D.up[1] ? g1 : 0.f), fmaxf(D.up[2] ? g2 : 0.f, D.up[3] ? g3 : 0.f));
+                gd = fmaxf(fmaxf(D.up[0] ? 0.f : g0, D.up[1] ? 0.f : g1), fmaxf(D.up[2] ? 0.f : g2, D.up[3] ? 0.f : g3));
+            }
+            // boundary layer of the x/y groups: set, not integrated
+            if (wrap && (q == 0 || q == NQ - 1)) {
+                for (int d = 0; d < MAXD; ++d)
+                    if (D.up[d] ? q == 0 : q == NQ - 1) v[d] = bc_value(a, *Ug, D, d, p, q, m, sp);
+                if (q == 0) gu = 0.f;
+                if (q == NQ - 1) gd = 0.f;
+            }
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) {
+                if (!D.active[d]) v[d] = T(0);
+                put(fI(cur, F_I0 + d), k, v[d]);
+            }
+            if (!acc) {
+                put(fI(cur, F_GU), k, (T)gu);
+                put(fI(cur, F_GD), k, (T)gd);
+                gmax = fmaxf(gmax, fmaxf(gu, gd));
+            } else {
+                T aJ = 0, aX = 0, aY = 0, aZ = 0;
+#pragma unroll
+                for (int d = 0; d < MAXD; ++d) {
+                    aJ += D.cJ[d] * v[d]; aX += D.cF[0][d] * v[d]; aY += D.cF[1][d] * v[d]; aZ += D.cF[2][d] * v[d];
+                }
+#pragma unroll
+                for (int kk = 0; kk < TQ; ++kk)
+                    if (kk == k - 1) { ps[kk][0] = aJ; ps[kk][1] = aX; ps[kk][2] = aY; ps[kk][3] = aZ; }
+                if (itop && (axis == 2 ? top_plane : q == NQ - 1)) {
+                    int i, j;
+                    natural_ij(axis, p, q, m, i, j);
+                    for (int d = 0; d < MAXD; ++d)
+                        if (D.up[d] && D.active[d]) itop[((long long)D.udx[d] * uny + j) * unx + i] = v[d];
+                }
+            }
+            // first and last rows go to the neighbours through the global ring
+            if (k == 1 || k == nrows) {
+                for (int sd = 0; sd < 2; ++sd) {
+                    if (!((sd == 0 && k == 1) || (sd == 1 && k == nrows))) continue;
+                    T *dst = myhalo + ((long long)(cur * 2 + sd) * HALO_CH) * NP + p;
+                    for (int d = 0; d < MAXD; ++d) dst[(long long)d * NP] = v[d];
+                    if (!acc) {
+                        dst[(long long)MAXD * NP] = (T)gu;
+                        dst[(long long)(MAXD + 1) * NP] = (T)gd;
+                    }
+                }
+            }
+        };
+
+        // ---- interior rows need only this tile's own rows; then each thread
+        //      waits for the neighbours' plane t-1 and loads its column of
+        //      their edge rows into the halo rows ----
+        if (act) {
+#pragma unroll 1
+            for (int k = 2; k < nrows; ++k) do_row(k);
+        }
+        if (t > t_first && act) {
+            bool ok = true;
+            if (has_lower) ok = wait_flag_geq(a.flags + tile0 + lower, t, a.status, a.timeout_ns);
+            if (ok && has_upper) ok = wait_flag_geq(a.flags + tile0 + upper, t, a.status, a.timeout_ns);
+            if (!ok) {
+                s_ctl[0] = 1;
+            } else {
+                const int hslot = (t - 1) & 1;
+                for (int side = 0; side < 2; ++side) {
+                    if (side == 0 ? !has_lower : !has_upper) continue;
+                    const int nb = side == 0 ? lower : upper;
+                    const int row = side == 0 ? 0 : nrows + 1;
+                    // the neighbour below sends its last row (sd 1), the one above its first (sd 0)
+                    const T *src = halo_base + (long long)nb * tile_stride +
+                                   ((long long)(hslot * 2 + (side == 0 ? 1 : 0)) * HALO_CH) * NP + p;
+                    T hv[HALO_CH];
+#pragma unroll
+                    for (int ch = 0; ch < HALO_CH; ++ch)
+                        hv[ch] = (ch < MAXD || !acc) ? ld_cg(src + (long long)ch * NP) : T(0);
+#pragma unroll
+                    for (int d = 0; d < MAXD; ++d) put(fI(prv, F_I0 + d), row, hv[d]);
+                    if (!acc) {
+                        put(fI(prv, F_GU), row, hv[MAXD]);
+                        put(fI(prv, F_GD), row, hv[MAXD + 1]);
+                    }
+                }
+            }
+        }
+        __syncthreads();  // B1: halo rows of plane t-1 are in place
+        if (s_ctl[0]) {
+            cp_async_wait_all();
+            return;
+        }
+        if (act) {
+            do_row(1);
+            if (nrows > 1) do_row(nrows);
+        }
+        if (!acc) {
+            for (int o = 16; o; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+            if (lane == 0) s_wmax[warp] = gmax;
+        }
+        // decision for plane t+1 (its bound is L planes old: normally already complete)
+        if (tid == dec_thread && t_acc < 0 && t + 1 - a.L >= 0) {
+            const int ts = t + 1 - a.L;
             const int slot = ts % a.R;
             const unsigned want = (unsigned)ntl * (unsigned)(ts / a.R + 1);
-            const unsigned int *cnt = a.gcnt + (long long)uidx * a.R + slot;
-            bool ok = wait_count_geq(cnt, want, a.status, a.timeout_ns);
+            bool ok = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
             if (ok) {
                 const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
                 if ((unsigned)(v >> 32) != (unsigned)(ts + 1)) {
                     atomicOr(a.status, ST_BADARG);  // ring overrun: never expected
                     ok = false;
                 } else {
-                    s_ctl[2] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.tol ? 1 : 0;
+                    s_ctl[1] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.tol ? 1 : 0;
                 }
             }
             if (!ok) s_ctl[0] = 1;
         }
-        cp_async_wait_all();
-        __syncthreads();
-        if (s_ctl[0]) return;
-        if (need_decision && s_ctl[2]) {
-            t_acc = t;
-            if (r == 0 && tid == 0) a.unit_tacc[uidx] = t;
-        }
-        if (U.wrap && t_acc < 0 && t >= warm_cap) {
-            if (tid == 0) atomicOr(a.status, ST_NOCONV);
-            return;  // every tile of the unit stops at the same plane
-        }
-        const bool acc = t_acc >= 0;
-
-        // ---- (B) neighbours' edge rows of plane t-1 -> smem rows 0 and nrows+1 ----
-        if (t > t_first && act) {
-            const int slot = (t - 1) & 1;
-            for (int side = 0; side < 2; ++side) {
-                if (side == 0 ? !has_lower : !has_upper) continue;
-                const int nb = side == 0 ? lower : upper;
-                const int row = side == 0 ? 0 : nrows + 1;
-                // the neighbour below sends its last row (sd 1), the one above its first (sd 0)
-                const T *src = a.halo + U.halo_off + (long long)nb * tile_stride +
-                               ((long long)(slot * 2 + (side == 0 ? 1 : 0)) * HALO_CH) * NP + p;
-                for (int d = 0; d < nd; ++d) sI[d * PL + row * NP + p] = ld_cg(src + (long long)d * NP);
-                if (!acc) {
-                    sG[row * NP + p] = (float)ld_cg(src + (long long)MAXD * NP);
-                    sG[PL + row * NP + p] = (float)ld_cg(src + (long long)(MAXD + 1) * NP);
-                }
-            }
-        }
-        __syncthreads();
-
-        // ---- (C) integrate the own points of plane t ----
-        const T *Xp = sX + ((t - 1) & 1) * PL, *Sp = sS + ((t - 1) & 1) * PL;
-        const T *Xc = sX + (t & 1) * PL, *Sc = sS + (t & 1) * PL;
-        T nI[TQ][MAXD];
-        float nG[TQ][2];
-        float gmax = 0.f;
-#pragma unroll
-        for (int k = 0; k < TQ; ++k) {
-            const int row = k + 1;
-            nG[k][0] = 0.f;
-            nG[k][1] = 0.f;
-            if (!act || row > nrows) continue;
-            const int q = q0 + k;
-            const T xp = Xc[row * NP + p], sp = Sc[row * NP + p];
-#pragma unroll
-            for (int d = 0; d < MAXD; ++d) {
-                if (d >= nd) break;
-                const bool bcrow = U.wrap && ((D.up[d] && q == 0) || (!D.up[d] && q == NQ - 1));
-                if (bcrow) {
-                    nI[k][d] = bc_value(a, U, D, d, p, q, m, sp);
-                    continue;
-                }
-                const int pc = D.sP[d] > 0 ? pm : pn;
-                const int rc = row - D.sQ[d];
-                const int i0 = row * NP + p, i1 = row * NP + pc, i2 = rc * NP + p, i3 = rc * NP + pc;
-                const T b0 = D.beta[d][0], b1 = D.beta[d][1], b2 = D.beta[d][2], b3 = D.beta[d][3];
-                const T *Id = sI + d * PL;
-                const T Iup = b0 * Id[i0] + b1 * Id[i1] + b2 * Id[i2] + b3 * Id[i3];
-                const T xup = b0 * Xp[i0] + b1 * Xp[i1] + b2 * Xp[i2] + b3 * Xp[i3];
-                const T sup = b0 * Sp[i0] + b1 * Sp[i1] + b2 * Sp[i2] + b3 * Sp[i3];
-                const T x = D.hds[d] * (xup + xp);
-                T e, wu, wp;
-                seg_weights(x, e, wu, wp);
-                nI[k][d] = Iup + wu * (sup - Iup) + wp * (sp - Iup);
-                if (!acc) {
-                    const int grp = D.up[d] ? 0 : 1;
-                    const float *Gd = sG + grp * PL;
-                    const float g = (float)e * ((float)b0 * Gd[i0] + (float)b1 * Gd[i1] + (float)b2 * Gd[i2] +
-                                                (float)b3 * Gd[i3]);
-                    nG[k][grp] = fmaxf(nG[k][grp], g);
-                }
-            }
-            gmax = fmaxf(gmax, fmaxf(nG[k][0], nG[k][1]));
-        }
-        if (!acc) {
-            for (int o = 16; o; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-            if (lane == 0) s_wmax[warp] = gmax;
-        }
-        __syncthreads();
-
-        // ---- (D) plane t becomes the previous plane; publish edge rows ----
-        const int oslot = t & 1;
-        const bool last = acc && (t - t_acc == NM - 1);
-        if (!last) prefetch(t + 1);  // into the slot of plane t-1, no longer read
-#pragma unroll
-        for (int k = 0; k < TQ; ++k) {
-            const int row = k + 1;
-            if (!act || row > nrows) continue;
-            const int q = q0 + k;
-            T aJ = 0, aX = 0, aY = 0, aZ = 0;
-#pragma unroll
-            for (int d = 0; d < MAXD; ++d) {
-                if (d >= nd) break;
-                const T v = nI[k][d];
-                sI[d * PL + row * NP + p] = v;
-                aJ += D.cJ[d] * v; aX += D.cF[0][d] * v; aY += D.cF[1][d] * v; aZ += D.cF[2][d] * v;
-            }
-            if (!acc) {
-                sG[row * NP + p] = nG[k][0];
-                sG[PL + row * NP + p] = nG[k][1];
-            }
-            for (int sd = 0; sd < 2; ++sd) {
-                if (!((sd == 0 && row == 1) || (sd == 1 && row == nrows))) continue;
-                T *dst = myhalo + ((long long)(oslot * 2 + sd) * HALO_CH) * NP + p;
-                for (int d = 0; d < nd; ++d) dst[(long long)d * NP] = nI[k][d];
-                if (!acc) {
-                    dst[(long long)MAXD * NP] = (T)nG[k][0];
-                    dst[(long long)(MAXD + 1) * NP] = (T)nG[k][1];
-                }
-            }
-            if (acc) {
-                const long long off = (long long)m * U.sM + (long long)q * U.sQ + p;
-                part[off] = aJ; part[U.N + off] = aX; part[2 * U.N + off] = aY; part[3 * U.N + off] = aZ;
-                if (itop) {
-                    const bool top = U.axis == 2 ? (t == NM - 1 && U.sa > 0) : (q == NQ - 1);
-                    if (top) {
-                        int i, j;
-                        natural_ij(U.axis, p, q, m, i, j);
-                        for (int d = 0; d < nd; ++d)
-                            if (D.up[d]) itop[((long long)D.udx[d] * U.ny + j) * U.nx + i] = nI[k][d];
-                    }
-                }
-            }
-        }
-        __syncthreads();
+        __syncthreads();  // B2: plane t complete (smem and ring); plane t-1 no longer read
         if (tid == 0) {
+            // release the edge rows (the barrier orders the CTA's ring writes first)
+            st_release(a.flags + gt, t + 1);
             if (!acc) {
                 float g = 0.f;
                 for (int w = 0; w < (NT + 31) / 32; ++w) g = fmaxf(g, s_wmax[w]);
                 const int slot = t % a.R;
-                const unsigned long long v = ((unsigned long long)(unsigned)(t + 1) << 32) | __float_as_uint(g);
-                atomicMax(a.gmax + (long long)uidx * a.R + slot, v);
-                __threadfence();
-                atomicAdd(a.gcnt + (long long)uidx * a.R + slot, 1u);
+                const unsigned long long pv = ((unsigned long long)(unsigned)(t + 1) << 32) | __float_as_uint(g);
+                atomicMax(a.gmax + (long long)uidx * a.R + slot, pv);
+                red_release_add(a.gcnt + (long long)uidx * a.R + slot, 1u);
             }
-            __threadfence();
-            st_release(a.flags + gt, t + 1);
+        }
+        if (s_ctl[0]) return;
+        if (acc && act) {
+            T *const pplane = part + (long long)m * sM + p;
+#pragma unroll
+            for (int kk = 0; kk < TQ; ++kk) {
+                if (kk >= nrows) break;
+                T *pp = pplane + (long long)(q0 + kk) * sQ;
+                pp[0] = ps[kk][0]; pp[N] = ps[kk][1]; pp[2 * N] = ps[kk][2]; pp[3 * N] = ps[kk][3];
+            }
         }
         if (last) break;
+        prefetch(t + 1);  // into the slot of plane t-1
     }
 }
 
@@ -480,8 +546,7 @@ __global__ void __launch_bounds__(1024) sweep_kernel(SweepArgs<T> a)
         const int tile = s_tile;
         if (tile < 0 || tile >= a.total_tiles) return;
         const int u = a.unit_of_tile[tile];
-        const SweepUnit &U = a.units[u];
-        run_tile<T, TQ>(a, U, u, tile - U.tile0, tile, smem);
+        run_tile<T, TQ>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
     }
 }
 
