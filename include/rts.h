@@ -82,10 +82,11 @@ typedef struct {
 
 enum {
     RTS_FLAG_HOST_IO = 1, /* allocate staging buffers for rts_solve_host */
-    RTS_FLAG_TIMING = 2   /* record CUDA events around each phase of every
+    RTS_FLAG_TIMING = 2,  /* record CUDA events around each phase of every
                              solve (on the handle's stream); rts_get_stats
                              reports their mean over the solves since the
                              previous rts_get_stats call */
+    RTS_FLAG_ADJOINT = 4  /* allocate the scratch of rts_adjoint */
 };
 
 typedef struct {
@@ -100,6 +101,10 @@ typedef struct {
     int flags;            /* RTS_FLAG_* */
     double timeout_s;     /* device-side wait limit in seconds (default 2) */
     void *stream;         /* cudaStream_t to run on (NULL = legacy default stream) */
+    int adjoint_chunk_bands; /* bands whose intensities rts_adjoint recomputes
+                             and keeps at a time (the checkpoint unit;
+                             0 = 1 band); with all bands in one chunk the
+                             forward solve is not repeated */
 } rts_options;
 
 typedef struct {
@@ -161,6 +166,37 @@ const char *rts_last_error(rts_handle *h);
 int rts_num_up(rts_handle *h);
 
 void rts_destroy(rts_handle *h);
+
+/* Gradient of the scalar
+ *   L = <gI_top, I_top> + <gJ, J> + <gF, F> + <gQ, Q_rad>
+ * (the outputs of rts_solve on the same chi, S, bc) with respect to log chi
+ * and S of every band: reverse-mode differentiation of the discrete solve.
+ * The paper has no adjoint; this is the transpose of its forward operator:
+ *   1. the Q step transposed (cotangents of J_b and F_b, and the direct chi
+ *      and S terms of Q_rad);
+ *   2. per chunk of adjoint_chunk_bands bands (the checkpoint): the forward
+ *      sweep again, keeping the converged intensity of every ray of the chunk
+ *      (4 values per point and sweep unit), then the reverse sweep: the
+ *      cotangent of I along each ray, lam_p = lam0_p + sum over the downwind
+ *      points r that interpolate from p of beta e_r lam_r, swept in the
+ *      reverse plane order with the same tiles, ready flags and periodic-wrap
+ *      bound as the forward sweep; then the derivative of each segment's
+ *      formal solution with respect to the opacity and source it used,
+ *      gathered onto the grid points it was interpolated from;
+ *   3. g_logchi = chi * dL/dchi.
+ * Boundary layers with I = S pass their cotangent to g_S; explicit boundary
+ * intensities are treated as constants.
+ * Arguments: chi, S, bc as for rts_solve. gI_top is [B][n_up][Ny][Nx] in the
+ * sweep precision; gJ [Nz][Ny][Nx], gF [3][Nz][Ny][Nx] and gQ [Nz][Ny][Nx]
+ * are float64; any cotangent may be NULL (zero). g_logchi and g_S are
+ * [B][Nz][Ny][Nx] in the sweep precision (written, not accumulated). All
+ * device pointers; outputs must not alias inputs. When gQ is NULL the first
+ * forward solve is skipped (J, F enter L linearly). Needs RTS_FLAG_ADJOINT
+ * at create time; allocates nothing and does not synchronise. Device errors
+ * as for rts_solve (rts_check). */
+rts_status rts_adjoint(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                       const void *gI_top, const double *gJ, const double *gF, const double *gQ,
+                       void *g_logchi, void *g_S);
 
 /* ---------------------------------------------------------------------------
  * Forward solve without any memory allocation. The paper has no counterpart:

@@ -18,6 +18,7 @@ FP64, FP32_MIXED, FP32_COMPENSATED = 0, 1, 2
 BC_ZERO, BC_EQUAL_S, BC_EXPLICIT = 0, 1, 2
 FLAG_HOST_IO = 1
 FLAG_TIMING = 2
+FLAG_ADJOINT = 4
 
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED, "fp32_compensated": FP32_COMPENSATED}
 _BC = {"zero": BC_ZERO, "equal_s": BC_EQUAL_S}
@@ -35,7 +36,8 @@ class Quadrature(C.Structure):
 class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("tau_switch", C.c_double), ("wrap_tol", C.c_double),
                 ("max_wrap_iters", C.c_int), ("tile_rows", C.c_int), ("threads", C.c_int),
-                ("flags", C.c_int), ("timeout_s", C.c_double), ("stream", C.c_void_p)]
+                ("flags", C.c_int), ("timeout_s", C.c_double), ("stream", C.c_void_p),
+                ("adjoint_chunk_bands", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -54,7 +56,7 @@ _lib = None
 
 # every symbol include/rts.h declares
 EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "rts_check",
-           "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc")
+           "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint")
 
 
 def library_path() -> str:
@@ -80,6 +82,8 @@ def load(build_if_missing: bool = True):
     for f in ("rts_solve", "rts_solve_host"):
         getattr(L, f).argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp]
         getattr(L, f).restype = C.c_int
+    L.rts_adjoint.argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp, vp, vp]
+    L.rts_adjoint.restype = C.c_int
     L.rts_check.argtypes = [vp]
     L.rts_check.restype = C.c_int
     L.rts_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -117,7 +121,7 @@ class Solver:
 
     def __init__(self, nx, ny, nz, nbands=1, dx=1.0, dy=1.0, dz=1.0, precision="fp64", n=None, w=None,
                  tau_switch=0.1, wrap_tol=0.0, max_wrap_iters=64, tile_rows=0, timeout_s=2.0,
-                 host_io=False, timing=False, stream=None):
+                 host_io=False, timing=False, stream=None, adjoint=False, adjoint_chunk_bands=0):
         import torch
 
         L = load()
@@ -134,7 +138,8 @@ class Solver:
         o.max_wrap_iters = max_wrap_iters
         o.tile_rows = tile_rows
         o.timeout_s = timeout_s
-        o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0)
+        o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0) | (FLAG_ADJOINT if adjoint else 0)
+        o.adjoint_chunk_bands = adjoint_chunk_bands
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -204,6 +209,41 @@ class Solver:
         b, keep = self._bc(bottom, top)
         rc = self._L.rts_solve(self._h, _ptr(chi), _ptr(S), C.byref(b), _ptr(out.get("I_top")), _ptr(out.get("J")),
                                _ptr(out.get("F")), _ptr(out.get("Q")))
+        self._err(rc)
+        if check:
+            self.check()
+        del keep
+        return out
+
+    def adjoint(self, chi, S, gI_top=None, gJ=None, gF=None, gQ=None, bottom="equal_s", top="zero", check=True,
+                out=None):
+        """Gradient of <gI_top,I_top> + <gJ,J> + <gF,F> + <gQ,Q> with respect to
+        log chi and S (rts_adjoint). Cotangents may be None (zero); gI_top in
+        the solver dtype, gJ/gF/gQ float64. Returns (g_logchi, g_S), each
+        [B, nz, ny, nx] in the solver dtype. Needs Solver(..., adjoint=True)."""
+        torch = self.torch
+        shape = (self.nbands, self.nz, self.ny, self.nx)
+        assert tuple(chi.shape) == shape and tuple(S.shape) == shape, (chi.shape, shape)
+        assert chi.dtype == self.dtype and S.dtype == self.dtype and chi.is_cuda and S.is_cuda
+        chi = chi.contiguous()
+        S = S.contiguous()
+
+        def cot(t, shp, dt):
+            if t is None:
+                return None
+            assert tuple(t.shape) == shp, (t.shape, shp)
+            assert t.dtype == dt and t.is_cuda
+            return t.contiguous()
+
+        gI_top = cot(gI_top, (self.nbands, self.n_up, self.ny, self.nx), self.dtype)
+        gJ = cot(gJ, (self.nz, self.ny, self.nx), torch.float64)
+        gF = cot(gF, (3, self.nz, self.ny, self.nx), torch.float64)
+        gQ = cot(gQ, (self.nz, self.ny, self.nx), torch.float64)
+        if out is None:
+            out = (torch.empty_like(chi), torch.empty_like(S))
+        b, keep = self._bc(bottom, top)
+        rc = self._L.rts_adjoint(self._h, _ptr(chi), _ptr(S), C.byref(b), _ptr(gI_top), _ptr(gJ), _ptr(gF),
+                                 _ptr(gQ), _ptr(out[0]), _ptr(out[1]))
         self._err(rc)
         if check:
             self.check()

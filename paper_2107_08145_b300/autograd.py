@@ -1,0 +1,45 @@
+"""torch.autograd binding of the solver: outputs (I_top, J, F, Q_rad) as a
+differentiable function of (log chi, S).
+
+The forward pass is rts_solve; the backward pass is rts_adjoint, the
+reverse-sweep adjoint of the discrete short-characteristics solve (the
+library's kernels compute every step of both; torch only forms chi = exp(log
+chi) and holds the tensors).
+"""
+from __future__ import annotations
+
+import torch
+
+from . import Solver
+
+
+class RTSFunction(torch.autograd.Function):
+    """RTSFunction.apply(solver, log_chi, S, bottom, top) -> (I_top, J, F, Q).
+
+    solver must have been created with adjoint=True. log_chi and S are CUDA
+    tensors [B, nz, ny, nx] in the solver's dtype."""
+
+    @staticmethod
+    def forward(ctx, solver: Solver, log_chi, S, bottom="equal_s", top="zero"):
+        chi = torch.exp(log_chi)
+        out = solver.solve(chi, S, bottom=bottom, top=top)
+        ctx.solver = solver
+        ctx.bc = (bottom, top)
+        ctx.save_for_backward(chi, S)
+        ctx.set_materialize_grads(False)
+        return out["I_top"], out["J"], out["F"], out["Q"]
+
+    @staticmethod
+    def backward(ctx, gI_top, gJ, gF, gQ):
+        chi, S = ctx.saved_tensors
+        solver = ctx.solver
+        if all(g is None for g in (gI_top, gJ, gF, gQ)):
+            return None, None, None, None, None
+        g_logchi, g_S = solver.adjoint(chi, S, gI_top=gI_top, gJ=gJ, gF=gF, gQ=gQ, bottom=ctx.bc[0],
+                                       top=ctx.bc[1])
+        return None, g_logchi, g_S, None, None
+
+
+def rts_apply(solver: Solver, log_chi, S, bottom="equal_s", top="zero"):
+    """Differentiable solve: returns (I_top, J, F, Q)."""
+    return RTSFunction.apply(solver, log_chi, S, bottom, top)

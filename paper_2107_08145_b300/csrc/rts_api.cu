@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "rts.h"
+#include "adjoint.cuh"
 #include "qstep.cuh"
 #include "sweep.cuh"
 
@@ -202,6 +203,13 @@ struct rts_handle {
     unsigned long long *d_gmax = nullptr;
     rts::RedUnit *d_ru = nullptr;
     int *d_ru_begin = nullptr;
+    // adjoint scratch (RTS_FLAG_ADJOINT): lam0 [B][4][N] natural and
+    // x-transposed, direct Q-step terms [B][2][N], and per checkpoint chunk of
+    // at most chunk_units units: I [u][4][N], lam/B [u][4][N], C [u][4][N], G [u][2][N]
+    void *d_lam0 = nullptr, *d_lam0T = nullptr, *d_direct = nullptr;
+    void *d_adjI = nullptr, *d_adjL = nullptr, *d_adjC = nullptr, *d_adjG = nullptr;
+    int chunk_bands = 1, chunk_units = 0, grid_adj = 0;
+    std::vector<int> band_unit;   // first unit of band b (b = 0..B)
     // host-IO staging
     void *d_in_chi = nullptr, *d_in_S = nullptr, *d_out_itop = nullptr;
     double *d_out_J = nullptr, *d_out_F = nullptr, *d_out_Q = nullptr;
@@ -248,6 +256,18 @@ static SweepFn<T> sweep_fn(int tq)
     }
 }
 
+template <typename T>
+static SweepFn<T> sweep_adj_fn(int tq)
+{
+    switch (tq) {
+    case 1: return rts::sweep_adj_kernel<T, 1>;
+    case 2: return rts::sweep_adj_kernel<T, 2>;
+    case 3: return rts::sweep_adj_kernel<T, 3>;
+    case 4: return rts::sweep_adj_kernel<T, 4>;
+    default: return rts::sweep_adj_kernel<T, 4>;
+    }
+}
+
 static const int kTileRows[4] = {4, 3, 2, 1};
 
 // shared memory of one sweep CTA: per plane parity I of 4 slots and the two
@@ -272,13 +292,13 @@ static int pick_tile_rows(int requested, int np, int esize)
 }
 
 template <typename T>
-static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a)
+static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool reverse = false)
 {
-    SweepFn<T> kern = sweep_fn<T>(h->tq);
+    SweepFn<T> kern = reverse ? sweep_adj_fn<T>(h->tq) : sweep_fn<T>(h->tq);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(h->grid);
+    cfg.gridDim = dim3(std::min(reverse ? h->grid_adj : h->grid, a.total_tiles));
     cfg.blockDim = dim3(h->nt);
     cfg.dynamicSmemBytes = h->smem;
     cfg.stream = h->stream;
@@ -291,9 +311,9 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a)
 }
 
 template <typename T>
-static cudaError_t occupancy(rts_handle *h, int *blocks)
+static cudaError_t occupancy(rts_handle *h, int *blocks, bool reverse = false)
 {
-    SweepFn<T> kern = sweep_fn<T>(h->tq);
+    SweepFn<T> kern = reverse ? sweep_adj_fn<T>(h->tq) : sweep_fn<T>(h->tq);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, h->nt, h->smem);
@@ -427,6 +447,25 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         return bail(fail(h, RTS_EINVAL, "a sweep unit has %d tiles but only %d CTAs fit on the GPU", h->max_ntiles,
                          blocks * nsm));
 
+    const bool adjoint = (o.flags & RTS_FLAG_ADJOINT) != 0;
+    h->band_unit.assign(nbands + 1, 0);
+    for (size_t u = 0; u < h->units.size(); ++u) h->band_unit[h->units[u].band + 1]++;
+    for (int b = 0; b < nbands; ++b) h->band_unit[b + 1] += h->band_unit[b];
+    if (adjoint) {
+        h->chunk_bands = std::min(nbands, std::max(1, o.adjoint_chunk_bands));
+        for (int b = 0; b < nbands; b += h->chunk_bands) {
+            const int b1 = std::min(nbands, b + h->chunk_bands);
+            h->chunk_units = std::max(h->chunk_units, h->band_unit[b1] - h->band_unit[b]);
+        }
+        int ablocks = 0;
+        oe = o.prec == RTS_FP64 ? occupancy<double>(h, &ablocks, true) : occupancy<float>(h, &ablocks, true);
+        if (oe != cudaSuccess) return bail(fail(h, RTS_ECUDA, "occupancy query: %s", cudaGetErrorString(oe)));
+        h->grid_adj = ablocks * nsm;
+        if (ablocks < 1 || h->grid_adj < h->max_ntiles)
+            return bail(fail(h, RTS_EINVAL, "a sweep unit has %d tiles but only %d reverse-sweep CTAs fit",
+                             h->max_ntiles, h->grid_adj));
+    }
+
     // ---- device memory ----
     const size_t es = h->esize;
     const size_t accsz = 8;  // double or df32
@@ -447,6 +486,17 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_tacc = take(sizeof(int) * h->units.size());
     const size_t o_ru = take(sizeof(rts::RedUnit) * h->units.size());
     const size_t o_rub = take(sizeof(int) * (nbands + 1));
+    size_t o_adj[7] = {0};
+    if (adjoint) {
+        const size_t cu = (size_t)h->chunk_units;
+        o_adj[0] = take((size_t)nbands * 4 * h->N * es);
+        o_adj[1] = h->has_x ? take((size_t)nbands * 4 * h->N * es) : 0;
+        o_adj[2] = take((size_t)nbands * 2 * h->N * es);
+        o_adj[3] = take(cu * 4 * h->N * es);
+        o_adj[4] = take(cu * 4 * h->N * es);
+        o_adj[5] = take(cu * 4 * h->N * es);
+        o_adj[6] = take(cu * 2 * h->N * es);
+    }
     size_t o_io[6] = {0};
     const bool hostio = (o.flags & RTS_FLAG_HOST_IO) != 0;
     if (hostio) {
@@ -478,6 +528,15 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->d_unit_tacc = (int *)(base + o_tacc);
     h->d_ru = (rts::RedUnit *)(base + o_ru);
     h->d_ru_begin = (int *)(base + o_rub);
+    if (adjoint) {
+        h->d_lam0 = base + o_adj[0];
+        h->d_lam0T = h->has_x ? base + o_adj[1] : nullptr;
+        h->d_direct = base + o_adj[2];
+        h->d_adjI = base + o_adj[3];
+        h->d_adjL = base + o_adj[4];
+        h->d_adjC = base + o_adj[5];
+        h->d_adjG = base + o_adj[6];
+    }
     if (hostio) {
         h->d_in_chi = base + o_io[0];
         h->d_in_S = base + o_io[1];
@@ -506,6 +565,50 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
 }
 
 }  // extern "C"
+
+// launch arguments of a sweep over all units; callers narrow the tile range
+template <typename T>
+static rts::SweepArgs<T> sweep_args(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc)
+{
+    rts::SweepArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.units = h->d_units;
+    a.unit_of_tile = h->d_unit_of_tile;
+    a.total_tiles = h->total_tiles;
+    a.chi = (const T *)chi;
+    a.S = (const T *)S;
+    a.chiT = (const T *)h->d_chiT;
+    a.ST = (const T *)h->d_ST;
+    a.bc_bottom = bc ? bc->bottom : RTS_BC_EQUAL_S;
+    a.bc_top = bc ? bc->top : RTS_BC_ZERO;
+    a.bc_up = bc ? (const T *)bc->bottom_I : nullptr;
+    a.bc_dn = bc ? (const T *)bc->top_I : nullptr;
+    a.n_up = h->n_up;
+    a.n_dn = h->n_dn;
+    a.ticket = h->d_ticket;
+    a.flags = h->d_flags;
+    a.halo = (T *)h->d_halo;
+    a.gcnt = h->d_gcnt;
+    a.gmax = h->d_gmax;
+    a.R = h->R;
+    a.L = kLag;
+    a.status = h->d_status;
+    a.unit_tacc = h->d_unit_tacc;
+    a.tol = (float)h->opt.wrap_tol;
+    a.max_periods = h->opt.max_wrap_iters;
+    a.timeout_ns = (unsigned long long)(h->opt.timeout_s * 1e9);
+    return a;
+}
+
+// clear the ticket, ready flags and wrap-decision counters before a sweep launch
+static rts_status reset_sweep_state(rts_handle *h, cudaStream_t st)
+{
+    CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->total_tiles, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
+    return RTS_OK;
+}
 
 template <typename T, typename Acc>
 static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top,
@@ -539,34 +642,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
         kernels += 2;
     }
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[1], st));
-    rts::SweepArgs<T> a;
-    std::memset(&a, 0, sizeof(a));
-    a.units = h->d_units;
-    a.unit_of_tile = h->d_unit_of_tile;
-    a.total_tiles = h->total_tiles;
-    a.chi = (const T *)chi;
-    a.S = (const T *)S;
-    a.chiT = (const T *)h->d_chiT;
-    a.ST = (const T *)h->d_ST;
+    rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
     a.itop = (T *)I_top;
-    a.bc_bottom = bc ? bc->bottom : RTS_BC_EQUAL_S;
-    a.bc_top = bc ? bc->top : RTS_BC_ZERO;
-    a.bc_up = bc ? (const T *)bc->bottom_I : nullptr;
-    a.bc_dn = bc ? (const T *)bc->top_I : nullptr;
-    a.n_up = h->n_up;
-    a.n_dn = h->n_dn;
-    a.ticket = h->d_ticket;
-    a.flags = h->d_flags;
-    a.halo = (T *)h->d_halo;
-    a.gcnt = h->d_gcnt;
-    a.gmax = h->d_gmax;
-    a.R = h->R;
-    a.L = kLag;
-    a.status = h->d_status;
-    a.unit_tacc = h->d_unit_tacc;
-    a.tol = (float)h->opt.wrap_tol;
-    a.max_periods = h->opt.max_wrap_iters;
-    a.timeout_ns = (unsigned long long)(h->opt.timeout_s * 1e9);
     cudaError_t e = launch_sweep<T>(h, a);
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     kernels += 1;
@@ -601,6 +678,142 @@ static rts_status check_bc(rts_handle *h, const rts_boundary *bc)
     return RTS_OK;
 }
 
+// Reverse-mode gradient (declared in rts.h). Enqueues, on the handle's stream:
+// [transpose of chi, S] [forward sweep + band reduction, only when Q_rad
+// enters L] -> Q-step adjoint -> [transpose of lam0], then per checkpoint chunk
+// of bands: forward sweep that keeps I -> reverse sweep -> two gradient
+// passes -> reduce into g_logchi, g_S.
+template <typename T, typename Acc>
+static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                               const void *gI_top, const double *gJ, const double *gF, const double *gQ,
+                               void *g_logchi, void *g_S)
+{
+    const rts_grid &g = h->g;
+    const int B = h->B;
+    const long long N = h->N;
+    cudaStream_t st = h->stream;
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
+    int kernels = 0;
+    const dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
+    if (h->has_x) {
+        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)h->d_chiT, g.nx, g.ny, g.nz);
+        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)h->d_ST, g.nx, g.ny, g.nz);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 2;
+    }
+    if (gQ) {  // J_b, F_b of the forward solve
+        rts_status rs = reset_sweep_state(h, st);
+        if (rs) return rs;
+        rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
+        cudaError_t e = launch_sweep<T>(h, a);
+        if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+        rts::reduce_units_kernel<T, Acc><<<tg, tb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 2;
+    }
+    {
+        rts::QAdjParams P;
+        P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
+        P.dx = g.dx; P.dy = g.dy; P.dz = g.dz;
+        P.thin = std::min(g.dx, std::min(g.dy, g.dz)) / h->opt.tau_switch;
+        const dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
+        rts::qstep_adjoint_kernel<T, Acc><<<qg, tb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, gJ,
+                                                            gF, gQ, P, (T *)h->d_lam0, (T *)h->d_direct);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 1;
+    }
+    if (h->has_x) {
+        const dim3 lg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B * 4));
+        rts::transpose_x_kernel<T><<<lg, tb, 0, st>>>((const T *)h->d_lam0, (T *)h->d_lam0T, g.nx, g.ny, g.nz);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 1;
+    }
+    for (int b0 = 0; b0 < B; b0 += h->chunk_bands) {
+        const int b1 = std::min(B, b0 + h->chunk_bands);
+        const int u0 = h->band_unit[b0], u1 = h->band_unit[b1];
+        const rts::SweepUnit &U0 = h->units[u0], &U1 = h->units[u1 - 1];
+        rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
+        a.tile_base = U0.tile0;
+        a.total_tiles = U1.tile0 + U1.ntiles - U0.tile0;
+        a.unit_base = u0;
+        // forward sweep of the chunk, keeping every ray's converged I
+        rts_status rs = reset_sweep_state(h, st);
+        if (rs) return rs;
+        a.store = (T *)h->d_adjI;
+        cudaError_t e = launch_sweep<T>(h, a);
+        if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+        // reverse sweep: cotangent of I of every ray
+        rs = reset_sweep_state(h, st);
+        if (rs) return rs;
+        a.store = (T *)h->d_adjL;
+        a.lam0 = (const T *)h->d_lam0;
+        a.lam0T = (const T *)h->d_lam0T;
+        a.gitop = (const T *)gI_top;
+        e = launch_sweep<T>(h, a, true);
+        if (e != cudaSuccess) return fail(h, RTS_ECUDA, "reverse sweep launch: %s", cudaGetErrorString(e));
+        kernels += 2;
+        // gradient passes over every point of every unit of the chunk
+        rts::GradArgs<T> ga;
+        ga.units = h->d_units;
+        ga.unit_base = u0;
+        ga.chi = (const T *)chi;
+        ga.S = (const T *)S;
+        ga.chiT = (const T *)h->d_chiT;
+        ga.ST = (const T *)h->d_ST;
+        ga.I = (const T *)h->d_adjI;
+        ga.LB = (T *)h->d_adjL;
+        ga.C = (T *)h->d_adjC;
+        ga.G = (T *)h->d_adjG;
+        ga.bc_bottom = bc ? bc->bottom : RTS_BC_EQUAL_S;
+        ga.bc_top = bc ? bc->top : RTS_BC_ZERO;
+        int np = 0, nq = 0, nm = 0;
+        for (int u = u0; u < u1; ++u) {
+            np = std::max(np, h->units[u].NP);
+            nq = std::max(nq, h->units[u].NQ);
+            nm = std::max(nm, h->units[u].NM);
+        }
+        // blockIdx.z = m + nm * (unit - first unit of the launch); at most 65535
+        const int per = std::max(1, 65535 / nm);
+        for (int us = u0; us < u1; us += per) {
+            const int ue = std::min(u1, us + per);
+            rts::GradArgs<T> gs = ga;
+            gs.unit_base = us;
+            const long long shift = (long long)(us - u0);
+            gs.I = ga.I + shift * 4 * N;
+            gs.LB = ga.LB + shift * 4 * N;
+            gs.C = ga.C + shift * 4 * N;
+            gs.G = ga.G + shift * 2 * N;
+            const dim3 gg((np + 127) / 128, nq, (unsigned)(nm * (ue - us)));
+            rts::adj_pass1_kernel<T><<<gg, 128, 0, st>>>(gs, nm);
+            CUDA_TRY(h, cudaGetLastError());
+            kernels += 1;
+        }
+        for (int us = u0; us < u1; us += per) {
+            const int ue = std::min(u1, us + per);
+            rts::GradArgs<T> gs = ga;
+            gs.unit_base = us;
+            const long long shift = (long long)(us - u0);
+            gs.I = ga.I + shift * 4 * N;
+            gs.LB = ga.LB + shift * 4 * N;
+            gs.C = ga.C + shift * 4 * N;
+            gs.G = ga.G + shift * 2 * N;
+            const dim3 gg((np + 127) / 128, nq, (unsigned)(nm * (ue - us)));
+            rts::adj_pass2_kernel<T><<<gg, 128, 0, st>>>(gs, nm);
+            CUDA_TRY(h, cudaGetLastError());
+            kernels += 1;
+        }
+        const dim3 rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * (b1 - b0)));
+        rts::adj_reduce_kernel<T><<<rg, tb, 0, st>>>(h->d_units, u0, u1, b0, (const T *)h->d_adjG,
+                                                    (const T *)h->d_direct, (const T *)chi, (T *)g_logchi, (T *)g_S,
+                                                    g.nx, g.ny, g.nz);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 1;
+    }
+    h->kernels_last = kernels;
+    return RTS_OK;
+}
+
 extern "C" {
 
 rts_status rts_solve(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top, double *J,
@@ -614,6 +827,23 @@ rts_status rts_solve(rts_handle *h, const void *chi, const void *S, const rts_bo
     case RTS_FP64: return solve_impl<double, double>(h, chi, S, bc, I_top, J, F, Q);
     case RTS_FP32_MIXED: return solve_impl<float, double>(h, chi, S, bc, I_top, J, F, Q);
     default: return solve_impl<float, rts::df32>(h, chi, S, bc, I_top, J, F, Q);
+    }
+}
+
+rts_status rts_adjoint(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, const void *gI_top,
+                       const double *gJ, const double *gF, const double *gQ, void *g_logchi, void *g_S)
+{
+    if (!h || !h->dmem) return h ? fail(h, RTS_EINVAL, "handle was not created successfully") : RTS_EINVAL;
+    if (!h->d_lam0) return fail(h, RTS_EINVAL, "rts_adjoint needs RTS_FLAG_ADJOINT at create time");
+    if (!chi || !S || !g_logchi || !g_S) return fail(h, RTS_EINVAL, "chi, S, g_logchi and g_S must not be NULL");
+    if (g_logchi == g_S || g_logchi == chi || g_logchi == S || g_S == chi || g_S == S)
+        return fail(h, RTS_EINVAL, "gradient outputs must not alias the inputs or each other");
+    rts_status s = check_bc(h, bc);
+    if (s) return s;
+    switch (h->opt.prec) {
+    case RTS_FP64: return adjoint_impl<double, double>(h, chi, S, bc, gI_top, gJ, gF, gQ, g_logchi, g_S);
+    case RTS_FP32_MIXED: return adjoint_impl<float, double>(h, chi, S, bc, gI_top, gJ, gF, gQ, g_logchi, g_S);
+    default: return adjoint_impl<float, rts::df32>(h, chi, S, bc, gI_top, gJ, gF, gQ, g_logchi, g_S);
     }
 }
 

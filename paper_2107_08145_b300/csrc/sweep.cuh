@@ -75,7 +75,12 @@ template <typename T>
 struct SweepArgs {
     const SweepUnit *units;
     const int *unit_of_tile;
-    int total_tiles;
+    int total_tiles;            // tiles of this launch: tile_base .. tile_base+total_tiles-1
+    int tile_base, unit_base;   // first tile and first unit of this launch
+    T *store;                   // optional: converged plane values of unit u at store + (u-unit_base)*4N
+    // reverse (adjoint) sweep only
+    const T *lam0, *lam0T;      // [B][4][N] cotangents of J_b, F_b (natural / x-transposed layout)
+    const T *gitop;             // [B][n_up][ny][nx] cotangent of I_top, or null
     // per-call data
     const T *chi, *S;           // [B][N] natural layout
     const T *chiT, *ST;         // [B][N] x-transposed layout ([i][k][j])
@@ -332,6 +337,10 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 }
                 const long long off = (long long)m * sM + (long long)s_q[k] * sQ + p;
                 part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
+                if (a.store) {
+                    T *st = a.store + (long long)(uidx - a.unit_base) * 4 * N + off;
+                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = fI(par, F_I0 + d)[k * npp + c];
+                }
             }
         }
     }
@@ -416,6 +425,11 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
 #pragma unroll
                 for (int kk = 0; kk < TQ; ++kk)
                     if (kk == k - 1) { ps[kk][0] = aJ; ps[kk][1] = aX; ps[kk][2] = aY; ps[kk][3] = aZ; }
+                if (a.store) {
+                    T *st = a.store + (long long)(uidx - a.unit_base) * 4 * N + (long long)m * sM + (long long)q * sQ + p;
+#pragma unroll
+                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = v[d];
+                }
                 if (itop && (axis == 2 ? top_plane : q == NQ - 1)) {
                     int i, j;
                     natural_ij(axis, p, q, m, i, j);
@@ -543,8 +557,8 @@ __global__ void __launch_bounds__(1024) sweep_kernel(SweepArgs<T> a)
             s_tile = tk;
         }
         __syncthreads();
-        const int tile = s_tile;
-        if (tile < 0 || tile >= a.total_tiles) return;
+        if (s_tile < 0 || s_tile >= a.total_tiles) return;
+        const int tile = a.tile_base + s_tile;
         const int u = a.unit_of_tile[tile];
         run_tile<T, TQ>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
     }
