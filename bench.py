@@ -186,6 +186,48 @@ def sweep_algorithmic_bytes(prec, nb=NB, ndir=NDIR):
     return units * n * (2 * es + 4 * es) + nb * (ndir // 2) * NX * NY * es
 
 
+def _adjoint_timing(rts, torch, workload, name, grid, prec, stream, steps):
+    """Mean ms of rts_solve and of rts_adjoint (loss on I_top and Q_rad, one
+    band per checkpoint) on one workload, CUDA events on the solver's stream."""
+    import numpy as np
+
+    nx, ny, nz = grid
+    chi64, S64 = workload(name, nx=nx, ny=ny, nz=nz)
+    nb = chi64.shape[0]
+    s = rts.Solver(nx, ny, nz, nb, precision=prec, stream=stream, adjoint=True)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    chi = torch.as_tensor(chi64, dtype=s.dtype, device=dev)
+    S = torch.as_tensor(S64, dtype=s.dtype, device=dev)
+    out = s.solve(chi, S)
+    rng = np.random.default_rng(0)
+    gI = torch.as_tensor(rng.standard_normal(tuple(out["I_top"].shape)), dtype=s.dtype, device=dev)
+    gQ = 2e-3 * out["Q"]
+    grads = s.adjoint(chi, S, gI_top=gI, gQ=gQ)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / steps
+
+    fwd = timed(lambda: s.solve(chi, S, out=out, check=False))
+    bwd = timed(lambda: s.adjoint(chi, S, gI_top=gI, gQ=gQ, out=grads, check=False))
+    s.check()
+    upd = nx * ny * nz * NDIR * nb
+    r = {"forward_ms": round(fwd, 3), "adjoint_ms": round(bwd, 3), "adjoint_over_forward": round(bwd / fwd, 3),
+         "adjoint_gupd_s": round(upd / (bwd * 1e-3) / 1e9, 3), "checkpoint": "1 band", "steps": steps,
+         "loss": "sum gI*I_top + 1e-3 sum Q^2 cotangents"}
+    del s, chi, S, out, grads
+    torch.cuda.empty_cache()
+    return r
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -303,6 +345,17 @@ def run_ours(args):
                "api": "rts_solve_host (pinned host buffers; copies and sync inside the timed region)"}
         del sh
 
+    # adjoint (rts_adjoint) against the forward solve on the same inputs: the
+    # 96^3 x 4-band adjoint workload and the 288^3 x 4 workload
+    adj = None
+    if not args.skip_adjoint:
+        adj = {}
+        for name, grid in (("adj96x4", (96, 96, 96)), (WORKLOAD, (NX, NY, NZ))):
+            adj[name] = _adjoint_timing(rts, torch, workload, name, grid, prec, stream, max(3, min(args.steps, 10)))
+        ratio = adj[WORKLOAD]["adjoint_over_forward"]
+    else:
+        ratio = None
+
     cpu = None
     if rank == 0 and not args.skip_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -314,7 +367,7 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": st["kernels_per_solve"] * args.steps,
             "phases_ms": phases,
             "wrap": {"max_warmup_planes": st["max_warmup_steps"], "mean_warmup_planes": st["mean_warmup_steps"]},
-            "adjoint_over_forward": None}
+            "adjoint_over_forward": ratio, "adjoint": adj}
     line.update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -403,6 +456,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--grid", default="288,288,288",
                     help="NX,NY,NZ override (profiling of smaller cases); the metric is quoted at 288^3")

@@ -199,6 +199,50 @@ rts_status rts_adjoint(rts_handle *h, const void *chi, const void *S, const rts_
                        void *g_logchi, void *g_S);
 
 /* ---------------------------------------------------------------------------
+ * Batched solves: many independent grids ("subdomains") of uneven size, each
+ * with the same band count, solved in ONE persistent sweep launch (the paper
+ * pays one kernel launch per plane and direction per grid, Sect. 5.2; here
+ * all grids, bands and direction groups share one work list of tiles, longest
+ * units first), plus one launch each of the transpose, the unit reduction and
+ * the Q step over all grids. Results are identical to rts_solve on each grid.
+ *
+ * Packed layout: the arrays of subdomain s follow those of s-1 in one buffer:
+ *   chi, S:  [B][Nz_s][Ny_s][Nx_s] at element grid_offset(s)
+ *   I_top:   [B][n_up][Ny_s][Nx_s] at element top_offset(s)
+ *   J, Q:    [Nz_s][Ny_s][Nx_s] at element point_offset(s); F: [3][...] at 3 * point_offset(s)
+ * rts_batched_layout returns these offsets and the totals
+ * (totals[0] = chi elements, totals[1] = I_top elements, totals[2] = points).
+ * Boundary kinds ZERO and EQUAL_S only. RTS_FLAG_ADJOINT and RTS_FLAG_HOST_IO
+ * are not accepted. Errors as for rts_solve. */
+rts_status rts_create_batched(rts_handle **h, int nsub, const rts_grid *grids, int nbands,
+                              const rts_quadrature *q, const rts_options *opt);
+rts_status rts_solve_batched(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                             void *I_top, double *J, double *F, double *Q_rad);
+rts_status rts_batched_layout(rts_handle *h, int sub, long long *grid_offset, long long *top_offset,
+                              long long *point_offset, long long totals[3]);
+
+/* CUDA graph of one solve (rts_solve or rts_solve_batched, by handle kind)
+ * with fixed arguments, captured on the handle's stream, which must not be
+ * the legacy default stream. rts_graph_launch replays it on that stream (the
+ * pointers captured must stay valid); device errors are read with rts_check
+ * on the handle. */
+typedef struct rts_graph rts_graph;
+rts_status rts_graph_create(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                            void *I_top, double *J, double *F, double *Q_rad, rts_graph **g);
+rts_status rts_graph_launch(rts_graph *g);
+void rts_graph_destroy(rts_graph *g);
+
+/* Tile-size autotuner: for rows per tile 1, 2, 3, 4 builds a batched handle
+ * for the given grids (nsub = 1 for a single grid; packed chi, S as above,
+ * device pointers), times `repeats` solves with CUDA events on opt->stream
+ * after one warm-up, and returns the fastest in *best_tile_rows and every
+ * candidate's mean milliseconds in ms[0..3] (-1 where a size does not fit).
+ * Allocates and frees device memory and synchronises: a set-up step. */
+rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, const rts_quadrature *q,
+                        const rts_options *opt, const void *chi, const void *S, int repeats,
+                        int *best_tile_rows, float ms[4]);
+
+/* ---------------------------------------------------------------------------
  * Forward solve without any memory allocation. The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
  * code that runs while an enclosing application is capturing a CUDA graph,

@@ -56,7 +56,9 @@ _lib = None
 
 # every symbol include/rts.h declares
 EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "rts_check",
-           "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint")
+           "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint",
+           "rts_create_batched", "rts_solve_batched", "rts_batched_layout", "rts_graph_create", "rts_graph_launch",
+           "rts_graph_destroy", "rts_autotune")
 
 
 def library_path() -> str:
@@ -84,6 +86,23 @@ def load(build_if_missing: bool = True):
         getattr(L, f).restype = C.c_int
     L.rts_adjoint.argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp, vp, vp]
     L.rts_adjoint.restype = C.c_int
+    L.rts_create_batched.argtypes = [C.POINTER(C.c_void_p), C.c_int, C.POINTER(Grid), C.c_int,
+                                     C.POINTER(Quadrature), C.POINTER(Options)]
+    L.rts_create_batched.restype = C.c_int
+    L.rts_solve_batched.argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp]
+    L.rts_solve_batched.restype = C.c_int
+    ll = C.POINTER(C.c_longlong)
+    L.rts_batched_layout.argtypes = [vp, C.c_int, ll, ll, ll, ll]
+    L.rts_batched_layout.restype = C.c_int
+    L.rts_graph_create.argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp, C.POINTER(C.c_void_p)]
+    L.rts_graph_create.restype = C.c_int
+    L.rts_graph_launch.argtypes = [vp]
+    L.rts_graph_launch.restype = C.c_int
+    L.rts_graph_destroy.argtypes = [vp]
+    L.rts_graph_destroy.restype = None
+    L.rts_autotune.argtypes = [C.c_int, C.POINTER(Grid), C.c_int, C.POINTER(Quadrature), C.POINTER(Options), vp, vp,
+                               C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    L.rts_autotune.restype = C.c_int
     L.rts_check.argtypes = [vp]
     L.rts_check.restype = C.c_int
     L.rts_get_stats.argtypes = [vp, C.POINTER(Stats)]
@@ -250,6 +269,20 @@ class Solver:
         del keep
         return out
 
+    def graph(self, chi, S, bottom="equal_s", top="zero", out=None):
+        """Capture one solve with these tensors in a CUDA graph (rts_graph_create).
+        The solver's stream must not be the legacy default stream. Returns
+        (Graph, out); Graph.launch() replays it."""
+        torch = self.torch
+        if out is None:
+            dev = chi.device
+            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=self.dtype, device=dev),
+                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        b, keep = self._bc(bottom, top)
+        return Graph(self, self._L.rts_graph_create, (chi.contiguous(), S.contiguous()), b, out, keep), out
+
     def solve_host(self, chi, S, bottom="equal_s", top="zero", out=None):
         """Host (numpy) inputs and outputs; the library copies both ways."""
         import numpy as np
@@ -276,6 +309,157 @@ class Solver:
         rc = self._L.rts_get_stats(self._h, C.byref(s))
         self._err(rc)
         return {k: getattr(s, k) for k, _ in Stats._fields_ if k != "device_status"}
+
+
+class Graph:
+    """A captured solve (rts_graph_*); keeps its tensors alive."""
+
+    def __init__(self, solver, create, inputs, bc, out, keep):
+        self.solver = solver
+        self._keep = (inputs, out, keep, bc)
+        g = C.c_void_p()
+        rc = create(solver._h, _ptr(inputs[0]), _ptr(inputs[1]), C.byref(bc), _ptr(out.get("I_top")),
+                    _ptr(out.get("J")), _ptr(out.get("F")), _ptr(out.get("Q")), C.byref(g))
+        solver._err(rc)
+        self._g = g
+
+    def launch(self):
+        rc = self.solver._L.rts_graph_launch(self._g)
+        self.solver._err(rc)
+
+    def __del__(self):
+        try:
+            if self._g and self._g.value:
+                self.solver._L.rts_graph_destroy(self._g)
+                self._g = C.c_void_p()
+        except Exception:
+            pass
+
+
+def _grids(shapes, spacing):
+    arr = (Grid * len(shapes))()
+    for i, (nx, ny, nz) in enumerate(shapes):
+        dx, dy, dz = spacing[i] if spacing is not None else (1.0, 1.0, 1.0)
+        arr[i] = Grid(nx, ny, nz, dx, dy, dz)
+    return arr
+
+
+class BatchedSolver(Solver):
+    """Many grids of uneven size x nbands bands in one persistent launch
+    (rts_create_batched / rts_solve_batched).
+
+    shapes: list of (nx, ny, nz); spacing: optional list of (dx, dy, dz).
+    Inputs and outputs are packed 1-D tensors (see pack / unpack)."""
+
+    def __init__(self, shapes, nbands=1, spacing=None, precision="fp32", tau_switch=0.1, wrap_tol=0.0,
+                 max_wrap_iters=64, tile_rows=0, timeout_s=2.0, timing=False, stream=None):
+        import torch
+
+        L = load()
+        self.torch = torch
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        self.nbands = nbands
+        self.precision = precision
+        self.prec = _PREC[precision]
+        self.dtype = torch.float64 if self.prec == FP64 else torch.float32
+        o = Options()
+        L.rts_default_options(C.byref(o))
+        o.prec = self.prec
+        o.tau_switch = tau_switch
+        o.wrap_tol = wrap_tol
+        o.max_wrap_iters = max_wrap_iters
+        o.tile_rows = tile_rows
+        o.timeout_s = timeout_s
+        o.flags = FLAG_TIMING if timing else 0
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o.stream = C.c_void_p(stream.cuda_stream)
+        self._opt = o
+        self._gr = _grids(self.shapes, spacing)
+        h = C.c_void_p()
+        rc = L.rts_create_batched(C.byref(h), len(self.shapes), self._gr, nbands, None, C.byref(o))
+        self._h = h
+        self._L = L
+        if rc != RTS_OK:
+            msg = L.rts_last_error(h).decode() if h.value else "rts_create_batched failed"
+            L.rts_destroy(h)
+            self._h = C.c_void_p()
+            raise RTSError(rc, msg)
+        self.n_up = L.rts_num_up(h)
+        self.offsets = []
+        tot = (C.c_longlong * 3)()
+        for i in range(len(self.shapes)):
+            a, b, c = C.c_longlong(), C.c_longlong(), C.c_longlong()
+            self._err(L.rts_batched_layout(h, i, C.byref(a), C.byref(b), C.byref(c), tot))
+            self.offsets.append((a.value, b.value, c.value))
+        self.totals = tuple(tot)
+
+    def pack(self, arrays):
+        """List of per-subdomain [B, nz, ny, nx] tensors -> one packed tensor."""
+        return self.torch.cat([a.reshape(-1) for a in arrays])
+
+    def unpack(self, out):
+        """Packed outputs -> list of per-subdomain dicts of views."""
+        res = []
+        for (nx, ny, nz), (go, to, po) in zip(self.shapes, self.offsets):
+            n = nx * ny * nz
+            res.append(dict(I_top=out["I_top"][to:to + self.nbands * self.n_up * nx * ny].view(self.nbands, self.n_up, ny, nx),
+                            J=out["J"][po:po + n].view(nz, ny, nx), F=out["F"][3 * po:3 * po + 3 * n].view(3, nz, ny, nx),
+                            Q=out["Q"][po:po + n].view(nz, ny, nx)))
+        return res
+
+    def empty_outputs(self, device):
+        torch = self.torch
+        return dict(I_top=torch.empty(self.totals[1], dtype=self.dtype, device=device),
+                    J=torch.empty(self.totals[2], dtype=torch.float64, device=device),
+                    F=torch.empty(3 * self.totals[2], dtype=torch.float64, device=device),
+                    Q=torch.empty(self.totals[2], dtype=torch.float64, device=device))
+
+    def solve(self, chi, S, bottom="equal_s", top="zero", check=True, out=None):
+        """chi, S: packed CUDA tensors of totals[0] elements. Returns packed outputs."""
+        assert chi.numel() == self.totals[0] and S.numel() == self.totals[0], (chi.numel(), self.totals)
+        assert chi.dtype == self.dtype and S.dtype == self.dtype and chi.is_cuda and S.is_cuda
+        if out is None:
+            out = self.empty_outputs(chi.device)
+        b, keep = self._bc(bottom, top)
+        rc = self._L.rts_solve_batched(self._h, _ptr(chi.contiguous()), _ptr(S.contiguous()), C.byref(b),
+                                       _ptr(out.get("I_top")), _ptr(out.get("J")), _ptr(out.get("F")),
+                                       _ptr(out.get("Q")))
+        self._err(rc)
+        if check:
+            self.check()
+        del keep
+        return out
+
+    def graph(self, chi, S, bottom="equal_s", top="zero", out=None):
+        if out is None:
+            out = self.empty_outputs(chi.device)
+        b, keep = self._bc(bottom, top)
+        return Graph(self, self._L.rts_graph_create, (chi.contiguous(), S.contiguous()), b, out, keep), out
+
+
+def autotune(shapes, nbands, chi, S, precision="fp32", spacing=None, repeats=3, stream=None, **opts):
+    """rts_autotune: fastest rows per sweep tile for these grids (packed chi,
+    S as for BatchedSolver). Returns (best_tile_rows, {rows: ms})."""
+    import torch
+
+    L = load()
+    o = Options()
+    L.rts_default_options(C.byref(o))
+    o.prec = _PREC[precision]
+    for k, v in opts.items():
+        setattr(o, k, v)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o.stream = C.c_void_p(stream.cuda_stream)
+    gr = _grids([tuple(s) for s in shapes], spacing)
+    best = C.c_int()
+    ms = (C.c_float * 4)()
+    rc = L.rts_autotune(len(shapes), gr, nbands, None, C.byref(o), _ptr(chi), _ptr(S), repeats, C.byref(best), ms)
+    if rc != RTS_OK:
+        raise RTSError(rc, "autotune found no runnable tile size")
+    return best.value, {r + 1: ms[r] for r in range(4) if ms[r] >= 0}
 
 
 def solve_noalloc(chi, S, precision="fp32", dx=1.0, dy=1.0, dz=1.0, out=None, stream=None):

@@ -171,9 +171,9 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     const bool wrap = Ug->wrap != 0, qper = Ug->qper != 0;
     const int band = Ug->band, unx = Ug->nx, uny = Ug->ny;
     const long long sQ = Ug->sQ, sM = Ug->sM, N = Ug->N;
-    const T *__restrict__ chi = (Ug->transposed ? a.chiT : a.chi) + (long long)band * N;
+    const T *__restrict__ chi = (Ug->transposed ? a.chiT : a.chi) + Ug->in_off;
     const T *__restrict__ l0 = (Ug->transposed ? a.lam0T : a.lam0) + (long long)band * 4 * N;
-    const T *const gitop = a.gitop ? a.gitop + (long long)band * a.n_up * uny * unx : nullptr;
+    const T *const gitop = a.gitop ? a.gitop + Ug->top_off : nullptr;
     T *const lstore = a.store + (long long)(uidx - a.unit_base) * 4 * N;
     const long long tile_stride = (long long)2 * 2 * HALO_CH * NP;
     T *const halo_base = a.halo + Ug->halo_off;
@@ -500,8 +500,8 @@ __global__ void __launch_bounds__(128) adj_pass1_kernel(GradArgs<T> g, int maxNM
     const int p = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
     if (m >= NM || q >= NQ || p >= NP) return;
     const long long N = U.N, sQ = U.sQ, sM = U.sM;
-    const T *chi = (U.transposed ? g.chiT : g.chi) + (long long)U.band * N;
-    const T *S = (U.transposed ? g.ST : g.S) + (long long)U.band * N;
+    const T *chi = (U.transposed ? g.chiT : g.chi) + U.in_off;
+    const T *S = (U.transposed ? g.ST : g.S) + U.in_off;
     const T *I = g.I + (long long)uu * 4 * N;
     T *LB = g.LB + (long long)uu * 4 * N;
     T *C = g.C + (long long)uu * 4 * N;

@@ -16,16 +16,14 @@
 
 namespace rts {
 
-// out[b][i][k][j] = in[b][k][j][i]
+// out[b][i][k][j] = in[b][k][j][i] for the 32 x 32 (i, j) tile at (i0, j0)
+// of level k of band b
 template <typename T>
-__global__ void __launch_bounds__(256) transpose_x_kernel(const T *__restrict__ in, T *__restrict__ out,
-                                                            int nx, int ny, int nz)
+__device__ __forceinline__ void transpose_tile(const T *__restrict__ in, T *__restrict__ out, int nx, int ny, int nz,
+                                               int i0, int j0, long long b, long long k)
 {
     __shared__ T tile[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-    const long long bk = blockIdx.z;
-    const long long b = bk / nz, k = bk % nz;
     const T *src = in + (b * nz + k) * (long long)ny * nx;
     for (int jj = ty; jj < 32; jj += 8) {
         const int i = i0 + tx, j = j0 + jj;
@@ -36,6 +34,14 @@ __global__ void __launch_bounds__(256) transpose_x_kernel(const T *__restrict__ 
         const int i = i0 + ii, j = j0 + tx;
         if (i < nx && j < ny) out[((b * nx + i) * nz + k) * (long long)ny + j] = tile[tx][ii];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_x_kernel(const T *__restrict__ in, T *__restrict__ out,
+                                                            int nx, int ny, int nz)
+{
+    const long long bk = blockIdx.z;
+    transpose_tile(in, out, nx, ny, nz, blockIdx.x * 32, blockIdx.y * 32, bk / nz, bk % nz);
 }
 
 struct RedUnit {
@@ -73,17 +79,15 @@ __device__ __forceinline__ df32 part_out(const PartSum<float> &s, df32 *) { retu
 // layout are read along i; units of the x groups, stored [i][k][j], are read
 // along j into a shared tile and summed transposed, so every global read is
 // coalesced.
+// sums for the 32 x 32 (i, j) tile at (i0, j0) of level k, units u0..u1-1 of
+// one band, into JFb = JF of that band ([4][N])
 template <typename T, typename Acc>
-__global__ void __launch_bounds__(256) reduce_units_kernel(const RedUnit *__restrict__ ru,
-                                                            const int *__restrict__ ru_begin,
-                                                            Acc *__restrict__ JF, int nx, int ny, int nz)
+__device__ __forceinline__ void reduce_tile(const RedUnit *__restrict__ ru, int u0, int u1, Acc *__restrict__ JFb,
+                                            int nx, int ny, int nz, int i0, int j0, int k)
 {
     __shared__ PartSum<T> tile[4][32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
-    const int b = blockIdx.z / nz, k = blockIdx.z % nz;
     const long long N = (long long)nx * ny * nz;
-    const int u0 = ru_begin[b], u1 = ru_begin[b + 1];
     // transposed units: tile[c][i - i0][j - j0]
     for (int c = 0; c < 4; ++c)
         for (int jj = ty; jj < 32; jj += 8) tile[c][jj][tx] = PartSum<T>();
@@ -110,8 +114,19 @@ __global__ void __launch_bounds__(256) reduce_units_kernel(const RedUnit *__rest
             const T *pn = (const T *)ru[u].partial;
             for (int c = 0; c < 4; ++c) s[c].add(pn[c * N + noff]);
         }
-        for (int c = 0; c < 4; ++c) JF[((long long)b * 4 + c) * N + noff] = part_out(s[c], (Acc *)nullptr);
+        for (int c = 0; c < 4; ++c) JFb[c * N + noff] = part_out(s[c], (Acc *)nullptr);
     }
+}
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) reduce_units_kernel(const RedUnit *__restrict__ ru,
+                                                            const int *__restrict__ ru_begin,
+                                                            Acc *__restrict__ JF, int nx, int ny, int nz)
+{
+    const int b = blockIdx.z / nz, k = blockIdx.z % nz;
+    const long long N = (long long)nx * ny * nz;
+    reduce_tile<T, Acc>(ru, ru_begin[b], ru_begin[b + 1], JF + (long long)b * 4 * N, nx, ny, nz, blockIdx.x * 32,
+                        blockIdx.y * 32, k);
 }
 
 struct QParams {
@@ -137,15 +152,12 @@ __device__ __forceinline__ double accT(double *, double v) { return v; }
 __device__ __forceinline__ double accT(double *, float v) { return (double)v; }
 __device__ __forceinline__ df32 accT(df32 *, float v) { return df_make(v); }
 
+// Q step at point (i, j, k) of one grid (pointers at that grid's data)
 template <typename T, typename Acc>
-__global__ void __launch_bounds__(256) qstep_kernel(const Acc *__restrict__ JF, const T *__restrict__ chi,
-                                                     const T *__restrict__ S, QParams P,
-                                                     double *__restrict__ J, double *__restrict__ F,
-                                                     double *__restrict__ Q)
+__device__ __forceinline__ void qstep_point(const Acc *__restrict__ JF, const T *__restrict__ chi,
+                                            const T *__restrict__ S, const QParams &P, double *__restrict__ J,
+                                            double *__restrict__ F, double *__restrict__ Q, int i, int j, int k)
 {
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * 8 + threadIdx.y;
-    const int k = blockIdx.z;
     if (i >= P.nx || j >= P.ny) return;
     const long long nx = P.nx, ny = P.ny, nz = P.nz;
     const long long N = nx * ny * nz;
@@ -190,6 +202,16 @@ __global__ void __launch_bounds__(256) qstep_kernel(const Acc *__restrict__ JF, 
         F[2 * N + p] = acc_to_double(Fz);
     }
     if (Q) Q[p] = acc_to_double(Qt);
+}
+
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) qstep_kernel(const Acc *__restrict__ JF, const T *__restrict__ chi,
+                                                     const T *__restrict__ S, QParams P,
+                                                     double *__restrict__ J, double *__restrict__ F,
+                                                     double *__restrict__ Q)
+{
+    qstep_point<T, Acc>(JF, chi, S, P, J, F, Q, blockIdx.x * 32 + threadIdx.x, blockIdx.y * 8 + threadIdx.y,
+                        blockIdx.z);
 }
 
 }  // namespace rts

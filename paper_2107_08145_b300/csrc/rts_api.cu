@@ -23,6 +23,7 @@
 
 #include "rts.h"
 #include "adjoint.cuh"
+#include "batched.cuh"
 #include "qstep.cuh"
 #include "sweep.cuh"
 
@@ -120,6 +121,8 @@ bool plan_units(const DirGeo *geo, const int *udx, const double *n, const double
                 long long ny, long long nz, int B, int tq, rts::SweepUnit *units, int max_units, int *unit_of_tile,
                 int max_tiles, PlanOut &po)
 {
+    int n_up = 0, n_dn = 0;
+    for (int d = 0; d < ndir; ++d) (geo[d].up ? n_up : n_dn)++;
     const int keys[6][2] = {{0, 1}, {0, -1}, {1, 1}, {1, -1}, {2, 1}, {2, -1}};
     const long long N = nx * ny * nz;
     po = PlanOut();
@@ -138,6 +141,9 @@ bool plan_units(const DirGeo *geo, const int *udx, const double *n, const double
                 std::memset(&U, 0, sizeof(U));
                 U.N = N;
                 U.band = b;
+                U.in_off = (long long)b * N;
+                U.top_off = (long long)b * n_up * nx * ny;
+                U.dn_off = (long long)b * n_dn * nx * ny;
                 U.axis = k[0];
                 U.sa = k[1];
                 unit_extents(U.axis, nx, ny, nz, U.NP, U.NQ, U.NM);
@@ -210,6 +216,13 @@ struct rts_handle {
     void *d_adjI = nullptr, *d_adjL = nullptr, *d_adjC = nullptr, *d_adjG = nullptr;
     int chunk_bands = 1, chunk_units = 0, grid_adj = 0;
     std::vector<int> band_unit;   // first unit of band b (b = 0..B)
+    // batched handles (rts_create_batched): subdomain table and packed sizes
+    bool batched = false;
+    int nsub = 1;
+    std::vector<rts::SubDesc> subs;
+    rts::SubDesc *d_subs = nullptr;
+    long long in_total = 0, top_total = 0, out_total = 0, nblk[3] = {0, 0, 0};
+    bool capturing = false;
     // host-IO staging
     void *d_in_chi = nullptr, *d_in_S = nullptr, *d_out_itop = nullptr;
     double *d_out_J = nullptr, *d_out_F = nullptr, *d_out_Q = nullptr;
@@ -624,7 +637,7 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
     cudaEvent_t *ev = nullptr;
-    if (h->timing) {
+    if (h->timing && !h->capturing) {
         if (h->nrec == h->evs.size()) {
             std::array<cudaEvent_t, 5> set{};
             for (cudaEvent_t &e : set) CUDA_TRY(h, cudaEventCreate(&e));
@@ -1199,4 +1212,422 @@ extern "C" rts_status rts_solve_noalloc(const rts_grid *g, int nbands, rts_preci
         return noalloc_solve<float, rts::df32>(g, nbands, chi, S, I_top, J, F, Q_rad, st, err, errlen);
     default: noalloc_msg(err, errlen, "unknown precision %d", (int)prec); return RTS_EINVAL;
     }
+}
+
+// ===========================================================================
+// Batched solves: many independent grids of uneven size x bands in one
+// persistent sweep launch (plus one transpose, reduction and Q-step launch
+// each), CUDA-graph capture of a solve, and the tile-size autotuner.
+// ===========================================================================
+
+namespace {
+
+// expected length of a unit in planes: the periodic groups sweep about one
+// extra period of warm-up
+long long unit_weight(const rts::SweepUnit &U) { return (long long)U.NM * (U.wrap ? 2 : 1); }
+
+}  // namespace
+
+extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_grid *grids, int nbands,
+                                         const rts_quadrature *q, const rts_options *opt)
+{
+    if (!out) return RTS_EINVAL;
+    *out = nullptr;
+    rts_handle *h = new (std::nothrow) rts_handle();
+    if (!h) return RTS_ENOMEM;
+    if (opt) h->opt = *opt;
+    else rts_default_options(&h->opt);
+    rts_options &o = h->opt;
+    auto bail = [&](rts_status s) {
+        *out = h;
+        return s;
+    };
+    if (nsub < 1 || !grids || nbands < 1) return bail(fail(h, RTS_EINVAL, "need nsub >= 1, grids and nbands >= 1"));
+    for (int s = 0; s < nsub; ++s) {
+        const rts_grid &g = grids[s];
+        if (g.nx < 1 || g.ny < 1 || g.nz < 2)
+            return bail(fail(h, RTS_EINVAL, "subdomain %d: need nx, ny >= 1 and nz >= 2", s));
+        if (!(g.dx > 0 && g.dy > 0 && g.dz > 0) || !std::isfinite(g.dx) || !std::isfinite(g.dy) || !std::isfinite(g.dz))
+            return bail(fail(h, RTS_EINVAL, "subdomain %d: spacing must be finite and positive", s));
+    }
+    if (o.prec != RTS_FP64 && o.prec != RTS_FP32_MIXED && o.prec != RTS_FP32_COMPENSATED)
+        return bail(fail(h, RTS_EINVAL, "unknown precision %d", (int)o.prec));
+    if (!(o.tau_switch > 0)) return bail(fail(h, RTS_EINVAL, "tau_switch must be > 0"));
+    if (o.flags & (RTS_FLAG_ADJOINT | RTS_FLAG_HOST_IO))
+        return bail(fail(h, RTS_EINVAL, "batched handles take neither RTS_FLAG_ADJOINT nor RTS_FLAG_HOST_IO"));
+    if (o.max_wrap_iters < 1) o.max_wrap_iters = 64;
+    if (!(o.timeout_s > 0)) o.timeout_s = 2.0;
+    if (!(o.wrap_tol > 0)) o.wrap_tol = o.prec == RTS_FP64 ? 1e-15 : 0x1p-24;
+    h->batched = true;
+    h->nsub = nsub;
+    h->g = grids[0];
+    h->B = nbands;
+    h->stream = (cudaStream_t)o.stream;
+    h->esize = o.prec == RTS_FP64 ? 8 : 4;
+    if (q && q->ndir > 0) {
+        if (!q->n || !q->w) return bail(fail(h, RTS_EINVAL, "quadrature arrays are NULL"));
+        h->n.assign(q->n, q->n + 3 * q->ndir);
+        h->w.assign(q->w, q->w + q->ndir);
+    } else {
+        default_quadrature(h->n, h->w);
+    }
+    h->ndir = (int)h->w.size();
+
+    // ---- units of every subdomain (per subdomain in band-major plan order) ----
+    int npmax = 0;
+    long long maxext = 0;
+    for (int s = 0; s < nsub; ++s) {
+        npmax = std::max(npmax, std::max(grids[s].nx, grids[s].ny));
+        maxext = std::max<long long>(maxext, std::max(grids[s].nx, std::max(grids[s].ny, grids[s].nz)));
+    }
+    if (npmax > 1024) return bail(fail(h, RTS_EINVAL, "plane extent %d > 1024 is not supported", npmax));
+    const int tq = pick_tile_rows(o.tile_rows, npmax, h->esize);
+    h->tq = tq;
+    h->nt = 32 * ((npmax + 31) / 32);
+    h->smem = sweep_smem(tq, npmax, h->esize);
+    if (h->smem > 227 * 1024) return bail(fail(h, RTS_EINVAL, "tile of %d rows needs %zu B shared memory", tq, h->smem));
+
+    std::vector<rts::SweepUnit> plan;       // plan order
+    std::vector<int> plan_sub;              // subdomain of each planned unit
+    std::vector<int> ru_begin(1, 0);        // per (subdomain, band)
+    h->subs.resize(nsub);
+    const int max_units = nbands * 6 * h->ndir;
+    std::vector<rts::SweepUnit> tmp(max_units);
+    std::vector<int> tmp_uot((size_t)max_units * ((maxext + tq - 1) / tq));
+    long long in_off = 0, top_off = 0, out_off = 0, jf_off = 0, blk[3] = {0, 0, 0};
+    for (int s = 0; s < nsub; ++s) {
+        const rts_grid &g = grids[s];
+        const double hsp[3] = {g.dx, g.dy, g.dz};
+        std::vector<DirGeo> geo(h->ndir);
+        std::vector<int> udx(h->ndir);
+        int nup = 0, ndn = 0;
+        for (int d = 0; d < h->ndir; ++d) {
+            if (!direction_geometry(hsp, &h->n[3 * d], geo[d]))
+                return bail(fail(h, RTS_EINVAL, "direction %d has n_z == 0 or is zero", d));
+            udx[d] = geo[d].up ? nup++ : ndn++;
+        }
+        h->n_up = nup;
+        h->n_dn = ndn;
+        PlanOut po;
+        if (!plan_units(geo.data(), udx.data(), h->n.data(), h->w.data(), h->ndir, g.nx, g.ny, g.nz, nbands, tq,
+                        tmp.data(), max_units, tmp_uot.data(), (int)tmp_uot.size(), po))
+            return bail(fail(h, RTS_EINVAL, "subdomain %d: too many sweep units or tiles", s));
+        const long long N = (long long)g.nx * g.ny * g.nz;
+        rts::SubDesc &sd = h->subs[s];
+        std::memset(&sd, 0, sizeof(sd));
+        sd.nx = g.nx; sd.ny = g.ny; sd.nz = g.nz; sd.N = N;
+        sd.in_off = in_off; sd.top_off = top_off; sd.out_off = out_off; sd.jf_off = jf_off;
+        sd.ru0 = s * nbands;
+        for (int w = 0; w < 3; ++w) {
+            sd.blk[w] = (int)blk[w];
+            blk[w] += rts::sub_blocks(w, g.nx, g.ny, g.nz, nbands);
+        }
+        sd.P.nx = g.nx; sd.P.ny = g.ny; sd.P.nz = g.nz; sd.P.nbands = nbands;
+        sd.P.inv2dx = 0.5 / g.dx; sd.P.inv2dy = 0.5 / g.dy; sd.P.inv2dz = 0.5 / g.dz; sd.P.invdz = 1.0 / g.dz;
+        sd.P.thin = std::min(g.dx, std::min(g.dy, g.dz)) / o.tau_switch;
+        for (int u = 0; u < po.nunits; ++u) {
+            rts::SweepUnit U = tmp[u];
+            U.in_off += in_off;
+            U.top_off += top_off;
+            U.dn_off = 0;  // explicit boundary arrays are not taken by batched solves
+            plan.push_back(U);
+            plan_sub.push_back(s);
+        }
+        // units of (s, b) in plan order
+        std::vector<int> cnt(nbands, 0);
+        for (int u = 0; u < po.nunits; ++u) cnt[tmp[u].band]++;
+        for (int b = 0; b < nbands; ++b) ru_begin.push_back(ru_begin.back() + cnt[b]);
+        in_off += (long long)nbands * N;
+        top_off += (long long)nbands * nup * g.nx * g.ny;
+        out_off += N;
+        jf_off += (long long)nbands * 4 * N;
+        h->has_x = h->has_x || po.has_x;
+    }
+    if (blk[0] > 0x7fffffffLL || blk[1] > 0x7fffffffLL || blk[2] > 0x7fffffffLL)
+        return bail(fail(h, RTS_EINVAL, "batch too large for one launch of the per-grid kernels"));
+    h->in_total = in_off;
+    h->top_total = top_off;
+    h->out_total = out_off;
+    for (int w = 0; w < 3; ++w) h->nblk[w] = blk[w];
+
+    // ---- sweep order: longest units first (tickets are handed out in this order) ----
+    const int nunits = (int)plan.size();
+    std::vector<int> order(nunits);
+    for (int u = 0; u < nunits; ++u) order[u] = u;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return unit_weight(plan[a]) > unit_weight(plan[b]); });
+    std::vector<int> pos(nunits);
+    h->units.resize(nunits);
+    h->unit_of_tile.clear();
+    long long halo = 0, part_elems = 0;
+    std::vector<long long> part_off(nunits);
+    for (int k = 0; k < nunits; ++k) {
+        rts::SweepUnit U = plan[order[k]];
+        pos[order[k]] = k;
+        U.tile0 = (int)h->unit_of_tile.size();
+        for (int t = 0; t < U.ntiles; ++t) h->unit_of_tile.push_back(k);
+        U.halo_off = halo;
+        halo += (long long)U.ntiles * 4 * rts::HALO_CH * U.NP;
+        part_off[k] = part_elems;
+        part_elems += 4 * U.N;
+        h->max_ntiles = std::max(h->max_ntiles, U.ntiles);
+        h->units[k] = U;
+    }
+    h->total_tiles = (int)h->unit_of_tile.size();
+    int R = 8;
+    while (R < 2 * (h->max_ntiles + kLag + 2)) R *= 2;
+    h->R = R;
+
+    int dev = 0, nsm = 0, blocks = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    cudaError_t oe = o.prec == RTS_FP64 ? occupancy<double>(h, &blocks) : occupancy<float>(h, &blocks);
+    if (oe != cudaSuccess) return bail(fail(h, RTS_ECUDA, "occupancy query: %s", cudaGetErrorString(oe)));
+    h->grid = std::min(h->total_tiles, blocks * nsm);
+    if (blocks < 1 || h->grid < h->max_ntiles)
+        return bail(fail(h, RTS_EINVAL, "a sweep unit has %d tiles but only %d CTAs fit on the GPU", h->max_ntiles,
+                         blocks * nsm));
+
+    // ---- device memory ----
+    const size_t es = h->esize;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = round_up(off + bytes, 256); return at; };
+    const size_t o_units = take(sizeof(rts::SweepUnit) * nunits);
+    const size_t o_uot = take(sizeof(int) * h->unit_of_tile.size());
+    const size_t o_part = take((size_t)part_elems * es);
+    const size_t o_chiT = h->has_x ? take((size_t)h->in_total * es) : 0;
+    const size_t o_ST = h->has_x ? take((size_t)h->in_total * es) : 0;
+    const size_t o_JF = take((size_t)jf_off * 8);
+    const size_t o_halo = take((size_t)halo * es);
+    const size_t o_flags = take(sizeof(int) * h->total_tiles);
+    const size_t o_gcnt = take(sizeof(unsigned int) * nunits * R);
+    const size_t o_gmax = take(sizeof(unsigned long long) * nunits * R);
+    const size_t o_ticket = take(sizeof(int) * 4);
+    const size_t o_status = take(sizeof(int) * 4);
+    const size_t o_tacc = take(sizeof(int) * nunits);
+    const size_t o_ru = take(sizeof(rts::RedUnit) * nunits);
+    const size_t o_rub = take(sizeof(int) * ru_begin.size());
+    const size_t o_subs = take(sizeof(rts::SubDesc) * nsub);
+    cudaError_t ae = cudaMalloc(&h->dmem, off);
+    if (ae != cudaSuccess) {
+        h->dmem = nullptr;
+        return bail(fail(h, RTS_ENOMEM, "cudaMalloc of %zu bytes: %s", off, cudaGetErrorString(ae)));
+    }
+    char *base = (char *)h->dmem;
+    h->d_units = (rts::SweepUnit *)(base + o_units);
+    h->d_unit_of_tile = (int *)(base + o_uot);
+    h->d_partial = base + o_part;
+    h->d_chiT = h->has_x ? base + o_chiT : nullptr;
+    h->d_ST = h->has_x ? base + o_ST : nullptr;
+    h->d_JF = base + o_JF;
+    h->d_halo = base + o_halo;
+    h->d_flags = (int *)(base + o_flags);
+    h->d_gcnt = (unsigned int *)(base + o_gcnt);
+    h->d_gmax = (unsigned long long *)(base + o_gmax);
+    h->d_ticket = (int *)(base + o_ticket);
+    h->d_status = (int *)(base + o_status);
+    h->d_unit_tacc = (int *)(base + o_tacc);
+    h->d_ru = (rts::RedUnit *)(base + o_ru);
+    h->d_ru_begin = (int *)(base + o_rub);
+    h->d_subs = (rts::SubDesc *)(base + o_subs);
+    std::vector<rts::RedUnit> ru(nunits);
+    for (int k = 0; k < nunits; ++k) h->units[k].partial = (char *)h->d_partial + part_off[k] * es;
+    for (int u = 0; u < nunits; ++u) {  // reduction table in plan order: (subdomain, band), then group
+        ru[u].partial = h->units[pos[u]].partial;
+        ru[u].axis = plan[u].axis;
+    }
+    CUDA_TRY(h, cudaMemcpy(h->d_units, h->units.data(), sizeof(rts::SweepUnit) * nunits, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_unit_of_tile, h->unit_of_tile.data(), sizeof(int) * h->unit_of_tile.size(),
+                           cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * nunits, cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, ru_begin.data(), sizeof(int) * ru_begin.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(h, cudaMemcpy(h->d_subs, h->subs.data(), sizeof(rts::SubDesc) * nsub, cudaMemcpyHostToDevice));
+    h->band_unit.assign(1, 0);
+    h->timing = (o.flags & RTS_FLAG_TIMING) != 0;
+    *out = h;
+    return RTS_OK;
+}
+
+template <typename T, typename Acc>
+static rts_status solve_batched_impl(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                                     void *I_top, double *J, double *F, double *Q)
+{
+    cudaStream_t st = h->stream;
+    const int ns = h->nsub;
+    CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
+    rts_status rs = reset_sweep_state(h, st);
+    if (rs) return rs;
+    cudaEvent_t *ev = nullptr;
+    if (h->timing && !h->capturing) {
+        if (h->nrec == h->evs.size()) {
+            std::array<cudaEvent_t, 5> set{};
+            for (cudaEvent_t &e : set) CUDA_TRY(h, cudaEventCreate(&e));
+            h->evs.push_back(set);
+        }
+        ev = h->evs[h->nrec++].data();
+        CUDA_TRY(h, cudaEventRecord(ev[0], st));
+    }
+    int kernels = 0;
+    if (h->has_x) {
+        rts::transpose_x_batched<T><<<(unsigned)h->nblk[0], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->B, (const T *)chi,
+                                                                                 (T *)h->d_chiT);
+        rts::transpose_x_batched<T><<<(unsigned)h->nblk[0], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->B, (const T *)S,
+                                                                                 (T *)h->d_ST);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 2;
+    }
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev[1], st));
+    rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
+    a.itop = (T *)I_top;
+    cudaError_t e = launch_sweep<T>(h, a);
+    if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+    kernels += 1;
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
+    if (J || F || Q) {
+        rts::reduce_units_batched<T, Acc><<<(unsigned)h->nblk[1], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->d_ru,
+                                                                                       h->d_ru_begin, (Acc *)h->d_JF);
+        if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
+        rts::qstep_batched<T, Acc><<<(unsigned)h->nblk[2], dim3(32, 8), 0, st>>>(
+            h->d_subs, ns, (const Acc *)h->d_JF, (const T *)chi, (const T *)S, J, F, Q);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 2;
+    } else if (ev) {
+        CUDA_TRY(h, cudaEventRecord(ev[3], st));
+    }
+    if (ev) CUDA_TRY(h, cudaEventRecord(ev[4], st));
+    h->kernels_last = kernels;
+    return RTS_OK;
+}
+
+extern "C" rts_status rts_solve_batched(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                                        void *I_top, double *J, double *F, double *Q)
+{
+    if (!h || !h->dmem) return h ? fail(h, RTS_EINVAL, "handle was not created successfully") : RTS_EINVAL;
+    if (!h->batched) return fail(h, RTS_EINVAL, "rts_solve_batched needs a handle from rts_create_batched");
+    if (!chi || !S) return fail(h, RTS_EINVAL, "chi and S must not be NULL");
+    if (bc && (bc->bottom == RTS_BC_EXPLICIT || bc->top == RTS_BC_EXPLICIT))
+        return fail(h, RTS_EINVAL, "batched solves take boundary kinds ZERO and EQUAL_S only");
+    rts_status s = check_bc(h, bc);
+    if (s) return s;
+    switch (h->opt.prec) {
+    case RTS_FP64: return solve_batched_impl<double, double>(h, chi, S, bc, I_top, J, F, Q);
+    case RTS_FP32_MIXED: return solve_batched_impl<float, double>(h, chi, S, bc, I_top, J, F, Q);
+    default: return solve_batched_impl<float, rts::df32>(h, chi, S, bc, I_top, J, F, Q);
+    }
+}
+
+extern "C" rts_status rts_batched_layout(rts_handle *h, int sub, long long *grid_offset, long long *top_offset,
+                                         long long *point_offset, long long totals[3])
+{
+    if (!h || !h->dmem || !h->batched) return h ? fail(h, RTS_EINVAL, "not a batched handle") : RTS_EINVAL;
+    if (sub < 0 || sub >= h->nsub) return fail(h, RTS_EINVAL, "subdomain %d out of range", sub);
+    const rts::SubDesc &sd = h->subs[sub];
+    if (grid_offset) *grid_offset = sd.in_off;
+    if (top_offset) *top_offset = sd.top_off;
+    if (point_offset) *point_offset = sd.out_off;
+    if (totals) {
+        totals[0] = h->in_total;
+        totals[1] = h->top_total;
+        totals[2] = h->out_total;
+    }
+    return RTS_OK;
+}
+
+// ---- CUDA graph of one solve ----------------------------------------------
+struct rts_graph {
+    rts_handle *h = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" rts_status rts_graph_create(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                                       void *I_top, double *J, double *F, double *Q, rts_graph **out)
+{
+    if (!h || !h->dmem || !out) return h ? fail(h, RTS_EINVAL, "bad arguments") : RTS_EINVAL;
+    *out = nullptr;
+    if (!h->stream) return fail(h, RTS_EINVAL, "graph capture needs a handle created with a non-default stream");
+    rts_graph *g = new (std::nothrow) rts_graph();
+    if (!g) return RTS_ENOMEM;
+    g->h = h;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    rts_status s = h->batched ? rts_solve_batched(h, chi, S, bc, I_top, J, F, Q) : rts_solve(h, chi, S, bc, I_top, J, F, Q);
+    h->capturing = false;
+    cudaError_t ce = cudaStreamEndCapture(h->stream, &g->graph);
+    if (s != RTS_OK || ce != cudaSuccess) {
+        if (g->graph) cudaGraphDestroy(g->graph);
+        delete g;
+        return s != RTS_OK ? s : fail(h, RTS_ECUDA, "stream capture: %s", cudaGetErrorString(ce));
+    }
+    ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(g->graph);
+        delete g;
+        return fail(h, RTS_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+    }
+    *out = g;
+    return RTS_OK;
+}
+
+extern "C" rts_status rts_graph_launch(rts_graph *g)
+{
+    if (!g || !g->exec) return RTS_EINVAL;
+    CUDA_TRY(g->h, cudaGraphLaunch(g->exec, g->h->stream));
+    return RTS_OK;
+}
+
+extern "C" void rts_graph_destroy(rts_graph *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    delete g;
+}
+
+// ---- tile-size autotuner --------------------------------------------------
+extern "C" rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, const rts_quadrature *q,
+                                   const rts_options *opt, const void *chi, const void *S, int repeats,
+                                   int *best_tile_rows, float ms[4])
+{
+    if (nsub < 1 || !grids || !chi || !S || !best_tile_rows) return RTS_EINVAL;
+    rts_options o;
+    if (opt) o = *opt;
+    else rts_default_options(&o);
+    o.flags &= ~(RTS_FLAG_TIMING | RTS_FLAG_ADJOINT | RTS_FLAG_HOST_IO);
+    const int reps = std::max(1, repeats);
+    float best = 0.f;
+    *best_tile_rows = 0;
+    for (int c = 0; c < 4; ++c) {
+        const int tq = kTileRows[3 - c];  // 1, 2, 3, 4
+        if (ms) ms[c] = -1.f;
+        o.tile_rows = tq;
+        rts_handle *h = nullptr;
+        rts_status s = rts_create_batched(&h, nsub, grids, nbands, q, &o);
+        if (s != RTS_OK || !h || h->tq != tq) {
+            rts_destroy(h);
+            continue;
+        }
+        cudaStream_t st = h->stream;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        bool ok = cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+        ok = ok && rts_solve_batched(h, chi, S, nullptr, nullptr, nullptr, nullptr, nullptr) == RTS_OK;
+        ok = ok && cudaEventRecord(e0, st) == cudaSuccess;
+        for (int r = 0; ok && r < reps; ++r)
+            ok = rts_solve_batched(h, chi, S, nullptr, nullptr, nullptr, nullptr, nullptr) == RTS_OK;
+        ok = ok && cudaEventRecord(e1, st) == cudaSuccess && rts_check(h) == RTS_OK;
+        float t = 0.f;
+        ok = ok && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        rts_destroy(h);
+        if (!ok) continue;
+        t /= reps;
+        if (ms) ms[c] = t;
+        if (*best_tile_rows == 0 || t < best) {
+            best = t;
+            *best_tile_rows = tq;
+        }
+    }
+    return *best_tile_rows ? RTS_OK : RTS_ECUDA;
 }

@@ -58,6 +58,9 @@ struct SweepUnit {
     void *partial;              // [4][N] J, Fx, Fy, Fz of this unit, unit layout
     long long sQ, sM, N;        // strides of Q and M (elements), points
     long long halo_off;         // element offset of tile 0's halo block
+    long long in_off;           // offset of this unit's band in chi, S (and their x-transposed copies)
+    long long top_off;          // offset of this unit's band in I_top and the explicit bottom intensities
+    long long dn_off;           // offset of this unit's band in the explicit top intensities
     int band, transposed;       // band index; reads the x-transposed copy
     int NP, NQ, NM;
     int axis, sa, wrap, qper;
@@ -170,8 +173,7 @@ __device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U,
     int i, j;
     natural_ij(U.axis, p, q, m, i, j);
     const long long plane = (long long)U.ny * U.nx;
-    const T *arr = D.up[d] ? a.bc_up + (long long)U.band * a.n_up * plane
-                           : a.bc_dn + (long long)U.band * a.n_dn * plane;
+    const T *arr = D.up[d] ? a.bc_up + U.top_off : a.bc_dn + U.dn_off;
     return arr[(long long)D.udx[d] * plane + (long long)j * U.nx + i];
 }
 
@@ -217,11 +219,11 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const int NP = Ug->NP, NQ = Ug->NQ, NM = Ug->NM;
     const int axis = Ug->axis, sa = Ug->sa, ntl = Ug->ntiles, tile0 = Ug->tile0;
     const bool wrap = Ug->wrap != 0, qper = Ug->qper != 0;
-    const int band = Ug->band, unx = Ug->nx, uny = Ug->ny;
+    const int unx = Ug->nx, uny = Ug->ny;
     const long long sQ = Ug->sQ, sM = Ug->sM, N = Ug->N;
-    const T *__restrict__ chi = (Ug->transposed ? a.chiT : a.chi) + (long long)band * N;
-    const T *__restrict__ Sg = (Ug->transposed ? a.ST : a.S) + (long long)band * N;
-    T *const itop = a.itop ? a.itop + (long long)band * a.n_up * uny * unx : nullptr;
+    const T *__restrict__ chi = (Ug->transposed ? a.chiT : a.chi) + Ug->in_off;
+    const T *__restrict__ Sg = (Ug->transposed ? a.ST : a.S) + Ug->in_off;
+    T *const itop = a.itop ? a.itop + Ug->top_off : nullptr;
     T *const part = (T *)Ug->partial;
     const long long tile_stride = (long long)2 * 2 * HALO_CH * NP;
     T *const halo_base = a.halo + Ug->halo_off;

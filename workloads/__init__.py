@@ -10,4 +10,5 @@ from .atmosphere import (  # noqa: F401
     WORKLOADS,
     workload,
     batched_subdomain_shapes,
+    batched_bands,
 )
