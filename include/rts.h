@@ -232,15 +232,17 @@ rts_status rts_graph_create(rts_handle *h, const void *chi, const void *S, const
 rts_status rts_graph_launch(rts_graph *g);
 void rts_graph_destroy(rts_graph *g);
 
-/* Tile-size autotuner: for rows per tile 1, 2, 3, 4 builds a batched handle
- * for the given grids (nsub = 1 for a single grid; packed chi, S as above,
- * device pointers), times `repeats` solves with CUDA events on opt->stream
- * after one warm-up, and returns the fastest in *best_tile_rows and every
- * candidate's mean milliseconds in ms[0..3] (-1 where a size does not fit).
- * Allocates and frees device memory and synchronises: a set-up step. */
+/* Tile-size autotuner: for every tile height the library instantiates for
+ * these plane extents (1, 2, 4, 6, 7, 8, 12, 16 rows, where the tile fits) builds a
+ * batched handle for the given grids (nsub = 1 for a single grid; packed chi,
+ * S as above, device pointers), times `repeats` solves with CUDA events on
+ * opt->stream after one warm-up, and returns the fastest in *best_tile_rows;
+ * the *ncand candidates timed and their mean milliseconds go to rows[] and
+ * ms[] (up to 8). Allocates and frees device memory and synchronises: a
+ * set-up step, not for the hot path. */
 rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, const rts_quadrature *q,
                         const rts_options *opt, const void *chi, const void *S, int repeats,
-                        int *best_tile_rows, float ms[4]);
+                        int *best_tile_rows, int *ncand, int rows[8], float ms[8]);
 
 /* ---------------------------------------------------------------------------
  * Forward solve without any memory allocation. The paper has no counterpart:

@@ -101,7 +101,8 @@ def load(build_if_missing: bool = True):
     L.rts_graph_destroy.argtypes = [vp]
     L.rts_graph_destroy.restype = None
     L.rts_autotune.argtypes = [C.c_int, C.POINTER(Grid), C.c_int, C.POINTER(Quadrature), C.POINTER(Options), vp, vp,
-                               C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_float)]
+                               C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                               C.POINTER(C.c_float)]
     L.rts_autotune.restype = C.c_int
     L.rts_check.argtypes = [vp]
     L.rts_check.restype = C.c_int
@@ -454,12 +455,14 @@ def autotune(shapes, nbands, chi, S, precision="fp32", spacing=None, repeats=3, 
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream)
     gr = _grids([tuple(s) for s in shapes], spacing)
-    best = C.c_int()
-    ms = (C.c_float * 4)()
-    rc = L.rts_autotune(len(shapes), gr, nbands, None, C.byref(o), _ptr(chi), _ptr(S), repeats, C.byref(best), ms)
+    best, n = C.c_int(), C.c_int()
+    rows = (C.c_int * 8)()
+    ms = (C.c_float * 8)()
+    rc = L.rts_autotune(len(shapes), gr, nbands, None, C.byref(o), _ptr(chi), _ptr(S), repeats, C.byref(best),
+                        C.byref(n), rows, ms)
     if rc != RTS_OK:
         raise RTSError(rc, "autotune found no runnable tile size")
-    return best.value, {r + 1: ms[r] for r in range(4) if ms[r] >= 0}
+    return best.value, {rows[i]: ms[i] for i in range(n.value)}
 
 
 def solve_noalloc(chi, S, precision="fp32", dx=1.0, dy=1.0, dz=1.0, out=None, stream=None):

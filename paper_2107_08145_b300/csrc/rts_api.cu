@@ -194,8 +194,16 @@ struct rts_handle {
 
     std::vector<rts::SweepUnit> units;
     std::vector<int> unit_of_tile;
-    int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, nt = 32, tq = 0;
+    int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, nt = 32, tq = 0, maxt = 0;  // maxt: register cap
     size_t smem = 0;
+    // reverse sweep: the same units tiled for the adjoint kernel
+    std::vector<rts::SweepUnit> adj_units;
+    std::vector<int> adj_unit_of_tile;
+    rts::SweepUnit *d_adj_units = nullptr;
+    int *d_adj_uot = nullptr;
+    int adj_tq = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
+    int flag_tiles = 0;           // ready flags allocated (max over both tilings)
+    size_t adj_smem = 0;
     bool has_x = false;
     long long N = 0;
 
@@ -256,64 +264,135 @@ static rts_status fail(rts_handle *h, rts_status s, const char *fmt, ...)
 template <typename T>
 using SweepFn = void (*)(rts::SweepArgs<T>);
 
-// the sweep kernel instantiated for tq rows per tile
+// Forward sweep kernels instantiated: (rows per tile, register cap per thread).
+// The caps let 2 to 4 CTAs of up to 288 threads share an SM; the last three
+// serve CTAs of up to 1024 threads (plane extents above 384).
+struct FwdCfg {
+    int tq, maxr;
+};
+static const FwdCfg kFwdCfg[] = {{16, 168}, {12, 168}, {8, 112}, {7, 112}, {6, 104}, {4, 72}, {2, 56}, {1, 56},
+                                 {4, 64}, {2, 64}, {1, 64}};
+static const int kNumFwdCfg = sizeof(kFwdCfg) / sizeof(kFwdCfg[0]);
+// reverse (adjoint) sweep kernels
+static const int kAdjRows[] = {4, 3, 2, 1};
+
 template <typename T>
-static SweepFn<T> sweep_fn(int tq)
+static SweepFn<T> fwd_kernel(int tq, int maxr)
 {
-    switch (tq) {
-    case 1: return rts::sweep_kernel<T, 1>;
-    case 2: return rts::sweep_kernel<T, 2>;
-    case 3: return rts::sweep_kernel<T, 3>;
-    case 4: return rts::sweep_kernel<T, 4>;
-    default: return rts::sweep_kernel<T, 4>;
-    }
+#define RTS_CFG(A, B)                                                                                              \
+    if (tq == A && maxr == B) return rts::sweep_kernel<T, A, B>;
+    RTS_CFG(16, 168) RTS_CFG(12, 168) RTS_CFG(8, 112) RTS_CFG(7, 112) RTS_CFG(6, 104) RTS_CFG(4, 72)
+    RTS_CFG(2, 56) RTS_CFG(1, 56) RTS_CFG(4, 64) RTS_CFG(2, 64) RTS_CFG(1, 64)
+#undef RTS_CFG
+    return nullptr;
 }
 
 template <typename T>
-static SweepFn<T> sweep_adj_fn(int tq)
+static SweepFn<T> adj_kernel(int tq)
 {
     switch (tq) {
     case 1: return rts::sweep_adj_kernel<T, 1>;
     case 2: return rts::sweep_adj_kernel<T, 2>;
     case 3: return rts::sweep_adj_kernel<T, 3>;
     case 4: return rts::sweep_adj_kernel<T, 4>;
-    default: return rts::sweep_adj_kernel<T, 4>;
+    default: return nullptr;
     }
 }
 
-static const int kTileRows[4] = {4, 3, 2, 1};
-
-// shared memory of one sweep CTA: per plane parity I of 4 slots and the two
-// seed-error bounds, per chi/S slot (3) chi and S: 18 fields of (tq+2) rows x
-// (np+2) columns in the sweep precision
-static size_t sweep_smem(int tq, int np, int esize)
+static size_t fwd_smem(int tq, int np, int esize)
 {
-    return (size_t)rts::NFIELD * (tq + 2) * (np + 2) * esize;
+    return esize == 8 ? rts::tile_smem_bytes<double>(tq, np) : rts::tile_smem_bytes<float>(tq, np);
 }
 
-// rows per tile: the option if given (rounded down to an instantiated size),
-// else the largest size whose CTA fits in ~75 KB (FP32) / ~110 KB (FP64) of
-// shared memory so that two or three CTAs share an SM
-static int pick_tile_rows(int requested, int np, int esize)
+// reverse sweep CTA: per plane parity the 4 slots' A = e lam and the two
+// bounds, plus chi of two planes, in the sweep precision
+static size_t adj_smem(int tq, int np, int esize)
 {
-    const size_t budget = esize == 4 ? 110 * 1024 : 112 * 1024;
-    for (int tq : kTileRows) {
+    return (size_t)rts::NFIELD_A * (tq + 2) * (np + 2) * esize;
+}
+
+struct Tiling {
+    int tq = 0, nt = 32, maxt = 0, blocks = 0;  // maxt: register cap of the forward kernel
+    size_t smem = 0;
+};
+
+template <typename T>
+static cudaError_t kernel_occupancy(SweepFn<T> kern, int nt, size_t smem, int *blocks)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, nt, smem);
+}
+
+// Forward tiling for plane extents up to npmax and units of up to
+// ceil(nqmax / tq) tiles. Candidates are the instantiated (rows, register cap)
+// pairs whose cap fits the CTA size. With `requested` > 0: the tallest tile
+// not above it that fits. Otherwise the score is the plane rows resident per
+// SM, halved when only one CTA fits (one CTA cannot hide its own barrier and
+// neighbour waits). Every unit's tiles must fit on the GPU at once (the
+// persistent launch waits on neighbours).
+template <typename T>
+static Tiling choose_fwd(int requested, int npmax, int nqmax, int nsm)
+{
+    Tiling best;
+    best.nt = 32 * ((npmax + 31) / 32);
+    double best_score = -1;
+    for (int i = 0; i < kNumFwdCfg; ++i) {
+        const int tq = kFwdCfg[i].tq, maxr = kFwdCfg[i].maxr;
+        if ((long long)maxr * best.nt > 65536) continue;
         if (requested > 0 && tq > requested) continue;
-        if (requested > 0 || sweep_smem(tq, np, esize) <= budget) return tq;
+        const size_t smem = fwd_smem(tq, npmax, (int)sizeof(T));
+        if (smem > 227 * 1024) continue;
+        int blocks = 0;
+        if (kernel_occupancy<T>(fwd_kernel<T>(tq, maxr), best.nt, smem, &blocks) != cudaSuccess || blocks < 1)
+            continue;
+        if ((long long)blocks * nsm < (nqmax + tq - 1) / tq) continue;
+        double score = (double)tq * blocks * (blocks > 1 ? 1.0 : 0.5);
+        if (requested > 0) score = tq;  // tallest fitting tile
+        if (score > best_score) {
+            best_score = score;
+            best.tq = tq;
+            best.maxt = maxr;
+            best.blocks = blocks;
+            best.smem = smem;
+        }
     }
-    return 1;
+    return best;
+}
+
+// reverse-sweep tiling: the tallest tile of at most ~110 KB shared memory
+template <typename T>
+static Tiling choose_adj(int npmax, int nqmax, int nsm)
+{
+    Tiling best;
+    best.nt = 32 * ((npmax + 31) / 32);
+    best.maxt = 1024;
+    for (int tq : kAdjRows) {
+        const size_t smem = adj_smem(tq, npmax, (int)sizeof(T));
+        if (smem > 110 * 1024 && tq > 1) continue;
+        int blocks = 0;
+        if (kernel_occupancy<T>(adj_kernel<T>(tq), best.nt, smem, &blocks) != cudaSuccess || blocks < 1) continue;
+        if ((long long)blocks * nsm < (nqmax + tq - 1) / tq) continue;
+        best.tq = tq;
+        best.blocks = blocks;
+        best.smem = smem;
+        break;
+    }
+    return best;
 }
 
 template <typename T>
 static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool reverse = false)
 {
-    SweepFn<T> kern = reverse ? sweep_adj_fn<T>(h->tq) : sweep_fn<T>(h->tq);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
+    SweepFn<T> kern = reverse ? adj_kernel<T>(h->adj_tq) : fwd_kernel<T>(h->tq, h->maxt);
+    const size_t smem = reverse ? h->adj_smem : h->smem;
+    if (!kern) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(std::min(reverse ? h->grid_adj : h->grid, a.total_tiles));
     cfg.blockDim = dim3(h->nt);
-    cfg.dynamicSmemBytes = h->smem;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = h->stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident
@@ -321,15 +400,6 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, a);
-}
-
-template <typename T>
-static cudaError_t occupancy(rts_handle *h, int *blocks, bool reverse = false)
-{
-    SweepFn<T> kern = reverse ? sweep_adj_fn<T>(h->tq) : sweep_fn<T>(h->tq);
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern, h->nt, h->smem);
 }
 
 extern "C" {
@@ -425,13 +495,20 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         npmax = std::max(npmax, NP);
     }
     if (npmax > 1024) return bail(fail(h, RTS_EINVAL, "plane extent %d > 1024 is not supported", npmax));
-    const int tq = pick_tile_rows(o.tile_rows, npmax, h->esize);
+    const int nqmax = (int)std::max(ny, nz);
+    int dev = 0, nsm = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const Tiling tl = o.prec == RTS_FP64 ? choose_fwd<double>(o.tile_rows, npmax, nqmax, nsm)
+                                         : choose_fwd<float>(o.tile_rows, npmax, nqmax, nsm);
+    if (tl.tq < 1) return bail(fail(h, RTS_EINVAL, "no sweep tile fits plane extent %d with %d-row units", npmax, nqmax));
+    const int tq = tl.tq;
     h->tq = tq;
-    h->nt = 32 * ((npmax + 31) / 32);
-    h->smem = sweep_smem(tq, npmax, h->esize);
-    if (h->smem > 227 * 1024) return bail(fail(h, RTS_EINVAL, "tile of %d rows needs %zu B shared memory", tq, h->smem));
+    h->nt = tl.nt;
+    h->maxt = tl.maxt;
+    h->smem = tl.smem;
     const int max_units = nbands * 6 * h->ndir;
-    const long long max_tiles = (long long)max_units * ((std::max(nx, std::max(ny, nz)) + tq - 1) / tq);
+    const long long max_tiles = (long long)max_units * std::max(nx, std::max(ny, nz));  // tiles of >= 1 row
     h->units.resize(max_units);
     h->unit_of_tile.resize(max_tiles);
     PlanOut po;
@@ -442,42 +519,45 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->unit_of_tile.resize(po.ntiles);
     h->has_x = po.has_x;
     h->max_ntiles = po.max_ntiles;
-    const long long halo_elems = po.halo_elems;
-    const int tile0 = po.ntiles;
-    h->total_tiles = tile0;
-    int R = 8;
-    while (R < 2 * (h->max_ntiles + kLag + 2)) R *= 2;
-    h->R = R;
-
-    // ---- residency of the persistent launch ----
-    int dev = 0, nsm = 0, blocks = 0;
-    CUDA_TRY(h, cudaGetDevice(&dev));
-    CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    cudaError_t oe = o.prec == RTS_FP64 ? occupancy<double>(h, &blocks) : occupancy<float>(h, &blocks);
-    if (oe != cudaSuccess) return bail(fail(h, RTS_ECUDA, "occupancy query: %s", cudaGetErrorString(oe)));
-    h->grid = std::min(h->total_tiles, blocks * nsm);
-    if (blocks < 1 || h->grid < h->max_ntiles)
-        return bail(fail(h, RTS_EINVAL, "a sweep unit has %d tiles but only %d CTAs fit on the GPU", h->max_ntiles,
-                         blocks * nsm));
+    long long halo_elems = po.halo_elems;
+    h->total_tiles = po.ntiles;
+    h->grid = std::min(h->total_tiles, tl.blocks * nsm);
 
     const bool adjoint = (o.flags & RTS_FLAG_ADJOINT) != 0;
     h->band_unit.assign(nbands + 1, 0);
     for (size_t u = 0; u < h->units.size(); ++u) h->band_unit[h->units[u].band + 1]++;
     for (int b = 0; b < nbands; ++b) h->band_unit[b + 1] += h->band_unit[b];
+    int flag_tiles = h->total_tiles, max_nt = h->max_ntiles;
     if (adjoint) {
         h->chunk_bands = std::min(nbands, std::max(1, o.adjoint_chunk_bands));
         for (int b = 0; b < nbands; b += h->chunk_bands) {
             const int b1 = std::min(nbands, b + h->chunk_bands);
             h->chunk_units = std::max(h->chunk_units, h->band_unit[b1] - h->band_unit[b]);
         }
-        int ablocks = 0;
-        oe = o.prec == RTS_FP64 ? occupancy<double>(h, &ablocks, true) : occupancy<float>(h, &ablocks, true);
-        if (oe != cudaSuccess) return bail(fail(h, RTS_ECUDA, "occupancy query: %s", cudaGetErrorString(oe)));
-        h->grid_adj = ablocks * nsm;
-        if (ablocks < 1 || h->grid_adj < h->max_ntiles)
-            return bail(fail(h, RTS_EINVAL, "a sweep unit has %d tiles but only %d reverse-sweep CTAs fit",
-                             h->max_ntiles, h->grid_adj));
+        const Tiling ta = o.prec == RTS_FP64 ? choose_adj<double>(npmax, nqmax, nsm) : choose_adj<float>(npmax, nqmax, nsm);
+        if (ta.tq < 1) return bail(fail(h, RTS_EINVAL, "no reverse-sweep tile fits plane extent %d", npmax));
+        h->adj_tq = ta.tq;
+        h->adj_smem = ta.smem;
+        h->adj_units.resize(max_units);
+        h->adj_unit_of_tile.resize(max_tiles);
+        PlanOut pa;
+        if (!plan_units(geo.data(), udx.data(), h->n.data(), h->w.data(), h->ndir, nx, ny, nz, nbands, ta.tq,
+                        h->adj_units.data(), max_units, h->adj_unit_of_tile.data(), (int)max_tiles, pa) ||
+            pa.nunits != po.nunits)
+            return bail(fail(h, RTS_EINVAL, "too many reverse-sweep tiles"));
+        h->adj_units.resize(pa.nunits);
+        h->adj_unit_of_tile.resize(pa.ntiles);
+        h->adj_total_tiles = pa.ntiles;
+        h->adj_max_ntiles = pa.max_ntiles;
+        h->grid_adj = std::min(pa.ntiles, ta.blocks * nsm);
+        halo_elems = std::max(halo_elems, pa.halo_elems);
+        flag_tiles = std::max(flag_tiles, pa.ntiles);
+        max_nt = std::max(max_nt, pa.max_ntiles);
     }
+    h->flag_tiles = flag_tiles;
+    int R = 8;
+    while (R < 2 * (max_nt + kLag + 2)) R *= 2;
+    h->R = R;
 
     // ---- device memory ----
     const size_t es = h->esize;
@@ -491,7 +571,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_ST = h->has_x ? take((size_t)nbands * h->N * es) : 0;
     const size_t o_JF = take((size_t)nbands * 4 * h->N * accsz);
     const size_t o_halo = take((size_t)halo_elems * es);
-    const size_t o_flags = take(sizeof(int) * h->total_tiles);
+    const size_t o_flags = take(sizeof(int) * flag_tiles);
     const size_t o_gcnt = take(sizeof(unsigned int) * h->units.size() * R);
     const size_t o_gmax = take(sizeof(unsigned long long) * h->units.size() * R);
     const size_t o_ticket = take(sizeof(int) * 4);
@@ -499,8 +579,10 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_tacc = take(sizeof(int) * h->units.size());
     const size_t o_ru = take(sizeof(rts::RedUnit) * h->units.size());
     const size_t o_rub = take(sizeof(int) * (nbands + 1));
-    size_t o_adj[7] = {0};
+    size_t o_adj[9] = {0};
     if (adjoint) {
+        o_adj[7] = take(sizeof(rts::SweepUnit) * h->adj_units.size());
+        o_adj[8] = take(sizeof(int) * h->adj_unit_of_tile.size());
         const size_t cu = (size_t)h->chunk_units;
         o_adj[0] = take((size_t)nbands * 4 * h->N * es);
         o_adj[1] = h->has_x ? take((size_t)nbands * 4 * h->N * es) : 0;
@@ -542,6 +624,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->d_ru = (rts::RedUnit *)(base + o_ru);
     h->d_ru_begin = (int *)(base + o_rub);
     if (adjoint) {
+        h->d_adj_units = (rts::SweepUnit *)(base + o_adj[7]);
+        h->d_adj_uot = (int *)(base + o_adj[8]);
         h->d_lam0 = base + o_adj[0];
         h->d_lam0T = h->has_x ? base + o_adj[1] : nullptr;
         h->d_direct = base + o_adj[2];
@@ -572,6 +656,13 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     CUDA_TRY(h, cudaMemcpy(h->d_unit_of_tile, h->unit_of_tile.data(), sizeof(int) * h->unit_of_tile.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * ru.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, rub.data(), sizeof(int) * rub.size(), cudaMemcpyHostToDevice));
+    if (adjoint) {
+        for (size_t u = 0; u < h->adj_units.size(); ++u) h->adj_units[u].partial = h->units[u].partial;
+        CUDA_TRY(h, cudaMemcpy(h->d_adj_units, h->adj_units.data(), sizeof(rts::SweepUnit) * h->adj_units.size(),
+                               cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(h->d_adj_uot, h->adj_unit_of_tile.data(), sizeof(int) * h->adj_unit_of_tile.size(),
+                               cudaMemcpyHostToDevice));
+    }
     h->timing = (o.flags & RTS_FLAG_TIMING) != 0;
     *out = h;
     return RTS_OK;
@@ -617,7 +708,7 @@ static rts::SweepArgs<T> sweep_args(rts_handle *h, const void *chi, const void *
 static rts_status reset_sweep_state(rts_handle *h, cudaStream_t st)
 {
     CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->total_tiles, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * std::max(h->flag_tiles, h->total_tiles), st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
     return RTS_OK;
@@ -756,9 +847,14 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
         a.store = (T *)h->d_adjI;
         cudaError_t e = launch_sweep<T>(h, a);
         if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
-        // reverse sweep: cotangent of I of every ray
+        // reverse sweep: cotangent of I of every ray (the adjoint kernel's tiling)
         rs = reset_sweep_state(h, st);
         if (rs) return rs;
+        const rts::SweepUnit &A0 = h->adj_units[u0], &A1 = h->adj_units[u1 - 1];
+        a.units = h->d_adj_units;
+        a.unit_of_tile = h->d_adj_uot;
+        a.tile_base = A0.tile0;
+        a.total_tiles = A1.tile0 + A1.ntiles - A0.tile0;
         a.store = (T *)h->d_adjL;
         a.lam0 = (const T *)h->d_lam0;
         a.lam0T = (const T *)h->d_lam0T;
@@ -1030,9 +1126,19 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
         return RTS_EINVAL;
     }
     const size_t es = sizeof(T);
-    const int tq = pick_tile_rows(0, npmax, (int)es);
-    const int nt = 32 * ((npmax + 31) / 32);
-    const size_t smem = sweep_smem(tq, npmax, (int)es);
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        noalloc_msg(err, errlen, "cannot query the device");
+        return RTS_ECUDA;
+    }
+    const Tiling tl = choose_fwd<T>(0, npmax, (int)std::max(ny, nz), nsm);
+    if (tl.tq < 1) {
+        noalloc_msg(err, errlen, "no sweep tile fits plane extent %d", npmax);
+        return RTS_EINVAL;
+    }
+    const int tq = tl.tq;
+    const int nt = tl.nt;
+    const size_t smem = tl.smem;
 
     rts::SweepUnit units[kNoallocMaxUnits];
     int unit_of_tile[kNoallocMaxTiles];
@@ -1081,8 +1187,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     }
 
     // residency of the persistent launch
-    SweepFn<T> kern = sweep_fn<T>(tq);
-    int nsm = 0, blocks = 0;
+    SweepFn<T> kern = fwd_kernel<T>(tq, tl.maxt);
+    int blocks = 0;
 #define NA_TRY(call)                                                                              \
     do {                                                                                          \
         cudaError_t e_ = (call);                                                                  \
@@ -1091,7 +1197,6 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
             return RTS_ECUDA;                                                                     \
         }                                                                                         \
     } while (0)
-    NA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     NA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     NA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, nt, smem));
     const int grid = std::min(ntile, blocks * nsm);
@@ -1281,11 +1386,19 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
         maxext = std::max<long long>(maxext, std::max(grids[s].nx, std::max(grids[s].ny, grids[s].nz)));
     }
     if (npmax > 1024) return bail(fail(h, RTS_EINVAL, "plane extent %d > 1024 is not supported", npmax));
-    const int tq = pick_tile_rows(o.tile_rows, npmax, h->esize);
+    int nqmax = 0;
+    for (int s = 0; s < nsub; ++s) nqmax = std::max(nqmax, std::max(grids[s].ny, grids[s].nz));
+    int dev = 0, nsm = 0;
+    CUDA_TRY(h, cudaGetDevice(&dev));
+    CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const Tiling tl = o.prec == RTS_FP64 ? choose_fwd<double>(o.tile_rows, npmax, nqmax, nsm)
+                                         : choose_fwd<float>(o.tile_rows, npmax, nqmax, nsm);
+    if (tl.tq < 1) return bail(fail(h, RTS_EINVAL, "no sweep tile fits plane extent %d", npmax));
+    const int tq = tl.tq;
     h->tq = tq;
-    h->nt = 32 * ((npmax + 31) / 32);
-    h->smem = sweep_smem(tq, npmax, h->esize);
-    if (h->smem > 227 * 1024) return bail(fail(h, RTS_EINVAL, "tile of %d rows needs %zu B shared memory", tq, h->smem));
+    h->nt = tl.nt;
+    h->maxt = tl.maxt;
+    h->smem = tl.smem;
 
     std::vector<rts::SweepUnit> plan;       // plan order
     std::vector<int> plan_sub;              // subdomain of each planned unit
@@ -1378,15 +1491,8 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     while (R < 2 * (h->max_ntiles + kLag + 2)) R *= 2;
     h->R = R;
 
-    int dev = 0, nsm = 0, blocks = 0;
-    CUDA_TRY(h, cudaGetDevice(&dev));
-    CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    cudaError_t oe = o.prec == RTS_FP64 ? occupancy<double>(h, &blocks) : occupancy<float>(h, &blocks);
-    if (oe != cudaSuccess) return bail(fail(h, RTS_ECUDA, "occupancy query: %s", cudaGetErrorString(oe)));
-    h->grid = std::min(h->total_tiles, blocks * nsm);
-    if (blocks < 1 || h->grid < h->max_ntiles)
-        return bail(fail(h, RTS_EINVAL, "a sweep unit has %d tiles but only %d CTAs fit on the GPU", h->max_ntiles,
-                         blocks * nsm));
+    h->grid = std::min(h->total_tiles, tl.blocks * nsm);
+    h->flag_tiles = h->total_tiles;
 
     // ---- device memory ----
     const size_t es = h->esize;
@@ -1588,7 +1694,7 @@ extern "C" void rts_graph_destroy(rts_graph *g)
 // ---- tile-size autotuner --------------------------------------------------
 extern "C" rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, const rts_quadrature *q,
                                    const rts_options *opt, const void *chi, const void *S, int repeats,
-                                   int *best_tile_rows, float ms[4])
+                                   int *best_tile_rows, int *ncand, int rows[8], float ms[8])
 {
     if (nsub < 1 || !grids || !chi || !S || !best_tile_rows) return RTS_EINVAL;
     rts_options o;
@@ -1596,15 +1702,16 @@ extern "C" rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, 
     else rts_default_options(&o);
     o.flags &= ~(RTS_FLAG_TIMING | RTS_FLAG_ADJOINT | RTS_FLAG_HOST_IO);
     const int reps = std::max(1, repeats);
+    const int cand[8] = {1, 2, 4, 6, 7, 8, 12, 16};
     float best = 0.f;
+    int n = 0;
     *best_tile_rows = 0;
-    for (int c = 0; c < 4; ++c) {
-        const int tq = kTileRows[3 - c];  // 1, 2, 3, 4
-        if (ms) ms[c] = -1.f;
+    for (int c = 0; c < 8; ++c) {
+        const int tq = cand[c];
         o.tile_rows = tq;
         rts_handle *h = nullptr;
         rts_status s = rts_create_batched(&h, nsub, grids, nbands, q, &o);
-        if (s != RTS_OK || !h || h->tq != tq) {
+        if (s != RTS_OK || !h || h->tq != tq) {  // not instantiated for this extent, or does not fit
             rts_destroy(h);
             continue;
         }
@@ -1623,11 +1730,16 @@ extern "C" rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, 
         rts_destroy(h);
         if (!ok) continue;
         t /= reps;
-        if (ms) ms[c] = t;
+        if (rows && ms && n < 8) {
+            rows[n] = tq;
+            ms[n] = t;
+        }
+        ++n;
         if (*best_tile_rows == 0 || t < best) {
             best = t;
             *best_tile_rows = tq;
         }
     }
+    if (ncand) *ncand = std::min(n, 8);
     return *best_tile_rows ? RTS_OK : RTS_ECUDA;
 }

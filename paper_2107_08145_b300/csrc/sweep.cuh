@@ -156,12 +156,24 @@ __device__ __forceinline__ void natural_ij(int axis, int p, int q, int m, int &i
 
 // Ray constants of the unit's slots in shared memory.
 template <typename T>
-struct DirConst {
+struct __align__(16) DirConst {
     T beta[MAXD][4];
     T hds[MAXD];           // ds / 2
     T cJ[MAXD], cF[3][MAXD];
     int up[MAXD], bck[MAXD], udx[MAXD], active[MAXD];
 };
+
+// four consecutive values of a 16-byte aligned shared array in one or two loads
+__device__ __forceinline__ void ld4(const float *p, float &a, float &b, float &c, float &d)
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double &a, double &b, double &c, double &d)
+{
+    const double2 u = *reinterpret_cast<const double2 *>(p), v = *reinterpret_cast<const double2 *>(p + 2);
+    a = u.x; b = u.y; c = v.x; d = v.y;
+}
 
 template <typename T>
 __device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U, const DirConst<T> &D, int d,
@@ -179,32 +191,19 @@ __device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U,
 
 // Shared memory of a tile, NPP = NP + 2 columns per row: column c = p + 1,
 // columns 0 and NP+1 repeat p = NP-1 and p = 0 (periodic padding), so a P
-// neighbour is always the next column. Fields per plane parity: I of the 4
-// slots, the up/down seed-error bounds, chi and S; each field RW = TQ+2 rows
-// (halo row, TQ own rows, halo row).
-enum { F_I0 = 0, F_GU = 4, F_GD = 5, NPARF = 6, NXSF = 2, NFIELD = 2 * NPARF + 2 * NXSF };
+// neighbour is always the next column. Each field has RW = TQ+2 rows (halo
+// row, TQ own rows, halo row). The previous plane's intensities (4 slots)
+// and seed-error bounds (up / down rays, float) are kept once: a plane's new
+// values stay in registers until every thread has read the previous plane.
+// chi and S are kept for two planes (by plane parity): the previous plane for
+// the upwind interpolation, the current one for the own points, and the slot
+// of the plane before is refilled with cp.async a whole plane ahead.
+enum { SF_I = 4, SF_XS = 4, SF_G = 2 };
 
-// I of slot (SP, SQ) at one point from the previous plane: pointers at the
-// point, row stride npp; e = exp(-dtau) for the seed-error bound
-template <typename T, int SP, int SQ>
-__device__ __forceinline__ T slot_update(const T *__restrict__ Ip, const T *__restrict__ Xp,
-                                         const T *__restrict__ Sp, int npp, T b0, T b1, T b2, T b3, T hds,
-                                         T xp, T sp, T &e)
+template <typename T>
+__host__ __device__ constexpr size_t tile_smem_bytes(int tq, int np)
 {
-    const int oq = -SQ * npp;
-    const T Iup = b0 * Ip[0] + b1 * Ip[-SP] + b2 * Ip[oq] + b3 * Ip[oq - SP];
-    const T xup = b0 * Xp[0] + b1 * Xp[-SP] + b2 * Xp[oq] + b3 * Xp[oq - SP];
-    const T sup = b0 * Sp[0] + b1 * Sp[-SP] + b2 * Sp[oq] + b3 * Sp[oq - SP];
-    T wu, wp;
-    seg_weights(hds * (xup + xp), e, wu, wp);
-    return Iup + wu * (sup - Iup) + wp * (sp - Iup);
-}
-
-template <typename T, int SP, int SQ>
-__device__ __forceinline__ float slot_bound(const T *__restrict__ Gp, int npp, T b0, T b1, T b2, T b3, T e)
-{
-    const int oq = -SQ * npp;
-    return (float)(e * (b0 * Gp[0] + b1 * Gp[-SP] + b2 * Gp[oq] + b3 * Gp[oq - SP]));
+    return (size_t)(tq + 2) * (np + 2) * ((SF_I + SF_XS) * sizeof(T) + SF_G * sizeof(float));
 }
 
 // One tile of one sweep unit, from its first plane to the last. Thread p
@@ -236,10 +235,12 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const int c = p + 1;                        // smem column
     const int npp = NP + 2;
     const int FL = RW * npp;                    // one field
-    T *const sm = (T *)smem;
-    auto fI = [&](int par, int f) -> T * { return sm + (par * NPARF + f) * FL; };
-    auto fX = [&](int t) -> T * { return sm + (2 * NPARF + (t & 1) * NXSF) * FL; };
-    auto fS = [&](int t) -> T * { return sm + (2 * NPARF + (t & 1) * NXSF + 1) * FL; };
+    T *const sI = (T *)smem;                    // I of slot d: sI + d * FL
+    T *const sX = sI + SF_I * FL;               // chi of plane t: sX + (t & 1) * FL
+    T *const sS = sX + 2 * FL;                  // S of plane t:   sS + (t & 1) * FL
+    float *const sG = (float *)(sS + 2 * FL);   // bound of the up (0) / down (1) rays
+    auto fX = [&](int t) -> T * { return sX + (t & 1) * FL; };
+    auto fS = [&](int t) -> T * { return sS + (t & 1) * FL; };
 
     __shared__ DirConst<T> D;
     __shared__ float s_wmax[32];
@@ -272,7 +273,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const bool has_upper = qper || r < ntl - 1;
 
     // store v at column p + 1 of row k of field f, and its periodic copy
-    auto put = [&](T *f, int k, T v) {
+    auto put = [&](auto *f, int k, auto v) {
         f[k * npp + c] = v;
         if (p == 0) f[k * npp + NP + 1] = v;
         if (p == NP - 1) f[k * npp] = v;
@@ -297,13 +298,17 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     };
 
     __syncthreads();
+    int upm = 0, actm = 0;  // slot bit masks: upward ray, slot holds a ray
+    for (int d = 0; d < MAXD; ++d) {
+        upm |= D.up[d] ? 1 << d : 0;
+        actm |= D.active[d] ? 1 << d : 0;
+    }
 
     // ---------------- prologue: the plane before the first integrated one ----
     const int tp = t_first - 1;
     prefetch(t_first);
     if (act) {
         const int m = plane_of(tp, NM, sa);
-        const int par = tp & 1;
         const long long mo = (long long)m * sM + p;
         for (int k = 0; k < nrows + 2; ++k) {
             const int q = s_q[k];
@@ -313,7 +318,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             const T s = ok ? Sg[off] : T(0);
             put(fX(tp), k, x);
             put(fS(tp), k, s);
-            T gu = 0, gd = 0;
+            float gu = 0.f, gd = 0.f;
             for (int d = 0; d < MAXD; ++d) {
                 T v = T(0);
                 const bool bcrow = wrap ? ((D.up[d] && q == 0) || (!D.up[d] && q == NQ - 1)) : true;
@@ -321,27 +326,27 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                     if (bcrow) v = bc_value(a, *Ug, D, d, p, q, m, s);
                     else {  // seed: I = S, unit seed-error bound
                         v = s;
-                        if (D.up[d]) gu = 1; else gd = 1;
+                        if (D.up[d]) gu = 1.f; else gd = 1.f;
                     }
                 }
-                put(fI(par, F_I0 + d), k, v);
+                put(sI + d * FL, k, v);
             }
-            put(fI(par, F_GU), k, gu);
-            put(fI(par, F_GD), k, gd);
+            put(sG, k, gu);
+            put(sG + FL, k, gd);
         }
         // z groups: the boundary plane is the first of the NM accumulated planes
         if (!wrap) {
             for (int k = 1; k <= nrows; ++k) {
                 T aJ = 0, aX = 0, aY = 0, aZ = 0;
                 for (int d = 0; d < MAXD; ++d) {
-                    const T v = fI(par, F_I0 + d)[k * npp + c];
+                    const T v = sI[d * FL + k * npp + c];
                     aJ += D.cJ[d] * v; aX += D.cF[0][d] * v; aY += D.cF[1][d] * v; aZ += D.cF[2][d] * v;
                 }
                 const long long off = (long long)m * sM + (long long)s_q[k] * sQ + p;
                 part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
                 if (a.store) {
                     T *st = a.store + (long long)(uidx - a.unit_base) * 4 * N + off;
-                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = fI(par, F_I0 + d)[k * npp + c];
+                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = sI[d * FL + k * npp + c];
                 }
             }
         }
@@ -356,7 +361,6 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
 
     for (int t = t_first;; ++t) {
         const int m = plane_of(t, NM, sa);
-        const int cur = t & 1, prv = cur ^ 1;
         // decision taken during the previous plane
         if (t_acc < 0 && s_ctl[1]) {
             t_acc = t;
@@ -364,109 +368,118 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
         }
         if (wrap && t_acc < 0 && t >= warm_cap) {
             if (tid == 0) atomicOr(a.status, ST_NOCONV);
+            cp_async_wait_all();
             return;  // every tile of the unit stops at the same plane; nothing in flight
         }
         const bool acc = t_acc >= 0;
         const bool last = acc && (t - t_acc == NM - 1);
-        cp_async_wait_all();  // this thread's chi/S of plane t (read only by this thread until B1)
+        cp_async_wait_all();  // this thread's chi/S of plane t (read only by this thread in this step)
 
-        T b[MAXD][4], hds[MAXD];
-#pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-            hds[d] = D.hds[d];
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) b[d][cc] = D.beta[d][cc];
-        }
         const T *Xp = fX(t + 1), *Sp = fS(t + 1), *Xc = fX(t), *Sc = fS(t);  // (t+1) & 1 == (t-1) & 1
         const bool top_plane = axis == 2 && t == NM - 1 && sa > 0;
         float gmax = 0.f;
-        T ps[TQ][4];  // partial sums of the own rows, stored after the release
 
-        // integrate row k (1..nrows) of plane t from the previous plane
-        auto do_row = [&](int k) {
+        // new values of row k (1..nrows) from the previous plane in shared memory
+        struct Row {
+            T v[MAXD];      // intensities of the 4 slots
+            float g[2];     // seed-error bounds of the up / down rays (warm-up only)
+        };
+        // the plane's new rows, kept in registers until the previous plane is no
+        // longer read: rows 1 .. nrows-1 in nR (constant indices only), the last in rl
+        Row nR[TQ], rl;
+        auto do_row = [&](int k) -> Row {
+            Row out;
+            T *v = out.v;
             const int q = q0 + k - 1;
             const int o = k * npp + c;
+            // previous plane's chi and S on the 3 x 3 neighbourhood, shared by the rays
+            T xs[3][3], ss[3][3];
+#pragma unroll
+            for (int dq = 0; dq < 3; ++dq)
+#pragma unroll
+                for (int dp = 0; dp < 3; ++dp) {
+                    xs[dq][dp] = Xp[o + (dq - 1) * npp + dp - 1];
+                    ss[dq][dp] = Sp[o + (dq - 1) * npp + dp - 1];
+                }
             const T xp = Xc[o], sp = Sc[o];
-            T v[MAXD], e[MAXD];
-            v[0] = slot_update<T, 1, 1>(fI(prv, F_I0 + 0) + o, Xp + o, Sp + o, npp, b[0][0], b[0][1], b[0][2], b[0][3], hds[0], xp, sp, e[0]);
-            v[1] = slot_update<T, -1, 1>(fI(prv, F_I0 + 1) + o, Xp + o, Sp + o, npp, b[1][0], b[1][1], b[1][2], b[1][3], hds[1], xp, sp, e[1]);
-            v[2] = slot_update<T, 1, -1>(fI(prv, F_I0 + 2) + o, Xp + o, Sp + o, npp, b[2][0], b[2][1], b[2][2], b[2][3], hds[2], xp, sp, e[2]);
-            v[3] = slot_update<T, -1, -1>(fI(prv, F_I0 + 3) + o, Xp + o, Sp + o, npp, b[3][0], b[3][1], b[3][2], b[3][3], hds[3], xp, sp, e[3]);
+            T hd[MAXD];
+            ld4(D.hds, hd[0], hd[1], hd[2], hd[3]);
+            float g[MAXD];
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) {
+                const int SP = (d & 1) ? -1 : 1, SQ = (d & 2) ? -1 : 1;  // compile time after unrolling
+                T b0, b1, b2, b3;
+                ld4(D.beta[d], b0, b1, b2, b3);
+                const T *Ip = sI + d * FL + o;
+                const int oq = -SQ * npp;
+                const T Iup = b0 * Ip[0] + b1 * Ip[-SP] + b2 * Ip[oq] + b3 * Ip[oq - SP];
+                const T xup = b0 * xs[1][1] + b1 * xs[1][1 - SP] + b2 * xs[1 - SQ][1] + b3 * xs[1 - SQ][1 - SP];
+                const T sup = b0 * ss[1][1] + b1 * ss[1][1 - SP] + b2 * ss[1 - SQ][1] + b3 * ss[1 - SQ][1 - SP];
+                T e, wu, wp;
+                seg_weights(hd[d] * (xup + xp), e, wu, wp);
+                v[d] = Iup + wu * (sup - Iup) + wp * (sp - Iup);
+                g[d] = 0.f;
+                if (!acc) {
+                    const float *Gp = sG + (((upm >> d) & 1) ? 0 : FL) + o;
+                    g[d] = (float)e * ((float)b0 * Gp[0] + (float)b1 * Gp[-SP] + (float)b2 * Gp[oq] +
+                                       (float)b3 * Gp[oq - SP]);
+                }
+            }
             float gu = 0.f, gd = 0.f;
             if (!acc) {
-                // seed-error bound of the up and the down rays
-                const float g0 = slot_bound<T, 1, 1>(fI(prv, D.up[0] ? F_GU : F_GD) + o, npp, b[0][0], b[0][1], b[0][2], b[0][3], e[0]);
-                const float g1 = slot_bound<T, -1, 1>(fI(prv, D.up[1] ? F_GU : F_GD) + o, npp, b[1][0], b[1][1], b[1][2], b[1][3], e[1]);
-                const float g2 = slot_bound<T, 1, -1>(fI(prv, D.up[2] ? F_GU : F_GD) + o, npp, b[2][0], b[2][1], b[2][2], b[2][3], e[2]);
-                const float g3 = slot_bound<T, -1, -1>(fI(prv, D.up[3] ? F_GU : F_GD) + o, npp, b[3][0], b[3][1], b[3][2], b[3][3], e[3]);
-                gu = fmaxf(fmaxf(D.up[0] ? g0 : 0.f, D.up[1] ? g1 : 0.f), fmaxf(D.up[2] ? g2 : 0.f, D.up[3] ? g3 : 0.f));
-                gd = fmaxf(fmaxf(D.up[0] ? 0.f : g0, D.up[1] ? 0.f : g1), fmaxf(D.up[2] ? 0.f : g2, D.up[3] ? 0.f : g3));
+#pragma unroll
+                for (int d = 0; d < MAXD; ++d) {
+                    if ((upm >> d) & 1) gu = fmaxf(gu, g[d]);
+                    else gd = fmaxf(gd, g[d]);
+                }
             }
             // boundary layer of the x/y groups: set, not integrated
             if (wrap && (q == 0 || q == NQ - 1)) {
                 for (int d = 0; d < MAXD; ++d)
-                    if (D.up[d] ? q == 0 : q == NQ - 1) v[d] = bc_value(a, *Ug, D, d, p, q, m, sp);
+                    if (((upm >> d) & 1) ? q == 0 : q == NQ - 1) v[d] = bc_value(a, *Ug, D, d, p, q, m, sp);
                 if (q == 0) gu = 0.f;
                 if (q == NQ - 1) gd = 0.f;
             }
 #pragma unroll
-            for (int d = 0; d < MAXD; ++d) {
-                if (!D.active[d]) v[d] = T(0);
-                put(fI(cur, F_I0 + d), k, v[d]);
-            }
+            for (int d = 0; d < MAXD; ++d)
+                if (!((actm >> d) & 1)) v[d] = T(0);
+            out.g[0] = gu;
+            out.g[1] = gd;
+            if (!acc) gmax = fmaxf(gmax, fmaxf(gu, gd));
+            return out;
+        };
+
+        // first and last rows go to the neighbours through the global ring
+        auto to_ring = [&](int sd, Row rw) {
+            T *dst = myhalo + ((long long)((t & 1) * 2 + sd) * HALO_CH) * NP + p;
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) dst[(long long)d * NP] = rw.v[d];
             if (!acc) {
-                put(fI(cur, F_GU), k, (T)gu);
-                put(fI(cur, F_GD), k, (T)gd);
-                gmax = fmaxf(gmax, fmaxf(gu, gd));
-            } else {
-                T aJ = 0, aX = 0, aY = 0, aZ = 0;
-#pragma unroll
-                for (int d = 0; d < MAXD; ++d) {
-                    aJ += D.cJ[d] * v[d]; aX += D.cF[0][d] * v[d]; aY += D.cF[1][d] * v[d]; aZ += D.cF[2][d] * v[d];
-                }
-#pragma unroll
-                for (int kk = 0; kk < TQ; ++kk)
-                    if (kk == k - 1) { ps[kk][0] = aJ; ps[kk][1] = aX; ps[kk][2] = aY; ps[kk][3] = aZ; }
-                if (a.store) {
-                    T *st = a.store + (long long)(uidx - a.unit_base) * 4 * N + (long long)m * sM + (long long)q * sQ + p;
-#pragma unroll
-                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = v[d];
-                }
-                if (itop && (axis == 2 ? top_plane : q == NQ - 1)) {
-                    int i, j;
-                    natural_ij(axis, p, q, m, i, j);
-                    for (int d = 0; d < MAXD; ++d)
-                        if (D.up[d] && D.active[d]) itop[((long long)D.udx[d] * uny + j) * unx + i] = v[d];
-                }
-            }
-            // first and last rows go to the neighbours through the global ring
-            if (k == 1 || k == nrows) {
-                for (int sd = 0; sd < 2; ++sd) {
-                    if (!((sd == 0 && k == 1) || (sd == 1 && k == nrows))) continue;
-                    T *dst = myhalo + ((long long)(cur * 2 + sd) * HALO_CH) * NP + p;
-                    for (int d = 0; d < MAXD; ++d) dst[(long long)d * NP] = v[d];
-                    if (!acc) {
-                        dst[(long long)MAXD * NP] = (T)gu;
-                        dst[(long long)(MAXD + 1) * NP] = (T)gd;
-                    }
-                }
+                dst[(long long)MAXD * NP] = (T)rw.g[0];
+                dst[(long long)(MAXD + 1) * NP] = (T)rw.g[1];
             }
         };
 
-        // ---- interior rows need only this tile's own rows; then each thread
-        //      waits for the neighbours' plane t-1 and loads its column of
-        //      their edge rows into the halo rows ----
+
+        // ---- interior rows need only this tile's own rows of the previous
+        //      plane; meanwhile the neighbours finish their edge rows ----
         if (act) {
-#pragma unroll 1
-            for (int k = 2; k < nrows; ++k) do_row(k);
+#pragma unroll
+            for (int k = 2; k < TQ; ++k)
+                if (k < nrows) nR[k - 1] = do_row(k);
         }
-        if (t > t_first && act) {
-            bool ok = true;
-            if (has_lower) ok = wait_flag_geq(a.flags + tile0 + lower, t, a.status, a.timeout_ns);
-            if (ok && has_upper) ok = wait_flag_geq(a.flags + tile0 + upper, t, a.status, a.timeout_ns);
-            if (!ok) {
-                s_ctl[0] = 1;
-            } else {
+        // ---- one thread waits for the neighbours' plane t-1 (acquire); after
+        //      the barrier every thread loads its column of their edge rows
+        //      into the halo rows ----
+        if (t > t_first) {
+            if (tid == 0) {
+                bool ok = true;
+                if (has_lower) ok = wait_flag_geq(a.flags + tile0 + lower, t, a.status, a.timeout_ns);
+                if (ok && has_upper) ok = wait_flag_geq(a.flags + tile0 + upper, t, a.status, a.timeout_ns);
+                if (!ok) s_ctl[0] = 1;
+            }
+            __syncthreads();  // B0: the neighbours' rows of plane t-1 are published (or the wait failed)
+            if (act && !s_ctl[0]) {
                 const int hslot = (t - 1) & 1;
                 for (int side = 0; side < 2; ++side) {
                     if (side == 0 ? !has_lower : !has_upper) continue;
@@ -480,10 +493,10 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                     for (int ch = 0; ch < HALO_CH; ++ch)
                         hv[ch] = (ch < MAXD || !acc) ? ld_cg(src + (long long)ch * NP) : T(0);
 #pragma unroll
-                    for (int d = 0; d < MAXD; ++d) put(fI(prv, F_I0 + d), row, hv[d]);
+                    for (int d = 0; d < MAXD; ++d) put(sI + d * FL, row, hv[d]);
                     if (!acc) {
-                        put(fI(prv, F_GU), row, hv[MAXD]);
-                        put(fI(prv, F_GD), row, hv[MAXD + 1]);
+                        put(sG, row, (float)hv[MAXD]);
+                        put(sG + FL, row, (float)hv[MAXD + 1]);
                     }
                 }
             }
@@ -494,8 +507,10 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             return;
         }
         if (act) {
-            do_row(1);
-            if (nrows > 1) do_row(nrows);
+            nR[0] = do_row(1);
+            to_ring(0, nR[0]);
+            rl = nrows == 1 ? nR[0] : do_row(nrows);
+            to_ring(1, rl);
         }
         if (!acc) {
             for (int o = 16; o; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
@@ -518,7 +533,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             }
             if (!ok) s_ctl[0] = 1;
         }
-        __syncthreads();  // B2: plane t complete (smem and ring); plane t-1 no longer read
+        __syncthreads();  // B2: plane t's edge rows are in the ring; the previous plane is no longer read
         if (tid == 0) {
             // release the edge rows (the barrier orders the CTA's ring writes first)
             st_release(a.flags + gt, t + 1);
@@ -532,22 +547,57 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             }
         }
         if (s_ctl[0]) return;
-        if (acc && act) {
-            T *const pplane = part + (long long)m * sM + p;
+        // ---- plane t becomes the previous plane: own rows into shared memory;
+        //      accumulated planes also go out as partial sums ----
+        auto write_row = [&](int kk, Row rw) {
 #pragma unroll
-            for (int kk = 0; kk < TQ; ++kk) {
-                if (kk >= nrows) break;
-                T *pp = pplane + (long long)(q0 + kk) * sQ;
-                pp[0] = ps[kk][0]; pp[N] = ps[kk][1]; pp[2 * N] = ps[kk][2]; pp[3 * N] = ps[kk][3];
+            for (int d = 0; d < MAXD; ++d) put(sI + d * FL, kk + 1, rw.v[d]);
+            if (!acc) {
+                put(sG, kk + 1, rw.g[0]);
+                put(sG + FL, kk + 1, rw.g[1]);
+            } else {
+                const int q = q0 + kk;
+                const long long off = (long long)m * sM + (long long)q * sQ + p;
+                T cw[4][MAXD];
+                ld4(D.cJ, cw[0][0], cw[0][1], cw[0][2], cw[0][3]);
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) ld4(D.cF[cc], cw[cc + 1][0], cw[cc + 1][1], cw[cc + 1][2], cw[cc + 1][3]);
+                T aJ = 0, aX = 0, aY = 0, aZ = 0;
+#pragma unroll
+                for (int d = 0; d < MAXD; ++d) {
+                    const T v = rw.v[d];
+                    aJ += cw[0][d] * v; aX += cw[1][d] * v; aY += cw[2][d] * v; aZ += cw[3][d] * v;
+                }
+                part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
+                if (a.store) {
+                    T *st = a.store + (long long)(uidx - a.unit_base) * 4 * N + off;
+#pragma unroll
+                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = rw.v[d];
+                }
+                if (itop && (axis == 2 ? top_plane : q == NQ - 1)) {
+                    int i, j;
+                    natural_ij(axis, p, q, m, i, j);
+                    for (int d = 0; d < MAXD; ++d)
+                        if (D.up[d] && D.active[d]) itop[((long long)D.udx[d] * uny + j) * unx + i] = rw.v[d];
+                }
             }
+        };
+        if (act) {
+#pragma unroll
+            for (int kk = 0; kk < TQ - 1; ++kk)
+                if (kk < nrows - 1) write_row(kk, nR[kk]);
+            write_row(nrows - 1, rl);
         }
         if (last) break;
-        prefetch(t + 1);  // into the slot of plane t-1
+        prefetch(t + 1);  // into the slot of plane t-1 (no longer read)
+        __syncthreads();  // B3: plane t is the previous plane for every thread
     }
+    cp_async_wait_all();
 }
 
-template <typename T, int TQ>
-__global__ void __launch_bounds__(1024) sweep_kernel(SweepArgs<T> a)
+// MAXR caps the registers per thread so that two to four CTAs share an SM
+template <typename T, int TQ, int MAXR>
+__global__ void __maxnreg__(MAXR) sweep_kernel(SweepArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;

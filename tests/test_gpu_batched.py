@@ -80,7 +80,7 @@ def test_batched_fp64_vs_oracle(rts):
             assert norm_err(g[k].cpu().numpy(), ref[k]) <= 1e-12, k
 
 
-@pytest.mark.parametrize("tile_rows", [1, 2, 3, 4])
+@pytest.mark.parametrize("tile_rows", [1, 2, 3, 4, 8, 12, 16])
 def test_batched_tile_rows_do_not_change_results(rts, tile_rows):
     B = 2
     chis, Ss = _inputs(SHAPES, B, seed0=20)
