@@ -162,18 +162,26 @@ def _dist():
 
 
 def _traffic_from_profile(prec):
-    """DRAM bytes per sweep launch from the committed ncu summary, or None if
-    the sweep source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "sweep_rts288x4_dram.json")
+    """DRAM bytes per sweep launch from the committed ncu summary
+    (profiles/sweep_rts288x4_dram.md, "- key: value" lines), or None if the
+    sweep source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "sweep_rts288x4_dram.md")
+    rec = {}
     try:
-        rec = json.load(open(path))
-    except Exception:
+        for line in open(path):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                rec[k.strip()] = v.strip()
+    except OSError:
         return None
     src = os.path.join(ROOT, "paper_2107_08145_b300", "csrc", "sweep.cuh")
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if rec.get("sweep_source_sha256_16") != digest or rec.get("precision") != prec:
         return None
-    return rec.get("dram_bytes_per_launch")
+    try:
+        return int(rec["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def sweep_algorithmic_bytes(prec, nb=NB, ndir=NDIR):
@@ -226,6 +234,80 @@ def _adjoint_timing(rts, torch, workload, name, grid, prec, stream, steps):
     del s, chi, S, out, grads
     torch.cuda.empty_cache()
     return r
+
+
+def _batched_timing(rts, torch, steps):
+    """The batched workload: 64 uneven subdomains x 12 bands, FP32 sweep with
+    FP64 Q step, one persistent launch inside a CUDA graph, tile height from
+    rts_autotune; against 768 separate rts_solve calls (one per subdomain and
+    band) on the same data. CUDA events on the solvers' stream."""
+    from workloads import band_stack, batched_bands, batched_subdomain_shapes, stratified_atmosphere
+
+    shapes = batched_subdomain_shapes(64, seed=0)
+    cs, ss = batched_bands()
+    nb = len(cs)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    chis, Ss = [], []
+    for i, (nx, ny, nz) in enumerate(shapes):
+        T, _, chi = stratified_atmosphere(nx, ny, nz, seed=i)
+        c, s_ = band_stack(T, chi, cs, ss)
+        chis.append(torch.as_tensor(c, dtype=torch.float32, device=dev).reshape(-1))
+        Ss.append(torch.as_tensor(s_, dtype=torch.float32, device=dev).reshape(-1))
+        del T, chi, c, s_
+    chi = torch.cat(chis)
+    S = torch.cat(Ss)
+    del chis, Ss
+    side = torch.cuda.Stream()
+    best, tune_ms = rts.autotune(shapes, nb, chi, S, precision="fp32", repeats=1, stream=side)
+    bs = rts.BatchedSolver(shapes, nb, precision="fp32", tile_rows=best, stream=side)
+    g, out = bs.graph(chi, S)
+
+    def timed(fn, n, stream):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+
+    ms_b = timed(g.launch, steps, side)
+    bs.check()
+    st = bs.stats()
+    offs = bs.offsets
+    del g, bs, out
+    torch.cuda.empty_cache()
+    # separate solves: one handle per subdomain (one band), 12 calls each
+    singles = []
+    for (nx, ny, nz) in shapes:
+        so = rts.Solver(nx, ny, nz, 1, precision="fp32", stream=side)
+        singles.append((so, so.solve(chi[:nx * ny * nz].view(1, nz, ny, nx), S[:nx * ny * nz].view(1, nz, ny, nx))))
+    views = []
+    for (nx, ny, nz), (go, _, _) in zip(shapes, offs):
+        n = nx * ny * nz
+        views.append([(chi[go + b * n:go + (b + 1) * n].view(1, nz, ny, nx),
+                       S[go + b * n:go + (b + 1) * n].view(1, nz, ny, nx)) for b in range(nb)])
+
+    def all_separate():
+        for (so, o), vs in zip(singles, views):
+            for c, s_ in vs:
+                so.solve(c, s_, out=o, check=False)
+
+    ms_s = timed(all_separate, max(1, min(steps, 3)), side)
+    for so, _ in singles:
+        so.check()
+    del singles, views
+    torch.cuda.empty_cache()
+    upd = sum(nx * ny * nz for nx, ny, nz in shapes) * NDIR * nb
+    return {"workload": "64 subdomains, Nx=Ny in {48,64,96,128}, Nz in {96,128,192}, x 12 bands, FP32 sweep + FP64 Q",
+            "batched_ms": round(ms_b, 3), "separate_ms": round(ms_s, 3), "speedup": round(ms_s / ms_b, 3),
+            "batched_gupd_s": round(upd / (ms_b * 1e-3) / 1e9, 3), "separate_gupd_s": round(upd / (ms_s * 1e-3) / 1e9, 3),
+            "separate": "768 rts_solve calls (one per subdomain and band), same precision",
+            "tile_rows": best, "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
+            "units": st["n_units"], "tiles": st["n_tiles"], "grid": st["grid"], "launch": "cuda graph"}
 
 
 def run_ours(args):
@@ -356,6 +438,10 @@ def run_ours(args):
     else:
         ratio = None
 
+    batched = None
+    if not args.skip_batched:
+        batched = _batched_timing(rts, torch, max(3, min(args.steps, 10)))
+
     cpu = None
     if rank == 0 and not args.skip_cpu_baseline:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -367,7 +453,7 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": st["kernels_per_solve"] * args.steps,
             "phases_ms": phases,
             "wrap": {"max_warmup_planes": st["max_warmup_steps"], "mean_warmup_planes": st["mean_warmup_steps"]},
-            "adjoint_over_forward": ratio, "adjoint": adj}
+            "adjoint_over_forward": ratio, "adjoint": adj, "batched": batched}
     line.update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -457,6 +543,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--grid", default="288,288,288",
                     help="NX,NY,NZ override (profiling of smaller cases); the metric is quoted at 288^3")

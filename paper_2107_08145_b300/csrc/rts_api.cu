@@ -329,7 +329,7 @@ static cudaError_t kernel_occupancy(SweepFn<T> kern, int nt, size_t smem, int *b
 // pairs whose cap fits the CTA size. With `requested` > 0: the tallest tile
 // not above it that fits. Otherwise the score is the plane rows resident per
 // SM, halved when only one CTA fits (one CTA cannot hide its own barrier and
-// neighbour waits). Every unit's tiles must fit on the GPU at once (the
+// neighbour waits) and quartered for tiles taller than 4 rows. Every unit's tiles must fit on the GPU at once (the
 // persistent launch waits on neighbours).
 template <typename T>
 static Tiling choose_fwd(int requested, int npmax, int nqmax, int nsm)
@@ -347,7 +347,10 @@ static Tiling choose_fwd(int requested, int npmax, int nqmax, int nsm)
         if (kernel_occupancy<T>(fwd_kernel<T>(tq, maxr), best.nt, smem, &blocks) != cudaSuccess || blocks < 1)
             continue;
         if ((long long)blocks * nsm < (nqmax + tq - 1) / tq) continue;
-        double score = (double)tq * blocks * (blocks > 1 ? 1.0 : 0.5);
+        // Measured on B300 (rts288x4 and the batched workload): tiles taller than
+        // 4 rows lose more to instruction fetch (their unrolled row code) than
+        // they gain in resident rows, so they are only taken on request.
+        double score = (double)tq * blocks * (blocks > 1 ? 1.0 : 0.5) * (tq <= 4 ? 1.0 : 0.25);
         if (requested > 0) score = tq;  // tallest fitting tile
         if (score > best_score) {
             best_score = score;
