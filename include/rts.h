@@ -103,8 +103,8 @@ typedef struct {
     void *stream;         /* cudaStream_t to run on (NULL = legacy default stream) */
     int adjoint_chunk_bands; /* bands whose intensities rts_adjoint recomputes
                              and keeps at a time (the checkpoint unit;
-                             0 = 1 band); with all bands in one chunk the
-                             forward solve is not repeated */
+                             0 = 1 band); larger chunks run more sweep units
+                             at once and need proportionally more scratch */
 } rts_options;
 
 typedef struct {
@@ -120,6 +120,13 @@ typedef struct {
      * timed_solves solves since the previous call (else 0) */
     int timed_solves;
     float ms_transpose, ms_sweep, ms_reduce, ms_qstep;
+    /* with RTS_FLAG_TIMING: mean milliseconds per rts_adjoint call of its
+     * phases since the previous call: [0] transposes and Q-step adjoints,
+     * [1] forward re-sweeps (checkpoints) and their band reductions,
+     * [2] reverse sweeps, [3] gradient passes and reduction; over
+     * timed_adjoints calls */
+    int timed_adjoints;
+    float ms_adjoint[4];
 } rts_stats;
 
 typedef struct {
@@ -171,16 +178,17 @@ void rts_destroy(rts_handle *h);
  *   L = <gI_top, I_top> + <gJ, J> + <gF, F> + <gQ, Q_rad>
  * (the outputs of rts_solve on the same chi, S, bc) with respect to log chi
  * and S of every band: reverse-mode differentiation of the discrete solve.
- * The paper has no adjoint; this is the transpose of its forward operator:
- *   1. the Q step transposed (cotangents of J_b and F_b, and the direct chi
- *      and S terms of Q_rad);
- *   2. per chunk of adjoint_chunk_bands bands (the checkpoint): the forward
- *      sweep again, keeping the converged intensity of every ray of the chunk
- *      (4 values per point and sweep unit), then the reverse sweep: the
+ * The paper has no adjoint; this is the transpose of its forward operator.
+ * Per chunk of adjoint_chunk_bands bands (the checkpoint):
+ *   1. the forward sweep of the chunk, keeping the converged intensity of
+ *      every ray (4 values per point and sweep unit); its partial sums give
+ *      the chunk's J_b, F_b;
+ *   2. the Q step transposed for those bands (cotangents of J_b and F_b, and
+ *      the direct chi and S terms of Q_rad), then the reverse sweep: the
  *      cotangent of I along each ray, lam_p = lam0_p + sum over the downwind
  *      points r that interpolate from p of beta e_r lam_r, swept in the
- *      reverse plane order with the same tiles, ready flags and periodic-wrap
- *      bound as the forward sweep; then the derivative of each segment's
+ *      reverse plane order with tiles, ready flags and a periodic-wrap
+ *      bound like the forward sweep; then the derivative of each segment's
  *      formal solution with respect to the opacity and source it used,
  *      gathered onto the grid points it was interpolated from;
  *   3. g_logchi = chi * dL/dchi.
@@ -190,8 +198,8 @@ void rts_destroy(rts_handle *h);
  * sweep precision; gJ [Nz][Ny][Nx], gF [3][Nz][Ny][Nx] and gQ [Nz][Ny][Nx]
  * are float64; any cotangent may be NULL (zero). g_logchi and g_S are
  * [B][Nz][Ny][Nx] in the sweep precision (written, not accumulated). All
- * device pointers; outputs must not alias inputs. When gQ is NULL the first
- * forward solve is skipped (J, F enter L linearly). Needs RTS_FLAG_ADJOINT
+ * device pointers; outputs must not alias inputs. When gQ is NULL the band
+ * reductions are skipped (J, F enter L linearly). Needs RTS_FLAG_ADJOINT
  * at create time; allocates nothing and does not synchronise. Device errors
  * as for rts_solve (rts_check). */
 rts_status rts_adjoint(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,

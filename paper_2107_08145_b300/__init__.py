@@ -45,7 +45,7 @@ class Stats(C.Structure):
                 ("mean_warmup_steps", C.c_double), ("device_status", C.c_int), ("grid", C.c_int),
                 ("tile_rows", C.c_int), ("kernels_per_solve", C.c_int), ("timed_solves", C.c_int),
                 ("ms_transpose", C.c_float), ("ms_sweep", C.c_float), ("ms_reduce", C.c_float),
-                ("ms_qstep", C.c_float)]
+                ("ms_qstep", C.c_float), ("timed_adjoints", C.c_int), ("ms_adjoint", C.c_float * 4)]
 
 
 class Boundary(C.Structure):
@@ -309,7 +309,9 @@ class Solver:
         s = Stats()
         rc = self._L.rts_get_stats(self._h, C.byref(s))
         self._err(rc)
-        return {k: getattr(s, k) for k, _ in Stats._fields_ if k != "device_status"}
+        d = {k: getattr(s, k) for k, _ in Stats._fields_ if k not in ("device_status", "ms_adjoint")}
+        d["ms_adjoint"] = list(s.ms_adjoint)
+        return d
 
 
 class Graph:

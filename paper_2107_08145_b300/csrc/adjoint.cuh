@@ -3,71 +3,52 @@
 // log chi and S of every band.
 //
 // The solve is a chain  (chi, S) -> I (per ray, by the sweep recurrence)
-// -> (J_b, F_b) -> Q_rad. Its adjoint, written for this GPU layout:
-//  1. qstep_adjoint_kernel: cotangents of J_b and F_b (through the Q step
+// -> (J_b, F_b) -> Q_rad. Its adjoint, written for this GPU layout, runs per
+// checkpoint chunk of bands:
+//  1. the forward sweep of the chunk again (sweep.cuh), storing per point and
+//     ray of the converged period the segment's dI/d(dtau); its partial sums
+//     give the chunk's J_b and F_b;
+//  2. qstep_adjoint_kernel: cotangents of J_b and F_b (through the Q step
 //     and the band sums) and the direct chi/S terms of the Q step;
-//  2. the forward sweep again, storing the converged I of every ray of a
-//     band chunk (the checkpoint);
 //  3. sweep_adj_kernel: the reverse sweep. For ray d the cotangent of I obeys
 //     lam(p) = lam0(p) + sum_c beta_c e(r_c) lam(r_c), summed over the
 //     downwind points r_c whose upwind corner c is p: the transpose of the
-//     forward interpolation, run over the planes in reverse order with the
-//     same tiles, ready flags and periodic-wrap bound as the forward sweep;
-//  4. adj_pass1/adj_pass2: parallel over points, the derivative of each
-//     segment's formal solution with respect to its opacity and source,
-//     gathered onto the grid points they were interpolated from;
+//     forward interpolation, run over the planes in reverse order with tiles,
+//     ready flags and a periodic-wrap bound like the forward sweep. With lam
+//     known it writes each segment's gradient terms: B = lam dI/d(dtau) ds/2
+//     (opacity, own point and upwind corners), C = lam w_up (source at the
+//     corners) and the own-point chi and S terms; it recomputes the segment's
+//     dtau, e and weights from the same chi as the forward sweep;
+//  4. adj_gather_kernel: adds to every point the B and C of the downwind
+//     points that interpolated from it;
 //  5. adj_reduce_kernel: sum over the band's sweep units, times chi for
 //     d/d log chi.
 #pragma once
 #include "df32.cuh"
+#include "qstep.cuh"
 #include "sweep.cuh"
 
 namespace rts {
-
-// d w_up / dx and d w_p / dx of the linear-in-tau weights
-__device__ __forceinline__ void seg_derivs(double x, double e, double &dwu, double &dwp)
-{
-    if (x < 0.01) {
-        // derivatives of the Taylor series of w_up and w_p
-        dwp = 0.5 - x * (2.0 / 6.0 - x * (3.0 / 24.0 - x * (4.0 / 120.0 - x * (5.0 / 720.0 - x * (6.0 / 5040.0)))));
-        dwu = 0.5 - x * (4.0 / 6.0 - x * (9.0 / 24.0 - x * (16.0 / 120.0 - x * (25.0 / 720.0 - x * (36.0 / 5040.0)))));
-    } else {
-        const double ome = -expm1(-x);
-        dwu = e / x - ome / (x * x) + e;
-        dwp = ome / (x * x) - e / x;
-    }
-}
-__device__ __forceinline__ void seg_derivs(float x, float e, float &dwu, float &dwp)
-{
-    if (x < 0.25f) {
-        dwp = 0.5f - x * (2.f / 6.f - x * (3.f / 24.f - x * (4.f / 120.f - x * (5.f / 720.f - x * (6.f / 5040.f - x * (7.f / 40320.f))))));
-        dwu = 0.5f - x * (4.f / 6.f - x * (9.f / 24.f - x * (16.f / 120.f - x * (25.f / 720.f - x * (36.f / 5040.f - x * (49.f / 40320.f))))));
-    } else {
-        const float r = 1.f / x;
-        const float ome = 1.f - e;
-        dwu = e * r - ome * r * r + e;
-        dwp = ome * r * r - e * r;
-    }
-}
 
 // ---------------------------------------------------------------------------
 // 1. Q step adjoint (natural layout, one thread per point, loop over bands)
 // ---------------------------------------------------------------------------
 struct QAdjParams {
     int nx, ny, nz, nbands;
-    double dx, dy, dz;
-    double thin;  // min(dx, dy, dz) / tau_switch
+    double inv2dx, inv2dy, inv2dz, invdz;  // stencil coefficients
+    double thin;                           // min(dx, dy, dz) / tau_switch
 };
 
 // coefficient of F_z(level k) in the z part of div F at level q: central
 // differences inside, first-order one-sided at the bottom and top levels,
 // nothing when there is a single level
-__device__ __forceinline__ double coef_z(int q, int k, int nz, double dz)
+__device__ __forceinline__ double coef_z(int q, int k, const QAdjParams &P)
 {
+    const int nz = P.nz;
     if (nz == 1) return 0.0;
-    if (q == 0) return k == 1 ? 1.0 / dz : (k == 0 ? -1.0 / dz : 0.0);
-    if (q == nz - 1) return k == nz - 1 ? 1.0 / dz : (k == nz - 2 ? -1.0 / dz : 0.0);
-    return k == q + 1 ? 0.5 / dz : (k == q - 1 ? -0.5 / dz : 0.0);
+    if (q == 0) return k == 1 ? P.invdz : (k == 0 ? -P.invdz : 0.0);
+    if (q == nz - 1) return k == nz - 1 ? P.invdz : (k == nz - 2 ? -P.invdz : 0.0);
+    return k == q + 1 ? P.inv2dz : (k == q - 1 ? -P.inv2dz : 0.0);
 }
 
 // Per band b and point p, with u = gQ (1 - om_b):
@@ -75,12 +56,15 @@ __device__ __forceinline__ double coef_z(int q, int k, int nz, double dz)
 //   direct d/dchi_b = gQ (om_b 4 pi (J_b - S_b) + dom_b/dchi_b (QJ_b - QF_b)),
 //   direct d/dS_b   = -gQ om_b 4 pi chi_b,
 // QJ_b = 4 pi chi_b (J_b - S_b), QF_b = -div F_b, D the divergence stencil.
+// The blend weights are evaluated exactly as the forward Q step does (in the
+// sweep precision, blend_weights), so this is the derivative of the computed
+// function. Bands b0 .. b1-1; JF, lam0, direct are indexed by band.
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restrict__ JF, const T *__restrict__ chi,
                                                              const T *__restrict__ S, const double *__restrict__ gJ,
                                                              const double *__restrict__ gF,
-                                                             const double *__restrict__ gQ, QAdjParams P,
-                                                             T *__restrict__ lam0, T *__restrict__ direct)
+                                                             const double *__restrict__ gQ, QAdjParams P, int b0,
+                                                             int b1, T *__restrict__ lam0, T *__restrict__ direct)
 {
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
@@ -93,42 +77,49 @@ __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restric
     const long long pxp = p - i + ip, pxm = p - i + im;
     const long long pyp = p + (long long)(jp - j) * nx, pym = p + (long long)(jm - j) * nx;
     const double four_pi = 12.566370614359172953850573533118;
+    const T thin = (T)P.thin;
     const double gq = gQ ? gQ[p] : 0.0;
-    for (int b = 0; b < P.nbands; ++b) {
+    for (int b = b0; b < b1; ++b) {
         const T *cb = chi + (long long)b * N;
         const Acc *jf = JF + (long long)b * 4 * N;
-        auto u_at = [&](long long q) -> double {
-            if (!gQ) return 0.0;
-            return gQ[q] * -expm1(-(double)cb[q] * P.thin);
+        // cancelling differences in FP64, the rest in the sweep precision T
+        auto u_at = [&](long long q) -> T {  // gQ (1 - om_b) at point q
+            if (!gQ) return T(0);
+            T om, omc;
+            blend_weights(cb[q], thin, om, omc);
+            return (T)gQ[q] * omc;
         };
-        const double c = (double)cb[p];
-        const double om = exp(-c * P.thin);
-        double gJb = gJ ? gJ[p] : 0.0, gchi = 0.0, gs = 0.0;
+        T om, omc;
+        blend_weights(cb[p], thin, om, omc);
+        const T c = cb[p];
+        const T fpc = (T)four_pi * c;
+        double gJb = gJ ? gJ[p] : 0.0;
+        T gchi = 0, gs = 0;
         if (gQ) {  // J_b and F_b of the forward solve are read only when Q_rad enters L
             double divz = 0.0;
             for (int q = k - 1; q <= k + 1; ++q) {
                 if (q < 0 || q >= P.nz) continue;
-                const double cf = coef_z(k, q, P.nz, P.dz);
+                const double cf = coef_z(k, q, P);
                 if (cf != 0.0) divz += cf * acc_to_double(jf[3 * N + (long long)q * pl + (long long)j * nx + i]);
             }
-            const double qf = -((acc_to_double(jf[N + pxp]) - acc_to_double(jf[N + pxm])) * 0.5 / P.dx +
-                                (acc_to_double(jf[2 * N + pyp]) - acc_to_double(jf[2 * N + pym])) * 0.5 / P.dy + divz);
-            const double s = (double)S[(long long)b * N + p];
-            const double Jb = acc_to_double(jf[p]);
-            const double qj = four_pi * c * (Jb - s);
-            gJb += gq * om * four_pi * c;
-            gchi = gq * (om * four_pi * (Jb - s) - P.thin * om * (qj - qf));
-            gs = -gq * om * four_pi * c;
+            const T qf = (T)(-((acc_to_double(jf[N + pxp]) - acc_to_double(jf[N + pxm])) * P.inv2dx +
+                               (acc_to_double(jf[2 * N + pyp]) - acc_to_double(jf[2 * N + pym])) * P.inv2dy + divz));
+            const T dJ = (T)(acc_to_double(jf[p]) - (double)S[(long long)b * N + p]);  // J_b - S_b
+            const T gqT = (T)gq;
+            const T qj = fpc * dJ;
+            gJb += gq * (double)(om * fpc);
+            gchi = gqT * (om * (T)four_pi * dJ - thin * om * (qj - qf));
+            gs = -gqT * om * fpc;
         }
-        const double gFx = (gF ? gF[p] : 0.0) + (u_at(pxp) - u_at(pxm)) * 0.5 / P.dx;
-        const double gFy = (gF ? gF[N + p] : 0.0) + (u_at(pyp) - u_at(pym)) * 0.5 / P.dy;
-        double dTz = 0.0;  // (D_z^T u)(k) = sum_q u(q) coef_z(q, k)
+        const double gFx = (gF ? gF[p] : 0.0) + (double)((u_at(pxp) - u_at(pxm)) * (T)P.inv2dx);
+        const double gFy = (gF ? gF[N + p] : 0.0) + (double)((u_at(pyp) - u_at(pym)) * (T)P.inv2dy);
+        T dTz = 0;  // (D_z^T u)(k) = sum_q u(q) coef_z(q, k)
         for (int q = k - 1; q <= k + 1; ++q) {
             if (q < 0 || q >= P.nz) continue;
-            const double cf = coef_z(q, k, P.nz, P.dz);
-            if (cf != 0.0) dTz += u_at((long long)q * pl + (long long)j * nx + i) * cf;
+            const T cf = (T)coef_z(q, k, P);
+            if (cf != T(0)) dTz += u_at((long long)q * pl + (long long)j * nx + i) * cf;
         }
-        const double gFz = (gF ? gF[2 * N + p] : 0.0) - dTz;
+        const double gFz = (gF ? gF[2 * N + p] : 0.0) - (double)dTz;
         T *l0 = lam0 + (long long)b * 4 * N;
         l0[p] = (T)gJb;
         l0[N + p] = (T)gFx;
@@ -143,22 +134,22 @@ __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restric
 // ---------------------------------------------------------------------------
 // 3. Reverse sweep of one tile (cotangent lam of the rays of one unit)
 // ---------------------------------------------------------------------------
-// sum_c beta_c A(r_c): r_c are the downwind points whose corner c is this one
-template <typename T, int SP, int SQ>
-__device__ __forceinline__ T gather_down(const T *__restrict__ A, int npp, T b0, T b1, T b2, T b3)
+// Shared memory of a reverse tile: A = e lam of the 4 slots (the downwind
+// plane, kept once: new rows stay in registers until every thread has read
+// it), the two seed-error bounds (float), and chi of three planes (the own
+// plane, its forward-upwind plane and the next one in flight).
+enum { AF_A = 4, AF_X = 3, AF_G = 2 };
+// gradient terms written by the reverse sweep per point of a unit: B of the 4
+// slots, C of the 4 slots, the own chi and S terms
+constexpr int GRAD_CH = 2 * MAXD + 2;
+
+template <typename T>
+__host__ __device__ constexpr size_t adj_tile_smem_bytes(int tq, int np)
 {
-    const int oq = SQ * npp;
-    return b0 * A[0] + b1 * A[SP] + b2 * A[oq] + b3 * A[oq + SP];
-}
-// forward-upwind interpolation (corners at -SP, -SQ)
-template <typename T, int SP, int SQ>
-__device__ __forceinline__ T interp_up(const T *__restrict__ X, int npp, T b0, T b1, T b2, T b3)
-{
-    const int oq = -SQ * npp;
-    return b0 * X[0] + b1 * X[-SP] + b2 * X[oq] + b3 * X[oq - SP];
+    return (size_t)(tq + 2) * (np + 2) * ((AF_A + AF_X) * sizeof(T) + AF_G * sizeof(float));
 }
 
-enum { FA_A0 = 0, FA_GU = 4, FA_GD = 5, NPARF_A = 6, NFIELD_A = 2 * NPARF_A + 2 };
+__device__ __forceinline__ void cp_async_wait_newest_pending() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 template <typename T, int TQ>
 __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug, int uidx, int r, int gt,
@@ -174,7 +165,9 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     const T *__restrict__ chi = (Ug->transposed ? a.chiT : a.chi) + Ug->in_off;
     const T *__restrict__ l0 = (Ug->transposed ? a.lam0T : a.lam0) + (long long)band * 4 * N;
     const T *const gitop = a.gitop ? a.gitop + Ug->top_off : nullptr;
-    T *const lstore = a.store + (long long)(uidx - a.unit_base) * 4 * N;
+    // gradient terms of this unit: B [4][N], C [4][N], own chi / S terms [2][N]
+    T *const gout = a.store + (long long)(uidx - a.unit_base) * GRAD_CH * N;
+    const T *const ck = a.ckpt + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N;
     const long long tile_stride = (long long)2 * 2 * HALO_CH * NP;
     T *const halo_base = a.halo + Ug->halo_off;
     T *const myhalo = halo_base + (long long)r * tile_stride;
@@ -187,9 +180,10 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     const int c = p + 1;
     const int npp = NP + 2;
     const int FL = RW * npp;
-    T *const sm = (T *)smem;
-    auto fA = [&](int par, int f) -> T * { return sm + (par * NPARF_A + f) * FL; };
-    auto fX = [&](int t) -> T * { return sm + (2 * NPARF_A + (t & 1)) * FL; };
+    T *const sA = (T *)smem;                    // A of slot d: sA + d * FL
+    T *const sX = sA + AF_A * FL;               // chi of reverse step t: sX + (t % 3) * FL
+    float *const sG = (float *)(sX + AF_X * FL);
+    auto fX = [&](int t) -> T * { return sX + (t % 3) * FL; };
 
     __shared__ DirConst<T> D;
     __shared__ float s_wmax[32];
@@ -203,7 +197,7 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
         D.cJ[d] = (T)Ug->cJ[d];
         for (int cc = 0; cc < 3; ++cc) D.cF[cc][d] = (T)Ug->cF[cc][d];
         D.up[d] = Ug->up[d];
-        D.bck[d] = 0;
+        D.bck[d] = Ug->up[d] ? a.bc_bottom : a.bc_top;
         D.udx[d] = Ug->udx[d];
         D.active[d] = Ug->active[d];
     }
@@ -220,12 +214,12 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     const bool has_lower = qper || r > 0;
     const bool has_upper = qper || r < ntl - 1;
 
-    auto put = [&](T *f, int k, T v) {
+    auto put = [&](auto *f, int k, auto v) {
         f[k * npp + c] = v;
         if (p == 0) f[k * npp + NP + 1] = v;
         if (p == NP - 1) f[k * npp] = v;
     };
-    // chi rows of reverse step t into slot t & 1
+    // chi rows of reverse step t into slot t % 3
     auto prefetch = [&](int t) {
         if (act) {
             const long long mo = (long long)plane_of(t, NM, msa) * sM + p;
@@ -243,27 +237,32 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     };
 
     __syncthreads();
+    int upm = 0, actm = 0;
+    for (int d = 0; d < MAXD; ++d) {
+        upm |= D.up[d] ? 1 << d : 0;
+        actm |= D.active[d] ? 1 << d : 0;
+    }
     // prologue: the (downwind) plane before the first reverse step carries
     // A = 0; for the periodic groups that is the seed, with a unit bound on
     // the points that are not set. Rows outside a non-periodic Q range stay
-    // zero in both parities for the whole sweep.
+    // zero for the whole sweep.
     if (act) {
-        for (int par = 0; par < 2; ++par)
-            for (int k = 0; k < nrows + 2; ++k) {
-                const int q = s_q[k];
-                for (int d = 0; d < MAXD; ++d) put(fA(par, FA_A0 + d), k, T(0));
-                T gu = 0, gd = 0;
-                if (par == 1 && wrap && q >= 0) {
-                    if (q != 0) gu = 1;
-                    if (q != NQ - 1) gd = 1;
-                }
-                put(fA(par, FA_GU), k, gu);
-                put(fA(par, FA_GD), k, gd);
+        for (int k = 0; k < nrows + 2; ++k) {
+            const int q = s_q[k];
+            for (int d = 0; d < MAXD; ++d) put(sA + d * FL, k, T(0));
+            float gu = 0.f, gd = 0.f;
+            if (wrap && q >= 0) {
+                if (q != 0) gu = 1.f;
+                if (q != NQ - 1) gd = 1.f;
             }
+            put(sG, k, gu);
+            put(sG + FL, k, gd);
+        }
     }
     prefetch(0);
     prefetch(1);
     cp_async_wait_all();
+    prefetch(2);
     __syncthreads();
 
     int t_acc = wrap ? -1 : 0;
@@ -272,118 +271,139 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
 
     for (int t = 0;; ++t) {
         const int m = plane_of(t, NM, msa);
-        const int cur = t & 1, prv = cur ^ 1;
         if (t_acc < 0 && s_ctl[1]) {
             t_acc = t;
             if (r == 0 && tid == 0) a.unit_tacc[uidx] = t;
         }
         if (wrap && t_acc < 0 && t >= warm_cap) {
             if (tid == 0) atomicOr(a.status, ST_NOCONV);
+            cp_async_wait_all();
             return;
         }
         const bool acc = t_acc >= 0;
         const bool last = acc && (t - t_acc == NM - 1);
-        T b[MAXD][4], hds[MAXD];
-#pragma unroll
-        for (int d = 0; d < MAXD; ++d) {
-            hds[d] = D.hds[d];
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) b[d][cc] = D.beta[d][cc];
-        }
         const T *Xc = fX(t), *Xn = fX(t + 1);  // chi of this plane and of its forward-upwind plane
         // a z group's last reverse plane is its boundary layer (set points)
         const bool bnd_plane = !wrap && t == NM - 1;
         const bool top_plane = axis == 2 && t == 0 && sa > 0;
         float gmax = 0.f;
 
-        auto do_row = [&](int k) {
+        struct Row {
+            T A[MAXD];      // e lam of the 4 slots (zero at set points)
+            float g[2];     // bounds of the up / down rays (warm-up only)
+        };
+        Row nR[TQ], rl;
+
+        // row k (1..nrows): lam from the downwind plane in shared memory, the
+        // point's own cotangents, then A = e lam for the upwind plane
+        auto do_row = [&](int k) -> Row {
+            Row out;
             const int q = q0 + k - 1;
             const int o = k * npp + c;
             const long long goff = (long long)m * sM + (long long)q * sQ + p;
             const T gJ = l0[goff], gFx = l0[N + goff], gFy = l0[2 * N + goff], gFz = l0[3 * N + goff];
             const bool top = axis == 2 ? top_plane : q == NQ - 1;
-            T lam[MAXD];
-            lam[0] = gather_down<T, 1, 1>(fA(prv, FA_A0 + 0) + o, npp, b[0][0], b[0][1], b[0][2], b[0][3]);
-            lam[1] = gather_down<T, -1, 1>(fA(prv, FA_A0 + 1) + o, npp, b[1][0], b[1][1], b[1][2], b[1][3]);
-            lam[2] = gather_down<T, 1, -1>(fA(prv, FA_A0 + 2) + o, npp, b[2][0], b[2][1], b[2][2], b[2][3]);
-            lam[3] = gather_down<T, -1, -1>(fA(prv, FA_A0 + 3) + o, npp, b[3][0], b[3][1], b[3][2], b[3][3]);
-            float gu = 0.f, gd = 0.f;
-            if (!acc) {
-                const float g0 = (float)gather_down<T, 1, 1>(fA(prv, D.up[0] ? FA_GU : FA_GD) + o, npp, b[0][0], b[0][1], b[0][2], b[0][3]);
-                const float g1 = (float)gather_down<T, -1, 1>(fA(prv, D.up[1] ? FA_GU : FA_GD) + o, npp, b[1][0], b[1][1], b[1][2], b[1][3]);
-                const float g2 = (float)gather_down<T, 1, -1>(fA(prv, D.up[2] ? FA_GU : FA_GD) + o, npp, b[2][0], b[2][1], b[2][2], b[2][3]);
-                const float g3 = (float)gather_down<T, -1, -1>(fA(prv, D.up[3] ? FA_GU : FA_GD) + o, npp, b[3][0], b[3][1], b[3][2], b[3][3]);
-                gu = fmaxf(fmaxf(D.up[0] ? g0 : 0.f, D.up[1] ? g1 : 0.f), fmaxf(D.up[2] ? g2 : 0.f, D.up[3] ? g3 : 0.f));
-                gd = fmaxf(fmaxf(D.up[0] ? 0.f : g0, D.up[1] ? 0.f : g1), fmaxf(D.up[2] ? 0.f : g2, D.up[3] ? 0.f : g3));
-            }
+            // forward-upwind plane's chi on the 3 x 3 neighbourhood, shared by the rays
+            T xs[3][3];
+#pragma unroll
+            for (int dq = 0; dq < 3; ++dq)
+#pragma unroll
+                for (int dp = 0; dp < 3; ++dp) xs[dq][dp] = Xn[o + (dq - 1) * npp + dp - 1];
             const T xp = Xc[o];
-            T Aout[MAXD];
-            float egu = 0.f, egd = 0.f;
+            T hd[MAXD], cw[4][MAXD];
+            ld4(D.hds, hd[0], hd[1], hd[2], hd[3]);
+            ld4(D.cJ, cw[0][0], cw[0][1], cw[0][2], cw[0][3]);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) ld4(D.cF[cc], cw[cc + 1][0], cw[cc + 1][1], cw[cc + 1][2], cw[cc + 1][3]);
+            float gu = 0.f, gd = 0.f, egu = 0.f, egd = 0.f;
+            T own_chi = 0, own_S = 0;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) {
-                // direct cotangent of this ray's intensity at this point
-                lam[d] += D.cJ[d] * gJ + D.cF[0][d] * gFx + D.cF[1][d] * gFy + D.cF[2][d] * gFz;
-                if (gitop && top && D.up[d] && D.active[d]) {
+                const int SP = (d & 1) ? -1 : 1, SQ = (d & 2) ? -1 : 1;  // compile time after unrolling
+                T b0, b1, b2, b3;
+                ld4(D.beta[d], b0, b1, b2, b3);
+                // downwind points r_c whose corner c is this point: offsets (+SP, +SQ)
+                const T *Ap = sA + d * FL + o;
+                const int oq = SQ * npp;
+                T lam = b0 * Ap[0] + b1 * Ap[SP] + b2 * Ap[oq] + b3 * Ap[oq + SP];
+                lam += cw[0][d] * gJ + cw[1][d] * gFx + cw[2][d] * gFy + cw[3][d] * gFz;
+                const bool isup = (upm >> d) & 1;
+                if (gitop && top && isup && ((actm >> d) & 1)) {
                     int i, j;
                     natural_ij(axis, p, q, m, i, j);
-                    lam[d] += gitop[((long long)D.udx[d] * uny + j) * unx + i];
+                    lam += gitop[((long long)D.udx[d] * uny + j) * unx + i];
                 }
-                if (!D.active[d]) lam[d] = T(0);
-                const bool set = wrap ? (D.up[d] ? q == 0 : q == NQ - 1) : bnd_plane;
-                T e = T(0);
+                if (!((actm >> d) & 1)) lam = T(0);
+                const bool set = wrap ? (isup ? q == 0 : q == NQ - 1) : bnd_plane;
+                T e = T(0), wu = T(0), wp = T(0);
                 if (!set) {
-                    T xup;
-                    if (d == 0) xup = interp_up<T, 1, 1>(Xn + o, npp, b[0][0], b[0][1], b[0][2], b[0][3]);
-                    else if (d == 1) xup = interp_up<T, -1, 1>(Xn + o, npp, b[1][0], b[1][1], b[1][2], b[1][3]);
-                    else if (d == 2) xup = interp_up<T, 1, -1>(Xn + o, npp, b[2][0], b[2][1], b[2][2], b[2][3]);
-                    else xup = interp_up<T, -1, -1>(Xn + o, npp, b[3][0], b[3][1], b[3][2], b[3][3]);
-                    T wu, wp;
-                    seg_weights(hds[d] * (xup + xp), e, wu, wp);
+                    const T xup = b0 * xs[1][1] + b1 * xs[1][1 - SP] + b2 * xs[1 - SQ][1] + b3 * xs[1 - SQ][1 - SP];
+                    seg_weights(hd[d] * (xup + xp), e, wu, wp);
                 }
-                Aout[d] = e * lam[d];
+                out.A[d] = e * lam;
+                if (acc) {
+                    // gradient terms of this point's segment (lam known now):
+                    // B = lam dI/dx ds/2 (to chi here and at the corners), C = lam w_up
+                    // (to S at the corners), lam w_p (to S here); set points with
+                    // I = S pass lam to S
+                    T Bv = 0, Cv = 0;
+                    if (((actm >> d) & 1) && !set) {
+                        const T dI = ck[(long long)d * N + goff];
+                        Bv = lam * dI * hd[d];
+                        Cv = lam * wu;
+                        own_chi += Bv;
+                        own_S += lam * wp;
+                    } else if (((actm >> d) & 1) && D.bck[d] == 1) {
+                        own_S += lam;
+                    }
+                    gout[(long long)d * N + goff] = Bv;
+                    gout[(long long)(MAXD + d) * N + goff] = Cv;
+                }
                 if (!acc) {
-                    if (D.up[d]) egu = fmaxf(egu, (float)e); else egd = fmaxf(egd, (float)e);
+                    const float *Gp = sG + (isup ? 0 : FL) + o;
+                    const float gg = (float)b0 * Gp[0] + (float)b1 * Gp[SP] + (float)b2 * Gp[oq] + (float)b3 * Gp[oq + SP];
+                    if (isup) { gu = fmaxf(gu, gg); egu = fmaxf(egu, (float)e); }
+                    else { gd = fmaxf(gd, gg); egd = fmaxf(egd, (float)e); }
                 }
+            }
+            if (acc) {
+                gout[(long long)(2 * MAXD) * N + goff] = own_chi;
+                gout[(long long)(2 * MAXD + 1) * N + goff] = own_S;
             }
             // the bound carried to the upwind plane: e * g (max over the rays of each set)
             gu *= egu;
             gd *= egd;
             if (wrap && q == 0) gu = 0.f;
             if (wrap && q == NQ - 1) gd = 0.f;
+            out.g[0] = gu;
+            out.g[1] = gd;
+            if (!acc) gmax = fmaxf(gmax, fmaxf(gu, gd));
+            return out;
+        };
+        auto to_ring = [&](int sd, Row rw) {
+            T *dst = myhalo + ((long long)((t & 1) * 2 + sd) * HALO_CH) * NP + p;
 #pragma unroll
-            for (int d = 0; d < MAXD; ++d) put(fA(cur, FA_A0 + d), k, Aout[d]);
+            for (int d = 0; d < MAXD; ++d) dst[(long long)d * NP] = rw.A[d];
             if (!acc) {
-                put(fA(cur, FA_GU), k, (T)gu);
-                put(fA(cur, FA_GD), k, (T)gd);
-                gmax = fmaxf(gmax, fmaxf(gu, gd));
-            } else {
-#pragma unroll
-                for (int d = 0; d < MAXD; ++d) lstore[(long long)d * N + goff] = lam[d];
-            }
-            if (k == 1 || k == nrows) {
-                for (int sd = 0; sd < 2; ++sd) {
-                    if (!((sd == 0 && k == 1) || (sd == 1 && k == nrows))) continue;
-                    T *dst = myhalo + ((long long)(cur * 2 + sd) * HALO_CH) * NP + p;
-                    for (int d = 0; d < MAXD; ++d) dst[(long long)d * NP] = Aout[d];
-                    if (!acc) {
-                        dst[(long long)MAXD * NP] = (T)gu;
-                        dst[(long long)(MAXD + 1) * NP] = (T)gd;
-                    }
-                }
+                dst[(long long)MAXD * NP] = (T)rw.g[0];
+                dst[(long long)(MAXD + 1) * NP] = (T)rw.g[1];
             }
         };
 
         if (act) {
-#pragma unroll 1
-            for (int k = 2; k < nrows; ++k) do_row(k);
+#pragma unroll
+            for (int k = 2; k < TQ; ++k)
+                if (k < nrows) nR[k - 1] = do_row(k);
         }
-        if (t > 0 && act) {
-            bool ok = true;
-            if (has_lower) ok = wait_flag_geq(a.flags + tile0 + lower, t, a.status, a.timeout_ns);
-            if (ok && has_upper) ok = wait_flag_geq(a.flags + tile0 + upper, t, a.status, a.timeout_ns);
-            if (!ok) {
-                s_ctl[0] = 1;
-            } else {
+        if (t > 0) {
+            if (tid == 0) {
+                bool ok = true;
+                if (has_lower) ok = wait_flag_geq(a.flags + tile0 + lower, t, a.status, a.timeout_ns);
+                if (ok && has_upper) ok = wait_flag_geq(a.flags + tile0 + upper, t, a.status, a.timeout_ns);
+                if (!ok) s_ctl[0] = 1;
+            }
+            __syncthreads();  // B0: the neighbours' rows of step t-1 are published (or the wait failed)
+            if (act && !s_ctl[0]) {
                 const int hslot = (t - 1) & 1;
                 for (int side = 0; side < 2; ++side) {
                     if (side == 0 ? !has_lower : !has_upper) continue;
@@ -396,10 +416,10 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
                     for (int ch = 0; ch < HALO_CH; ++ch)
                         hv[ch] = (ch < MAXD || !acc) ? ld_cg(src + (long long)ch * NP) : T(0);
 #pragma unroll
-                    for (int d = 0; d < MAXD; ++d) put(fA(prv, FA_A0 + d), row, hv[d]);
+                    for (int d = 0; d < MAXD; ++d) put(sA + d * FL, row, hv[d]);
                     if (!acc) {
-                        put(fA(prv, FA_GU), row, hv[MAXD]);
-                        put(fA(prv, FA_GD), row, hv[MAXD + 1]);
+                        put(sG, row, (float)hv[MAXD]);
+                        put(sG + FL, row, (float)hv[MAXD + 1]);
                     }
                 }
             }
@@ -410,8 +430,10 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
             return;
         }
         if (act) {
-            do_row(1);
-            if (nrows > 1) do_row(nrows);
+            nR[0] = do_row(1);
+            to_ring(0, nR[0]);
+            rl = nrows == 1 ? nR[0] : do_row(nrows);
+            to_ring(1, rl);
         }
         if (!acc) {
             for (int o = 16; o; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
@@ -433,7 +455,7 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
             }
             if (!ok) s_ctl[0] = 1;
         }
-        __syncthreads();  // B2: plane t complete; chi of plane t no longer read
+        __syncthreads();  // B2: step t's edge rows are in the ring; the downwind plane is no longer read
         if (tid == 0) {
             st_release(a.flags + gt, t + 1);
             if (!acc) {
@@ -445,18 +467,36 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
                 red_release_add(a.gcnt + (long long)uidx * a.R + slot, 1u);
             }
         }
-        if (s_ctl[0]) return;
+        if (s_ctl[0]) {
+            cp_async_wait_all();
+            return;
+        }
+        auto write_row = [&](int kk, Row rw) {
+#pragma unroll
+            for (int d = 0; d < MAXD; ++d) put(sA + d * FL, kk + 1, rw.A[d]);
+            if (!acc) {
+                put(sG, kk + 1, rw.g[0]);
+                put(sG + FL, kk + 1, rw.g[1]);
+            }
+        };
+        if (act) {
+#pragma unroll
+            for (int kk = 0; kk < TQ - 1; ++kk)
+                if (kk < nrows - 1) write_row(kk, nR[kk]);
+            write_row(nrows - 1, rl);
+        }
         if (last) break;
-        // chi of plane t+2 into the slot of plane t; needed across columns at
-        // step t+1, so wait and synchronise before it is read
-        prefetch(t + 2);
-        cp_async_wait_all();
-        __syncthreads();
+        // chi of step t+3 into the slot of step t; step t+2's copy (issued a
+        // step ago) must be complete before the barrier
+        prefetch(t + 3);
+        cp_async_wait_newest_pending();
+        __syncthreads();  // B3
     }
+    cp_async_wait_all();
 }
 
-template <typename T, int TQ>
-__global__ void __launch_bounds__(1024) sweep_adj_kernel(SweepArgs<T> a)
+template <typename T, int TQ, int MAXR>
+__global__ void __maxnreg__(MAXR) sweep_adj_kernel(SweepArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;
@@ -476,108 +516,69 @@ __global__ void __launch_bounds__(1024) sweep_adj_kernel(SweepArgs<T> a)
 }
 
 // ---------------------------------------------------------------------------
-// 4. Gradient of each segment, gathered to the grid (parallel over points)
+// 4. Segment gradient terms gathered onto the corners they interpolated from
 // ---------------------------------------------------------------------------
 template <typename T>
 struct GradArgs {
     const SweepUnit *units;
     int unit_base;
-    const T *chi, *S, *chiT, *ST;
-    const T *I;       // stored forward I, [units][4][N]
-    T *LB;            // in: lam [units][4][N]; pass 1 turns it into B = dL/d dtau * ds/2
-    T *C;             // [units][4][N]: lam * w_up
-    T *G;             // [units][2][N]: own terms (pass 1), then the gradients (pass 2)
-    int bc_bottom, bc_top;
+    T *grad;          // [units][GRAD_CH][N]: B, C (read), own terms (updated in place)
 };
 
-// point (p, q, m) of a unit, one thread per p; blockIdx.y = q, blockIdx.z = m + NM * (u - unit_base)
+// a unit's ray constants in the sweep precision, converted once per block
 template <typename T>
-__global__ void __launch_bounds__(128) adj_pass1_kernel(GradArgs<T> g, int maxNM)
+struct PassConst {
+    T beta[MAXD][4], hds[MAXD];
+    int active, up;
+};
+template <typename T>
+__device__ __forceinline__ void load_pass_const(const SweepUnit &U, PassConst<T> &K)
 {
-    const int uu = blockIdx.z / maxNM, m = blockIdx.z % maxNM;
-    const SweepUnit &U = g.units[g.unit_base + uu];
-    const int NP = U.NP, NQ = U.NQ, NM = U.NM;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
-    if (m >= NM || q >= NQ || p >= NP) return;
-    const long long N = U.N, sQ = U.sQ, sM = U.sM;
-    const T *chi = (U.transposed ? g.chiT : g.chi) + U.in_off;
-    const T *S = (U.transposed ? g.ST : g.S) + U.in_off;
-    const T *I = g.I + (long long)uu * 4 * N;
-    T *LB = g.LB + (long long)uu * 4 * N;
-    T *C = g.C + (long long)uu * 4 * N;
-    T *G = g.G + (long long)uu * 2 * N;
-    const long long off = (long long)m * sM + (long long)q * sQ + p;
-    const int mu = U.wrap ? (m - U.sa + NM) % NM : m - U.sa;  // forward-upwind plane
-    const bool zbnd = !U.wrap && (mu < 0 || mu >= NM);
-    T own_chi = 0, own_S = 0;
-    for (int d = 0; d < MAXD; ++d) {
-        const T lam = LB[(long long)d * N + off];
-        T Bv = 0, Cv = 0;
-        const int sP = (d & 1) ? -1 : 1, sQd = (d & 2) ? -1 : 1;
-        const bool set = U.wrap ? (U.up[d] ? q == 0 : q == NQ - 1) : zbnd;
-        if (!U.active[d]) {
-        } else if (set) {
-            const int kind = U.up[d] ? g.bc_bottom : g.bc_top;
-            if (kind == 1) own_S += lam;  // I = S on the boundary layer
-        } else {
-            T Iup = 0, Sup = 0, Xup = 0;
-            for (int cc = 0; cc < 4; ++cc) {
-                int pc = p - ((cc & 1) ? sP : 0);
-                pc = (pc + NP) % NP;
-                int qc = q - ((cc & 2) ? sQd : 0);
-                if (U.qper) qc = (qc + NQ) % NQ;
-                const long long oc = (long long)mu * sM + (long long)qc * sQ + pc;
-                const T bt = (T)U.beta[d][cc];
-                Iup += bt * I[(long long)d * N + oc];
-                Sup += bt * S[oc];
-                Xup += bt * chi[oc];
-            }
-            const T hds = (T)(0.5 * U.ds[d]);
-            const T x = hds * (Xup + chi[off]);
-            T e, wu, wp, dwu, dwp;
-            seg_weights(x, e, wu, wp);
-            seg_derivs(x, e, dwu, dwp);
-            const T gdt = lam * (-e * Iup + dwu * Sup + dwp * S[off]);
-            Bv = gdt * hds;
-            Cv = lam * wu;
-            own_chi += Bv;
-            own_S += lam * wp;
+    if (threadIdx.x < MAXD * 4) K.beta[threadIdx.x >> 2][threadIdx.x & 3] = (T)U.beta[threadIdx.x >> 2][threadIdx.x & 3];
+    if (threadIdx.x < MAXD) K.hds[threadIdx.x] = (T)(0.5 * U.ds[threadIdx.x]);
+    if (threadIdx.x == 0) {
+        int a = 0, u = 0;
+        for (int d = 0; d < MAXD; ++d) {
+            a |= U.active[d] ? 1 << d : 0;
+            u |= U.up[d] ? 1 << d : 0;
         }
-        LB[(long long)d * N + off] = Bv;
-        C[(long long)d * N + off] = Cv;
+        K.active = a;
+        K.up = u;
     }
-    G[off] = own_chi;
-    G[N + off] = own_S;
+    __syncthreads();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) adj_pass2_kernel(GradArgs<T> g, int maxNM)
+__global__ void __launch_bounds__(128) adj_gather_kernel(GradArgs<T> g, int maxNM)
 {
     const int uu = blockIdx.z / maxNM, m = blockIdx.z % maxNM;
     const SweepUnit &U = g.units[g.unit_base + uu];
+    __shared__ PassConst<T> K;
+    load_pass_const(U, K);
     const int NP = U.NP, NQ = U.NQ, NM = U.NM;
     const int p = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
     if (m >= NM || q >= NQ || p >= NP) return;
     const long long N = U.N, sQ = U.sQ, sM = U.sM;
-    const T *B = g.LB + (long long)uu * 4 * N;
-    const T *C = g.C + (long long)uu * 4 * N;
-    T *G = g.G + (long long)uu * 2 * N;
+    const T *B = g.grad + (long long)uu * GRAD_CH * N;
+    const T *C = B + MAXD * N;
+    T *G = g.grad + (long long)uu * GRAD_CH * N + 2 * MAXD * N;
     const long long off = (long long)m * sM + (long long)q * sQ + p;
-    const int md = U.wrap ? (m + U.sa + NM) % NM : m + U.sa;  // forward-downwind plane
+    int md = m + U.sa;  // forward-downwind plane
+    if (U.wrap) md = md < 0 ? md + NM : (md >= NM ? md - NM : md);
     T gx = G[off], gs = G[N + off];
     if (md >= 0 && md < NM) {
         for (int d = 0; d < MAXD; ++d) {
-            if (!U.active[d]) continue;
+            if (!((K.active >> d) & 1)) continue;
             const int sP = (d & 1) ? -1 : 1, sQd = (d & 2) ? -1 : 1;
             for (int cc = 0; cc < 4; ++cc) {
                 // the downwind point whose corner cc is this point
                 int pr = p + ((cc & 1) ? sP : 0);
-                pr = (pr + NP) % NP;
+                pr = pr < 0 ? pr + NP : (pr >= NP ? pr - NP : pr);
                 int qr = q + ((cc & 2) ? sQd : 0);
-                if (U.qper) qr = (qr + NQ) % NQ;
+                if (U.qper) qr = qr < 0 ? qr + NQ : (qr >= NQ ? qr - NQ : qr);
                 else if (qr < 0 || qr >= NQ) continue;
                 const long long orr = (long long)md * sM + (long long)qr * sQ + pr;
-                const T bt = (T)U.beta[d][cc];
+                const T bt = K.beta[d][cc];
                 gx += bt * B[(long long)d * N + orr];
                 gs += bt * C[(long long)d * N + orr];
             }
@@ -607,7 +608,7 @@ __global__ void __launch_bounds__(256) adj_reduce_kernel(const SweepUnit *__rest
     __syncthreads();
     for (int u = u0; u < u1; ++u) {
         if (units[u].band != b || !units[u].transposed) continue;
-        const T *pg = G + (long long)(u - u0) * 2 * N;
+        const T *pg = G + (long long)(u - u0) * GRAD_CH * N + 2 * MAXD * N;
         for (int ii = ty; ii < 32; ii += 8) {
             const int i = i0 + ii, j = j0 + tx;
             if (i >= nx || j >= ny) continue;
@@ -624,7 +625,7 @@ __global__ void __launch_bounds__(256) adj_reduce_kernel(const SweepUnit *__rest
         T gx = tile[0][tx][jj], gs = tile[1][tx][jj];
         for (int u = u0; u < u1; ++u) {
             if (units[u].band != b || units[u].transposed) continue;
-            const T *pg = G + (long long)(u - u0) * 2 * N;
+            const T *pg = G + (long long)(u - u0) * GRAD_CH * N + 2 * MAXD * N;
             gx += pg[noff];
             gs += pg[N + noff];
         }

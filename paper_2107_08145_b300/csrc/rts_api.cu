@@ -201,7 +201,7 @@ struct rts_handle {
     std::vector<int> adj_unit_of_tile;
     rts::SweepUnit *d_adj_units = nullptr;
     int *d_adj_uot = nullptr;
-    int adj_tq = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
+    int adj_tq = 0, adj_maxr = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
     int flag_tiles = 0;           // ready flags allocated (max over both tilings)
     size_t adj_smem = 0;
     bool has_x = false;
@@ -219,9 +219,10 @@ struct rts_handle {
     int *d_ru_begin = nullptr;
     // adjoint scratch (RTS_FLAG_ADJOINT): lam0 [B][4][N] natural and
     // x-transposed, direct Q-step terms [B][2][N], and per checkpoint chunk of
-    // at most chunk_units units: I [u][4][N], lam/B [u][4][N], C [u][4][N], G [u][2][N]
+    // at most chunk_units units: the checkpoint [u][STORE_CH*4][N] and the
+    // gradient terms [u][GRAD_CH][N]
     void *d_lam0 = nullptr, *d_lam0T = nullptr, *d_direct = nullptr;
-    void *d_adjI = nullptr, *d_adjL = nullptr, *d_adjC = nullptr, *d_adjG = nullptr;
+    void *d_ckpt = nullptr, *d_grad = nullptr;
     int chunk_bands = 1, chunk_units = 0, grid_adj = 0;
     std::vector<int> band_unit;   // first unit of band b (b = 0..B)
     // batched handles (rts_create_batched): subdomain table and packed sizes
@@ -239,6 +240,11 @@ struct rts_handle {
     bool timing = false;
     std::vector<std::array<cudaEvent_t, 5>> evs;
     size_t nrec = 0;
+    // adjoint phases: events in recording order and the phase each interval ends
+    std::vector<cudaEvent_t> adj_evs;
+    std::vector<int> adj_phase;
+    size_t adj_nev = 0;
+    int adj_calls = 0;
     int kernels_last = 0;
 
     char err[512] = {0};
@@ -273,9 +279,6 @@ struct FwdCfg {
 static const FwdCfg kFwdCfg[] = {{16, 168}, {12, 168}, {8, 112}, {7, 112}, {6, 104}, {4, 72}, {2, 56}, {1, 56},
                                  {4, 64}, {2, 64}, {1, 64}};
 static const int kNumFwdCfg = sizeof(kFwdCfg) / sizeof(kFwdCfg[0]);
-// reverse (adjoint) sweep kernels
-static const int kAdjRows[] = {4, 3, 2, 1};
-
 template <typename T>
 static SweepFn<T> fwd_kernel(int tq, int maxr)
 {
@@ -288,15 +291,13 @@ static SweepFn<T> fwd_kernel(int tq, int maxr)
 }
 
 template <typename T>
-static SweepFn<T> adj_kernel(int tq)
+static SweepFn<T> adj_kernel(int tq, int maxr)
 {
-    switch (tq) {
-    case 1: return rts::sweep_adj_kernel<T, 1>;
-    case 2: return rts::sweep_adj_kernel<T, 2>;
-    case 3: return rts::sweep_adj_kernel<T, 3>;
-    case 4: return rts::sweep_adj_kernel<T, 4>;
-    default: return nullptr;
-    }
+#define RTS_CFG(A, B)                                                                                              \
+    if (tq == A && maxr == B) return rts::sweep_adj_kernel<T, A, B>;
+    RTS_CFG(4, 72) RTS_CFG(2, 56) RTS_CFG(1, 56) RTS_CFG(4, 64) RTS_CFG(2, 64) RTS_CFG(1, 64)
+#undef RTS_CFG
+    return nullptr;
 }
 
 static size_t fwd_smem(int tq, int np, int esize)
@@ -304,11 +305,9 @@ static size_t fwd_smem(int tq, int np, int esize)
     return esize == 8 ? rts::tile_smem_bytes<double>(tq, np) : rts::tile_smem_bytes<float>(tq, np);
 }
 
-// reverse sweep CTA: per plane parity the 4 slots' A = e lam and the two
-// bounds, plus chi of two planes, in the sweep precision
 static size_t adj_smem(int tq, int np, int esize)
 {
-    return (size_t)rts::NFIELD_A * (tq + 2) * (np + 2) * esize;
+    return esize == 8 ? rts::adj_tile_smem_bytes<double>(tq, np) : rts::adj_tile_smem_bytes<float>(tq, np);
 }
 
 struct Tiling {
@@ -363,23 +362,32 @@ static Tiling choose_fwd(int requested, int npmax, int nqmax, int nsm)
     return best;
 }
 
-// reverse-sweep tiling: the tallest tile of at most ~110 KB shared memory
+// reverse-sweep tiling: among the instantiated (rows, register cap) pairs
+// (4,72), (2,56), (1,56) for CTAs up to 384 threads and (4,64), (2,64),
+// (1,64) above, the one that keeps the most plane rows resident per SM
 template <typename T>
 static Tiling choose_adj(int npmax, int nqmax, int nsm)
 {
+    static const int cfg[6][2] = {{4, 72}, {2, 56}, {1, 56}, {4, 64}, {2, 64}, {1, 64}};
     Tiling best;
     best.nt = 32 * ((npmax + 31) / 32);
-    best.maxt = 1024;
-    for (int tq : kAdjRows) {
+    long long best_rows = -1;
+    for (const auto &cf : cfg) {
+        const int tq = cf[0], maxr = cf[1];
+        if ((long long)maxr * best.nt > 65536) continue;
         const size_t smem = adj_smem(tq, npmax, (int)sizeof(T));
-        if (smem > 110 * 1024 && tq > 1) continue;
+        if (smem > 227 * 1024) continue;
         int blocks = 0;
-        if (kernel_occupancy<T>(adj_kernel<T>(tq), best.nt, smem, &blocks) != cudaSuccess || blocks < 1) continue;
+        if (kernel_occupancy<T>(adj_kernel<T>(tq, maxr), best.nt, smem, &blocks) != cudaSuccess || blocks < 1) continue;
         if ((long long)blocks * nsm < (nqmax + tq - 1) / tq) continue;
-        best.tq = tq;
-        best.blocks = blocks;
-        best.smem = smem;
-        break;
+        const long long rows = (long long)tq * blocks;
+        if (rows > best_rows) {
+            best_rows = rows;
+            best.tq = tq;
+            best.maxt = maxr;
+            best.blocks = blocks;
+            best.smem = smem;
+        }
     }
     return best;
 }
@@ -387,7 +395,7 @@ static Tiling choose_adj(int npmax, int nqmax, int nsm)
 template <typename T>
 static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool reverse = false)
 {
-    SweepFn<T> kern = reverse ? adj_kernel<T>(h->adj_tq) : fwd_kernel<T>(h->tq, h->maxt);
+    SweepFn<T> kern = reverse ? adj_kernel<T>(h->adj_tq, h->adj_maxr) : fwd_kernel<T>(h->tq, h->maxt);
     const size_t smem = reverse ? h->adj_smem : h->smem;
     if (!kern) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -426,6 +434,9 @@ static void free_all(rts_handle *h)
 {
     if (h->dmem) cudaFree(h->dmem);
     h->dmem = nullptr;
+    for (cudaEvent_t e : h->adj_evs)
+        if (e) cudaEventDestroy(e);
+    h->adj_evs.clear();
     for (auto &set : h->evs)
         for (cudaEvent_t e : set)
             if (e) cudaEventDestroy(e);
@@ -540,6 +551,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         const Tiling ta = o.prec == RTS_FP64 ? choose_adj<double>(npmax, nqmax, nsm) : choose_adj<float>(npmax, nqmax, nsm);
         if (ta.tq < 1) return bail(fail(h, RTS_EINVAL, "no reverse-sweep tile fits plane extent %d", npmax));
         h->adj_tq = ta.tq;
+        h->adj_maxr = ta.maxt;
         h->adj_smem = ta.smem;
         h->adj_units.resize(max_units);
         h->adj_unit_of_tile.resize(max_tiles);
@@ -590,10 +602,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         o_adj[0] = take((size_t)nbands * 4 * h->N * es);
         o_adj[1] = h->has_x ? take((size_t)nbands * 4 * h->N * es) : 0;
         o_adj[2] = take((size_t)nbands * 2 * h->N * es);
-        o_adj[3] = take(cu * 4 * h->N * es);
-        o_adj[4] = take(cu * 4 * h->N * es);
-        o_adj[5] = take(cu * 4 * h->N * es);
-        o_adj[6] = take(cu * 2 * h->N * es);
+        o_adj[3] = take(cu * rts::STORE_CH * rts::MAXD * h->N * es);
+        o_adj[4] = take(cu * rts::GRAD_CH * h->N * es);
     }
     size_t o_io[6] = {0};
     const bool hostio = (o.flags & RTS_FLAG_HOST_IO) != 0;
@@ -632,10 +642,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         h->d_lam0 = base + o_adj[0];
         h->d_lam0T = h->has_x ? base + o_adj[1] : nullptr;
         h->d_direct = base + o_adj[2];
-        h->d_adjI = base + o_adj[3];
-        h->d_adjL = base + o_adj[4];
-        h->d_adjC = base + o_adj[5];
-        h->d_adjG = base + o_adj[6];
+        h->d_ckpt = base + o_adj[3];
+        h->d_grad = base + o_adj[4];
     }
     if (hostio) {
         h->d_in_chi = base + o_io[0];
@@ -786,10 +794,11 @@ static rts_status check_bc(rts_handle *h, const rts_boundary *bc)
 }
 
 // Reverse-mode gradient (declared in rts.h). Enqueues, on the handle's stream:
-// [transpose of chi, S] [forward sweep + band reduction, only when Q_rad
-// enters L] -> Q-step adjoint -> [transpose of lam0], then per checkpoint chunk
-// of bands: forward sweep that keeps I -> reverse sweep -> two gradient
-// passes -> reduce into g_logchi, g_S.
+// [transpose of chi, S], then per checkpoint chunk of bands: forward sweep
+// that keeps every ray's I (and whose partial sums give the chunk's J_b, F_b:
+// reduction only when Q_rad enters L) -> Q-step adjoint of the chunk's bands
+// -> [transpose of lam0] -> reverse sweep -> two gradient passes -> reduce
+// into g_logchi, g_S.
 template <typename T, typename Acc>
 static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
                                const void *gI_top, const double *gJ, const double *gF, const double *gQ,
@@ -803,53 +812,78 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
     CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
     int kernels = 0;
     const dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
+    // RTS_FLAG_TIMING: an event at each phase boundary (phase ids as in rts_stats.ms_adjoint)
+    const bool tim = h->timing && !h->capturing;
+    auto mark = [&](int phase) -> rts_status {
+        if (!tim) return RTS_OK;
+        if (h->adj_nev == h->adj_evs.size()) {
+            cudaEvent_t e = nullptr;
+            CUDA_TRY(h, cudaEventCreate(&e));
+            h->adj_evs.push_back(e);
+            h->adj_phase.push_back(0);
+        }
+        h->adj_phase[h->adj_nev] = phase;
+        CUDA_TRY(h, cudaEventRecord(h->adj_evs[h->adj_nev++], st));
+        return RTS_OK;
+    };
+    if (tim) {
+        if (h->adj_calls == 0) h->adj_nev = 0;
+        if (rts_status ms = mark(-1)) return ms;
+        ++h->adj_calls;
+    }
     if (h->has_x) {
         rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)h->d_chiT, g.nx, g.ny, g.nz);
         rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)h->d_ST, g.nx, g.ny, g.nz);
         CUDA_TRY(h, cudaGetLastError());
         kernels += 2;
     }
-    if (gQ) {  // J_b, F_b of the forward solve
-        rts_status rs = reset_sweep_state(h, st);
-        if (rs) return rs;
-        rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
-        cudaError_t e = launch_sweep<T>(h, a);
-        if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
-        rts::reduce_units_kernel<T, Acc><<<tg, tb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
-        CUDA_TRY(h, cudaGetLastError());
-        kernels += 2;
-    }
-    {
-        rts::QAdjParams P;
-        P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
-        P.dx = g.dx; P.dy = g.dy; P.dz = g.dz;
-        P.thin = std::min(g.dx, std::min(g.dy, g.dz)) / h->opt.tau_switch;
-        const dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
-        rts::qstep_adjoint_kernel<T, Acc><<<qg, tb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, gJ,
-                                                            gF, gQ, P, (T *)h->d_lam0, (T *)h->d_direct);
-        CUDA_TRY(h, cudaGetLastError());
-        kernels += 1;
-    }
-    if (h->has_x) {
-        const dim3 lg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B * 4));
-        rts::transpose_x_kernel<T><<<lg, tb, 0, st>>>((const T *)h->d_lam0, (T *)h->d_lam0T, g.nx, g.ny, g.nz);
-        CUDA_TRY(h, cudaGetLastError());
-        kernels += 1;
-    }
+    if (rts_status ms = mark(0)) return ms;
+    rts::QAdjParams QP;
+    QP.nx = g.nx; QP.ny = g.ny; QP.nz = g.nz; QP.nbands = B;
+    QP.inv2dx = 0.5 / g.dx; QP.inv2dy = 0.5 / g.dy; QP.inv2dz = 0.5 / g.dz; QP.invdz = 1.0 / g.dz;
+    QP.thin = std::min(g.dx, std::min(g.dy, g.dz)) / h->opt.tau_switch;
     for (int b0 = 0; b0 < B; b0 += h->chunk_bands) {
-        const int b1 = std::min(B, b0 + h->chunk_bands);
+        const int b1 = std::min(B, b0 + h->chunk_bands), nbc = b1 - b0;
         const int u0 = h->band_unit[b0], u1 = h->band_unit[b1];
         const rts::SweepUnit &U0 = h->units[u0], &U1 = h->units[u1 - 1];
         rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
         a.tile_base = U0.tile0;
         a.total_tiles = U1.tile0 + U1.ntiles - U0.tile0;
         a.unit_base = u0;
-        // forward sweep of the chunk, keeping every ray's converged I
+        // forward sweep of the chunk (the checkpoint): every ray's converged I,
+        // and the partial sums that give J_b, F_b of the chunk's bands
         rts_status rs = reset_sweep_state(h, st);
         if (rs) return rs;
-        a.store = (T *)h->d_adjI;
+        a.store = (T *)h->d_ckpt;
         cudaError_t e = launch_sweep<T>(h, a);
         if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
+        kernels += 1;
+        if (gQ) {
+            const dim3 rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * nbc));
+            rts::reduce_units_kernel<T, Acc><<<rg, tb, 0, st>>>(h->d_ru, h->d_ru_begin + b0,
+                                                               (Acc *)h->d_JF + (long long)b0 * 4 * N, g.nx, g.ny,
+                                                               g.nz);
+            CUDA_TRY(h, cudaGetLastError());
+            kernels += 1;
+        }
+        if (rts_status ms = mark(1)) return ms;
+        {  // Q step transposed for the chunk's bands
+            const dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
+            rts::qstep_adjoint_kernel<T, Acc><<<qg, tb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S,
+                                                                gJ, gF, gQ, QP, b0, b1, (T *)h->d_lam0,
+                                                                (T *)h->d_direct);
+            CUDA_TRY(h, cudaGetLastError());
+            kernels += 1;
+            if (h->has_x) {
+                const dim3 lg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * nbc * 4));
+                rts::transpose_x_kernel<T><<<lg, tb, 0, st>>>((const T *)h->d_lam0 + (long long)b0 * 4 * N,
+                                                             (T *)h->d_lam0T + (long long)b0 * 4 * N, g.nx, g.ny,
+                                                             g.nz);
+                CUDA_TRY(h, cudaGetLastError());
+                kernels += 1;
+            }
+        }
+        if (rts_status ms = mark(0)) return ms;
         // reverse sweep: cotangent of I of every ray (the adjoint kernel's tiling)
         rs = reset_sweep_state(h, st);
         if (rs) return rs;
@@ -858,27 +892,21 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
         a.unit_of_tile = h->d_adj_uot;
         a.tile_base = A0.tile0;
         a.total_tiles = A1.tile0 + A1.ntiles - A0.tile0;
-        a.store = (T *)h->d_adjL;
+        a.store = (T *)h->d_grad;
+        a.ckpt = (const T *)h->d_ckpt;
         a.lam0 = (const T *)h->d_lam0;
         a.lam0T = (const T *)h->d_lam0T;
         a.gitop = (const T *)gI_top;
         e = launch_sweep<T>(h, a, true);
         if (e != cudaSuccess) return fail(h, RTS_ECUDA, "reverse sweep launch: %s", cudaGetErrorString(e));
-        kernels += 2;
-        // gradient passes over every point of every unit of the chunk
+        kernels += 1;
+        if (rts_status ms = mark(2)) return ms;
+        // each point gathers the gradient terms of the downwind points that
+        // interpolated from it (every unit of the chunk)
         rts::GradArgs<T> ga;
         ga.units = h->d_units;
         ga.unit_base = u0;
-        ga.chi = (const T *)chi;
-        ga.S = (const T *)S;
-        ga.chiT = (const T *)h->d_chiT;
-        ga.ST = (const T *)h->d_ST;
-        ga.I = (const T *)h->d_adjI;
-        ga.LB = (T *)h->d_adjL;
-        ga.C = (T *)h->d_adjC;
-        ga.G = (T *)h->d_adjG;
-        ga.bc_bottom = bc ? bc->bottom : RTS_BC_EQUAL_S;
-        ga.bc_top = bc ? bc->top : RTS_BC_ZERO;
+        ga.grad = (T *)h->d_grad;
         int np = 0, nq = 0, nm = 0;
         for (int u = u0; u < u1; ++u) {
             np = std::max(np, h->units[u].NP);
@@ -891,36 +919,19 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
             const int ue = std::min(u1, us + per);
             rts::GradArgs<T> gs = ga;
             gs.unit_base = us;
-            const long long shift = (long long)(us - u0);
-            gs.I = ga.I + shift * 4 * N;
-            gs.LB = ga.LB + shift * 4 * N;
-            gs.C = ga.C + shift * 4 * N;
-            gs.G = ga.G + shift * 2 * N;
+            gs.grad = ga.grad + (long long)(us - u0) * rts::GRAD_CH * N;
             const dim3 gg((np + 127) / 128, nq, (unsigned)(nm * (ue - us)));
-            rts::adj_pass1_kernel<T><<<gg, 128, 0, st>>>(gs, nm);
-            CUDA_TRY(h, cudaGetLastError());
-            kernels += 1;
-        }
-        for (int us = u0; us < u1; us += per) {
-            const int ue = std::min(u1, us + per);
-            rts::GradArgs<T> gs = ga;
-            gs.unit_base = us;
-            const long long shift = (long long)(us - u0);
-            gs.I = ga.I + shift * 4 * N;
-            gs.LB = ga.LB + shift * 4 * N;
-            gs.C = ga.C + shift * 4 * N;
-            gs.G = ga.G + shift * 2 * N;
-            const dim3 gg((np + 127) / 128, nq, (unsigned)(nm * (ue - us)));
-            rts::adj_pass2_kernel<T><<<gg, 128, 0, st>>>(gs, nm);
+            rts::adj_gather_kernel<T><<<gg, 128, 0, st>>>(gs, nm);
             CUDA_TRY(h, cudaGetLastError());
             kernels += 1;
         }
         const dim3 rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * (b1 - b0)));
-        rts::adj_reduce_kernel<T><<<rg, tb, 0, st>>>(h->d_units, u0, u1, b0, (const T *)h->d_adjG,
+        rts::adj_reduce_kernel<T><<<rg, tb, 0, st>>>(h->d_units, u0, u1, b0, (const T *)h->d_grad,
                                                     (const T *)h->d_direct, (const T *)chi, (T *)g_logchi, (T *)g_S,
                                                     g.nx, g.ny, g.nz);
         CUDA_TRY(h, cudaGetLastError());
         kernels += 1;
+        if (rts_status ms = mark(3)) return ms;
     }
     h->kernels_last = kernels;
     return RTS_OK;
@@ -1033,6 +1044,20 @@ rts_status rts_get_stats(rts_handle *h, rts_stats *out)
         out->ms_reduce = (float)(acc[2] / h->nrec);
         out->ms_qstep = (float)(acc[3] / h->nrec);
         h->nrec = 0;
+    }
+    if (h->timing && h->adj_calls > 0) {
+        double acc[4] = {0, 0, 0, 0};
+        for (size_t i = 1; i < h->adj_nev; ++i) {
+            const int ph = h->adj_phase[i];
+            if (ph < 0) continue;  // start of the next call
+            float ms = 0.f;
+            CUDA_TRY(h, cudaEventElapsedTime(&ms, h->adj_evs[i - 1], h->adj_evs[i]));
+            acc[ph] += ms;
+        }
+        out->timed_adjoints = h->adj_calls;
+        for (int i = 0; i < 4; ++i) out->ms_adjoint[i] = (float)(acc[i] / h->adj_calls);
+        h->adj_calls = 0;
+        h->adj_nev = 0;
     }
     return s;
 }

@@ -48,6 +48,7 @@
 namespace rts {
 
 constexpr int MAXD = 4;     // directions per sweep unit
+constexpr int STORE_CH = 1; // values per slot kept by the checkpoint sweep
 constexpr int HALO_CH = MAXD + 2;  // ring channels: I of each ray, g of up / down rays
 
 // Rays of a unit sit in "sign slots": slot s holds the ray whose components
@@ -80,10 +81,15 @@ struct SweepArgs {
     const int *unit_of_tile;
     int total_tiles;            // tiles of this launch: tile_base .. tile_base+total_tiles-1
     int tile_base, unit_base;   // first tile and first unit of this launch
-    T *store;                   // optional: converged plane values of unit u at store + (u-unit_base)*4N
+    // optional (forward: checkpoint for the adjoint): per accumulated point and
+    // slot d of unit u, at store + (u-unit_base)*STORE_CH*MAXD*N + d*N, the
+    // segment's D = dI/d(dtau) (0 at set points). Reverse sweep: the gradient
+    // terms, see adjoint.cuh.
+    T *store;
     // reverse (adjoint) sweep only
     const T *lam0, *lam0T;      // [B][4][N] cotangents of J_b, F_b (natural / x-transposed layout)
     const T *gitop;             // [B][n_up][ny][nx] cotangent of I_top, or null
+    const T *ckpt;              // the checkpoint sweep's store (layout of `store`, forward)
     // per-call data
     const T *chi, *S;           // [B][N] natural layout
     const T *chiT, *ST;         // [B][N] x-transposed layout ([i][k][j])
@@ -136,6 +142,32 @@ __device__ __forceinline__ void seg_weights(double x, double &e, double &wu, dou
         double q = ome / x;
         wu = q - e;
         wp = 1.0 - q;
+    }
+}
+
+// d w_up / dx and d w_p / dx of the linear-in-tau weights
+__device__ __forceinline__ void seg_derivs(double x, double e, double &dwu, double &dwp)
+{
+    if (x < 0.01) {
+        // derivatives of the Taylor series of w_up and w_p
+        dwp = 0.5 - x * (2.0 / 6.0 - x * (3.0 / 24.0 - x * (4.0 / 120.0 - x * (5.0 / 720.0 - x * (6.0 / 5040.0)))));
+        dwu = 0.5 - x * (4.0 / 6.0 - x * (9.0 / 24.0 - x * (16.0 / 120.0 - x * (25.0 / 720.0 - x * (36.0 / 5040.0)))));
+    } else {
+        const double ome = -expm1(-x);
+        dwu = e / x - ome / (x * x) + e;
+        dwp = ome / (x * x) - e / x;
+    }
+}
+__device__ __forceinline__ void seg_derivs(float x, float e, float &dwu, float &dwp)
+{
+    if (x < 0.25f) {
+        dwp = 0.5f - x * (2.f / 6.f - x * (3.f / 24.f - x * (4.f / 120.f - x * (5.f / 720.f - x * (6.f / 5040.f - x * (7.f / 40320.f))))));
+        dwu = 0.5f - x * (4.f / 6.f - x * (9.f / 24.f - x * (16.f / 120.f - x * (25.f / 720.f - x * (36.f / 5040.f - x * (49.f / 40320.f))))));
+    } else {
+        const float r = 1.f / x;
+        const float ome = 1.f - e;
+        dwu = e * r - ome * r * r + e;
+        dwp = ome * r * r - e * r;
     }
 }
 
@@ -344,9 +376,9 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 }
                 const long long off = (long long)m * sM + (long long)s_q[k] * sQ + p;
                 part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
-                if (a.store) {
-                    T *st = a.store + (long long)(uidx - a.unit_base) * 4 * N + off;
-                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = sI[d * FL + k * npp + c];
+                if (a.store) {  // boundary plane: set points, no segment
+                    T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + off;
+                    for (int d = 0; d < STORE_CH * MAXD; ++d) st[(long long)d * N] = T(0);
                 }
             }
         }
@@ -405,6 +437,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             T hd[MAXD];
             ld4(D.hds, hd[0], hd[1], hd[2], hd[3]);
             float g[MAXD];
+            T ck[STORE_CH][MAXD];
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) {
                 const int SP = (d & 1) ? -1 : 1, SQ = (d & 2) ? -1 : 1;  // compile time after unrolling
@@ -416,8 +449,14 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 const T xup = b0 * xs[1][1] + b1 * xs[1][1 - SP] + b2 * xs[1 - SQ][1] + b3 * xs[1 - SQ][1 - SP];
                 const T sup = b0 * ss[1][1] + b1 * ss[1][1 - SP] + b2 * ss[1 - SQ][1] + b3 * ss[1 - SQ][1 - SP];
                 T e, wu, wp;
-                seg_weights(hd[d] * (xup + xp), e, wu, wp);
+                const T x = hd[d] * (xup + xp);
+                seg_weights(x, e, wu, wp);
                 v[d] = Iup + wu * (sup - Iup) + wp * (sp - Iup);
+                if (acc && a.store) {  // checkpoint for the adjoint: dI/dx of the segment
+                    T dwu, dwp;
+                    seg_derivs(x, e, dwu, dwp);
+                    ck[0][d] = -e * Iup + dwu * sup + dwp * sp;
+                }
                 g[d] = 0.f;
                 if (!acc) {
                     const float *Gp = sG + (((upm >> d) & 1) ? 0 : FL) + o;
@@ -434,7 +473,8 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 }
             }
             // boundary layer of the x/y groups: set, not integrated
-            if (wrap && (q == 0 || q == NQ - 1)) {
+            const bool bnd = wrap && (q == 0 || q == NQ - 1);
+            if (bnd) {
                 for (int d = 0; d < MAXD; ++d)
                     if (((upm >> d) & 1) ? q == 0 : q == NQ - 1) v[d] = bc_value(a, *Ug, D, d, p, q, m, sp);
                 if (q == 0) gu = 0.f;
@@ -443,6 +483,17 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
 #pragma unroll
             for (int d = 0; d < MAXD; ++d)
                 if (!((actm >> d) & 1)) v[d] = T(0);
+            if (acc && a.store) {
+                T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + (long long)m * sM +
+                        (long long)q * sQ + p;
+#pragma unroll
+                for (int d = 0; d < MAXD; ++d) {
+                    const bool set = bnd && (((upm >> d) & 1) ? q == 0 : q == NQ - 1);
+                    const bool live = ((actm >> d) & 1) && !set;
+#pragma unroll
+                    for (int ch = 0; ch < STORE_CH; ++ch) st[(long long)(ch * MAXD + d) * N] = live ? ck[ch][d] : T(0);
+                }
+            }
             out.g[0] = gu;
             out.g[1] = gd;
             if (!acc) gmax = fmaxf(gmax, fmaxf(gu, gd));
@@ -569,11 +620,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                     aJ += cw[0][d] * v; aX += cw[1][d] * v; aY += cw[2][d] * v; aZ += cw[3][d] * v;
                 }
                 part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
-                if (a.store) {
-                    T *st = a.store + (long long)(uidx - a.unit_base) * 4 * N + off;
-#pragma unroll
-                    for (int d = 0; d < MAXD; ++d) st[(long long)d * N] = rw.v[d];
-                }
+
                 if (itop && (axis == 2 ? top_plane : q == NQ - 1)) {
                     int i, j;
                     natural_ij(axis, p, q, m, i, j);
