@@ -280,12 +280,16 @@ static const FwdCfg kFwdCfg[] = {{16, 168}, {12, 168}, {8, 112}, {7, 112}, {6, 1
                                  {4, 64}, {2, 64}, {1, 64}};
 static const int kNumFwdCfg = sizeof(kFwdCfg) / sizeof(kFwdCfg[0]);
 template <typename T>
-static SweepFn<T> fwd_kernel(int tq, int maxr)
+static SweepFn<T> fwd_kernel(int tq, int maxr, bool ckpt = false)
 {
 #define RTS_CFG(A, B)                                                                                              \
-    if (tq == A && maxr == B) return rts::sweep_kernel<T, A, B>;
-    RTS_CFG(16, 168) RTS_CFG(12, 168) RTS_CFG(8, 112) RTS_CFG(7, 112) RTS_CFG(6, 104) RTS_CFG(4, 72)
-    RTS_CFG(2, 56) RTS_CFG(1, 56) RTS_CFG(4, 64) RTS_CFG(2, 64) RTS_CFG(1, 64)
+    if (tq == A && maxr == B) return ckpt ? nullptr : rts::sweep_kernel<T, A, B, false>;
+    RTS_CFG(16, 168) RTS_CFG(12, 168) RTS_CFG(8, 112) RTS_CFG(7, 112) RTS_CFG(6, 104)
+#undef RTS_CFG
+    // the small tiles also exist with the adjoint's checkpoint
+#define RTS_CFG(A, B)                                                                                              \
+    if (tq == A && maxr == B) return ckpt ? rts::sweep_kernel<T, A, B, true> : rts::sweep_kernel<T, A, B, false>;
+    RTS_CFG(4, 72) RTS_CFG(2, 56) RTS_CFG(1, 56) RTS_CFG(4, 64) RTS_CFG(2, 64) RTS_CFG(1, 64)
 #undef RTS_CFG
     return nullptr;
 }
@@ -331,7 +335,7 @@ static cudaError_t kernel_occupancy(SweepFn<T> kern, int nt, size_t smem, int *b
 // neighbour waits) and quartered for tiles taller than 4 rows. Every unit's tiles must fit on the GPU at once (the
 // persistent launch waits on neighbours).
 template <typename T>
-static Tiling choose_fwd(int requested, int npmax, int nqmax, int nsm)
+static Tiling choose_fwd(int requested, int npmax, int nqmax, int nsm, bool ckpt = false)
 {
     Tiling best;
     best.nt = 32 * ((npmax + 31) / 32);
@@ -340,6 +344,7 @@ static Tiling choose_fwd(int requested, int npmax, int nqmax, int nsm)
         const int tq = kFwdCfg[i].tq, maxr = kFwdCfg[i].maxr;
         if ((long long)maxr * best.nt > 65536) continue;
         if (requested > 0 && tq > requested) continue;
+        if (ckpt && !fwd_kernel<T>(tq, maxr, true)) continue;  // the adjoint re-sweeps with this tiling
         const size_t smem = fwd_smem(tq, npmax, (int)sizeof(T));
         if (smem > 227 * 1024) continue;
         int blocks = 0;
@@ -395,7 +400,7 @@ static Tiling choose_adj(int npmax, int nqmax, int nsm)
 template <typename T>
 static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool reverse = false)
 {
-    SweepFn<T> kern = reverse ? adj_kernel<T>(h->adj_tq, h->adj_maxr) : fwd_kernel<T>(h->tq, h->maxt);
+    SweepFn<T> kern = reverse ? adj_kernel<T>(h->adj_tq, h->adj_maxr) : fwd_kernel<T>(h->tq, h->maxt, a.store != nullptr);
     const size_t smem = reverse ? h->adj_smem : h->smem;
     if (!kern) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -513,8 +518,9 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     int dev = 0, nsm = 0;
     CUDA_TRY(h, cudaGetDevice(&dev));
     CUDA_TRY(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    const Tiling tl = o.prec == RTS_FP64 ? choose_fwd<double>(o.tile_rows, npmax, nqmax, nsm)
-                                         : choose_fwd<float>(o.tile_rows, npmax, nqmax, nsm);
+    const bool want_adj = (o.flags & RTS_FLAG_ADJOINT) != 0;
+    const Tiling tl = o.prec == RTS_FP64 ? choose_fwd<double>(o.tile_rows, npmax, nqmax, nsm, want_adj)
+                                         : choose_fwd<float>(o.tile_rows, npmax, nqmax, nsm, want_adj);
     if (tl.tq < 1) return bail(fail(h, RTS_EINVAL, "no sweep tile fits plane extent %d with %d-row units", npmax, nqmax));
     const int tq = tl.tq;
     h->tq = tq;

@@ -240,7 +240,9 @@ __host__ __device__ constexpr size_t tile_smem_bytes(int tq, int np)
 
 // One tile of one sweep unit, from its first plane to the last. Thread p
 // owns column p (p < NP) of rows q0 .. q0+nrows-1.
-template <typename T, int TQ>
+// CKPT: this launch keeps the adjoint's checkpoint (SweepArgs::store); the
+// code for it is compiled only into the instantiations the adjoint uses.
+template <typename T, int TQ, bool CKPT>
 __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug, int uidx, int r, int gt,
                          unsigned char *smem)
 {
@@ -304,11 +306,15 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const bool has_lower = qper || r > 0;
     const bool has_upper = qper || r < ntl - 1;
 
-    // store v at column p + 1 of row k of field f, and its periodic copy
+    // store v at column p + 1 of row k of field f, and its periodic copy; only
+    // the warps holding column 0 or NP-1 take the (warp-uniform) copy branch
+    const bool edge_warp = warp == 0 || warp == (NP - 1) >> 5;
     auto put = [&](auto *f, int k, auto v) {
         f[k * npp + c] = v;
-        if (p == 0) f[k * npp + NP + 1] = v;
-        if (p == NP - 1) f[k * npp] = v;
+        if (edge_warp) {
+            if (p == 0) f[k * npp + NP + 1] = v;
+            if (p == NP - 1) f[k * npp] = v;
+        }
     };
     // asynchronous copy of this thread's column of the chi/S rows of plane t
     // into slot t & 1
@@ -376,7 +382,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 }
                 const long long off = (long long)m * sM + (long long)s_q[k] * sQ + p;
                 part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
-                if (a.store) {  // boundary plane: set points, no segment
+                if (CKPT) {  // boundary plane: set points, no segment
                     T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + off;
                     for (int d = 0; d < STORE_CH * MAXD; ++d) st[(long long)d * N] = T(0);
                 }
@@ -452,7 +458,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 const T x = hd[d] * (xup + xp);
                 seg_weights(x, e, wu, wp);
                 v[d] = Iup + wu * (sup - Iup) + wp * (sp - Iup);
-                if (acc && a.store) {  // checkpoint for the adjoint: dI/dx of the segment
+                if (CKPT && acc) {  // checkpoint for the adjoint: dI/dx of the segment
                     T dwu, dwp;
                     seg_derivs(x, e, dwu, dwp);
                     ck[0][d] = -e * Iup + dwu * sup + dwp * sp;
@@ -483,7 +489,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
 #pragma unroll
             for (int d = 0; d < MAXD; ++d)
                 if (!((actm >> d) & 1)) v[d] = T(0);
-            if (acc && a.store) {
+            if (CKPT && acc) {
                 T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + (long long)m * sM +
                         (long long)q * sQ + p;
 #pragma unroll
@@ -643,7 +649,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
 }
 
 // MAXR caps the registers per thread so that two to four CTAs share an SM
-template <typename T, int TQ, int MAXR>
+template <typename T, int TQ, int MAXR, bool CKPT = false>
 __global__ void __maxnreg__(MAXR) sweep_kernel(SweepArgs<T> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -659,7 +665,7 @@ __global__ void __maxnreg__(MAXR) sweep_kernel(SweepArgs<T> a)
         if (s_tile < 0 || s_tile >= a.total_tiles) return;
         const int tile = a.tile_base + s_tile;
         const int u = a.unit_of_tile[tile];
-        run_tile<T, TQ>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
+        run_tile<T, TQ, CKPT>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
     }
 }
 
