@@ -12,6 +12,8 @@
 // one-sided at k = 0 and k = Nz-1. The arithmetic type Acc is double (FP64)
 // or df32 (compensated two-FP32); outputs are written as double.
 #pragma once
+#include <type_traits>
+
 #include "df32.cuh"
 
 namespace rts {
@@ -174,6 +176,39 @@ __device__ __forceinline__ void qstep_point(const Acc *__restrict__ JF, const T 
     const Acc cx = acc_from(tag, P.inv2dx), cy = acc_from(tag, P.inv2dy);
     const Acc four_pi = acc_from(tag, 12.566370614359172953850573533118);
 
+    if constexpr (std::is_same<T, float>::value && std::is_same<Acc, double>::value) {
+        // FP32 sweep with the FP64 Q step: FP64 for the cancelling parts -- the
+        // band and direction sums, J_b - S_b, the flux differences and their
+        // sum, and the sum of Q over bands; the products with chi and the
+        // blend weights (no cancellation) in FP32, which B300 runs at many
+        // times its FP64 rate.
+        const double dcx = P.inv2dx, dcy = P.inv2dy, dcz = acc_to_double(cz);
+        const float four_pi_f = 12.566370614359172953850573533118f, thin_f = (float)P.thin;
+        double Jd = 0.0, Fxd = 0.0, Fyd = 0.0, Fzd = 0.0, Qd = 0.0;
+        for (int b = 0; b < P.nbands; ++b) {
+            const double *jf = (const double *)JF + (long long)b * 4 * N;
+            const double Jb = jf[p];
+            Jd += Jb;
+            Fxd += jf[N + p];
+            Fyd += jf[2 * N + p];
+            Fzd += jf[3 * N + p];
+            const double div = (jf[N + xp] - jf[N + xm]) * dcx + (jf[2 * N + yp] - jf[2 * N + ym]) * dcy +
+                               (jf[3 * N + zp] - jf[3 * N + zm]) * dcz;
+            const float c = chi[(long long)b * N + p], sv = S[(long long)b * N + p];
+            const float dJ = (float)(Jb - (double)sv);
+            float om, omc;
+            blend_weights(c, thin_f, om, omc);
+            Qd += (double)(om * (four_pi_f * c * dJ) + omc * (float)(-div));
+        }
+        if (J) J[p] = Jd;
+        if (F) {
+            F[p] = Fxd;
+            F[N + p] = Fyd;
+            F[2 * N + p] = Fzd;
+        }
+        if (Q) Q[p] = Qd;
+        return;
+    }
     Acc Jt = acc_zero(tag), Fx = acc_zero(tag), Fy = acc_zero(tag), Fz = acc_zero(tag), Qt = acc_zero(tag);
     for (int b = 0; b < P.nbands; ++b) {
         const Acc *jf = JF + (long long)b * 4 * N;
