@@ -86,7 +86,9 @@ enum {
                              solve (on the handle's stream); rts_get_stats
                              reports their mean over the solves since the
                              previous rts_get_stats call */
-    RTS_FLAG_ADJOINT = 4  /* allocate the scratch of rts_adjoint */
+    RTS_FLAG_ADJOINT = 4, /* allocate the scratch of rts_adjoint */
+    RTS_FLAG_HOST_IO_ASYNC = 8 /* two staging sets and two copy streams for
+                             rts_solve_host_async */
 };
 
 typedef struct {
@@ -157,6 +159,23 @@ rts_status rts_solve(rts_handle *h, const void *chi, const void *S, const rts_bo
  * accepted here (bc kinds ZERO / EQUAL_S only). */
 rts_status rts_solve_host(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
                           void *I_top, double *J, double *F, double *Q_rad);
+
+/* Pipelined form of rts_solve_host for a stream of solves: enqueues the
+ * copy of the inputs (a copy stream), the solve (the handle's stream) and the
+ * copy of the outputs back (a second copy stream) and returns at once.
+ * Consecutive calls alternate between two device staging sets, so the input
+ * copy of one call, the solve of the previous one and the output copy of the
+ * one before run at the same time (both copy engines and the SMs). Host
+ * buffers should be pinned (page-locked) for the copies to overlap; inputs
+ * must stay unchanged and outputs unread until rts_host_wait returns (or
+ * two later calls have been made and waited for). Needs
+ * RTS_FLAG_HOST_IO_ASYNC; bc kinds ZERO / EQUAL_S only. */
+rts_status rts_solve_host_async(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
+                                void *I_top, double *J, double *F, double *Q_rad);
+
+/* Wait for every rts_solve_host_async call of the handle and return the
+ * device status (as rts_check). */
+rts_status rts_host_wait(rts_handle *h);
 
 /* Wait for the handle's stream and return the device status of the last
  * solve (RTS_OK, RTS_ETIMEOUT, RTS_ENOCONV). */

@@ -19,6 +19,7 @@ BC_ZERO, BC_EQUAL_S, BC_EXPLICIT = 0, 1, 2
 FLAG_HOST_IO = 1
 FLAG_TIMING = 2
 FLAG_ADJOINT = 4
+FLAG_HOST_IO_ASYNC = 8
 
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED, "fp32_compensated": FP32_COMPENSATED}
 _BC = {"zero": BC_ZERO, "equal_s": BC_EQUAL_S}
@@ -58,7 +59,7 @@ _lib = None
 EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "rts_check",
            "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint",
            "rts_create_batched", "rts_solve_batched", "rts_batched_layout", "rts_graph_create", "rts_graph_launch",
-           "rts_graph_destroy", "rts_autotune")
+           "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait")
 
 
 def library_path() -> str:
@@ -81,7 +82,7 @@ def load(build_if_missing: bool = True):
     L.rts_default_options.restype = None
     L.rts_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Grid), C.c_int, C.POINTER(Quadrature), C.POINTER(Options)]
     L.rts_create.restype = C.c_int
-    for f in ("rts_solve", "rts_solve_host"):
+    for f in ("rts_solve", "rts_solve_host", "rts_solve_host_async"):
         getattr(L, f).argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp]
         getattr(L, f).restype = C.c_int
     L.rts_adjoint.argtypes = [vp, vp, vp, C.POINTER(Boundary), vp, vp, vp, vp, vp, vp]
@@ -106,6 +107,8 @@ def load(build_if_missing: bool = True):
     L.rts_autotune.restype = C.c_int
     L.rts_check.argtypes = [vp]
     L.rts_check.restype = C.c_int
+    L.rts_host_wait.argtypes = [vp]
+    L.rts_host_wait.restype = C.c_int
     L.rts_get_stats.argtypes = [vp, C.POINTER(Stats)]
     L.rts_get_stats.restype = C.c_int
     L.rts_last_error.argtypes = [vp]
@@ -141,7 +144,8 @@ class Solver:
 
     def __init__(self, nx, ny, nz, nbands=1, dx=1.0, dy=1.0, dz=1.0, precision="fp64", n=None, w=None,
                  tau_switch=0.1, wrap_tol=0.0, max_wrap_iters=64, tile_rows=0, timeout_s=2.0,
-                 host_io=False, timing=False, stream=None, adjoint=False, adjoint_chunk_bands=0):
+                 host_io=False, timing=False, stream=None, adjoint=False, adjoint_chunk_bands=0,
+                 host_io_async=False):
         import torch
 
         L = load()
@@ -158,7 +162,8 @@ class Solver:
         o.max_wrap_iters = max_wrap_iters
         o.tile_rows = tile_rows
         o.timeout_s = timeout_s
-        o.flags = (FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0) | (FLAG_ADJOINT if adjoint else 0)
+        o.flags = ((FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0) | (FLAG_ADJOINT if adjoint else 0)
+                   | (FLAG_HOST_IO_ASYNC if host_io_async else 0))
         o.adjoint_chunk_bands = adjoint_chunk_bands
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -301,6 +306,20 @@ class Solver:
                                     p(out.get("F")), p(out.get("Q")))
         self._err(rc)
         return out
+
+    def solve_host_async(self, chi, S, out, bottom="equal_s", top="zero"):
+        """Enqueue a solve on host (numpy, preferably pinned) buffers and return
+        at once (rts_solve_host_async); `out` as returned by solve_host. Call
+        host_wait() before reading the outputs."""
+        p = lambda a: None if a is None else C.c_void_p(a.ctypes.data)  # noqa: E731
+        b = Boundary(_BC[bottom], _BC[top], None, None)
+        rc = self._L.rts_solve_host_async(self._h, p(chi), p(S), C.byref(b), p(out.get("I_top")), p(out.get("J")),
+                                          p(out.get("F")), p(out.get("Q")))
+        self._err(rc)
+        return out
+
+    def host_wait(self):
+        self._err(self._L.rts_host_wait(self._h))
 
     def check(self):
         self._err(self._L.rts_check(self._h))

@@ -235,6 +235,15 @@ struct rts_handle {
     // host-IO staging
     void *d_in_chi = nullptr, *d_in_S = nullptr, *d_out_itop = nullptr;
     double *d_out_J = nullptr, *d_out_F = nullptr, *d_out_Q = nullptr;
+    // RTS_FLAG_HOST_IO_ASYNC: two staging sets (inputs chi, S; outputs I_top,
+    // J, F, Q), an input and an output copy stream, and per set the events
+    // "inputs copied", "solve done" and "outputs copied"
+    void *a_in[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    void *a_out[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_h2d[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_d2h[2] = {nullptr, nullptr};
+    bool a_used[2] = {false, false};
+    int a_next = 0;
 
     // RTS_FLAG_TIMING: one set of phase events per solve since the last stats call
     bool timing = false;
@@ -437,6 +446,17 @@ int rts_num_up(rts_handle *h) { return h ? h->n_up : 0; }
 
 static void free_all(rts_handle *h)
 {
+    if (h->s_h2d) cudaStreamSynchronize(h->s_h2d);
+    if (h->s_d2h) cudaStreamSynchronize(h->s_d2h);
+    for (int i = 0; i < 2; ++i) {
+        if (h->ev_h2d[i]) cudaEventDestroy(h->ev_h2d[i]);
+        if (h->ev_comp[i]) cudaEventDestroy(h->ev_comp[i]);
+        if (h->ev_d2h[i]) cudaEventDestroy(h->ev_d2h[i]);
+        h->ev_h2d[i] = h->ev_comp[i] = h->ev_d2h[i] = nullptr;
+    }
+    if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
+    if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
+    h->s_h2d = h->s_d2h = nullptr;
     if (h->dmem) cudaFree(h->dmem);
     h->dmem = nullptr;
     for (cudaEvent_t e : h->adj_evs)
@@ -611,6 +631,18 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         o_adj[3] = take(cu * rts::STORE_CH * rts::MAXD * h->N * es);
         o_adj[4] = take(cu * rts::GRAD_CH * h->N * es);
     }
+    size_t o_as[2][6] = {{0}};
+    const bool hostio_async = (o.flags & RTS_FLAG_HOST_IO_ASYNC) != 0;
+    if (hostio_async) {
+        for (int st_ = 0; st_ < 2; ++st_) {
+            o_as[st_][0] = take((size_t)nbands * h->N * es);
+            o_as[st_][1] = take((size_t)nbands * h->N * es);
+            o_as[st_][2] = take((size_t)nbands * h->n_up * nx * ny * es);
+            o_as[st_][3] = take((size_t)h->N * 8);
+            o_as[st_][4] = take((size_t)3 * h->N * 8);
+            o_as[st_][5] = take((size_t)h->N * 8);
+        }
+    }
     size_t o_io[6] = {0};
     const bool hostio = (o.flags & RTS_FLAG_HOST_IO) != 0;
     if (hostio) {
@@ -650,6 +682,18 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         h->d_direct = base + o_adj[2];
         h->d_ckpt = base + o_adj[3];
         h->d_grad = base + o_adj[4];
+    }
+    if (hostio_async) {
+        for (int st_ = 0; st_ < 2; ++st_) {
+            h->a_in[st_][0] = base + o_as[st_][0];
+            h->a_in[st_][1] = base + o_as[st_][1];
+            for (int i = 0; i < 4; ++i) h->a_out[st_][i] = base + o_as[st_][2 + i];
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_h2d[st_], cudaEventDisableTiming));
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_comp[st_], cudaEventDisableTiming));
+            CUDA_TRY(h, cudaEventCreateWithFlags(&h->ev_d2h[st_], cudaEventDisableTiming));
+        }
+        CUDA_TRY(h, cudaStreamCreateWithFlags(&h->s_h2d, cudaStreamNonBlocking));
+        CUDA_TRY(h, cudaStreamCreateWithFlags(&h->s_d2h, cudaStreamNonBlocking));
     }
     if (hostio) {
         h->d_in_chi = base + o_io[0];
@@ -999,6 +1043,54 @@ rts_status rts_solve_host(rts_handle *h, const void *chi, const void *S, const r
     if (J) CUDA_TRY(h, cudaMemcpyAsync(J, h->d_out_J, h->N * 8, cudaMemcpyDeviceToHost, st));
     if (F) CUDA_TRY(h, cudaMemcpyAsync(F, h->d_out_F, 3 * h->N * 8, cudaMemcpyDeviceToHost, st));
     if (Q) CUDA_TRY(h, cudaMemcpyAsync(Q, h->d_out_Q, h->N * 8, cudaMemcpyDeviceToHost, st));
+    return rts_check(h);
+}
+
+rts_status rts_solve_host_async(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top,
+                                double *J, double *F, double *Q)
+{
+    if (!h || !h->dmem) return h ? fail(h, RTS_EINVAL, "handle was not created successfully") : RTS_EINVAL;
+    if (!h->s_h2d) return fail(h, RTS_EINVAL, "rts_solve_host_async needs RTS_FLAG_HOST_IO_ASYNC at create time");
+    if (!chi || !S) return fail(h, RTS_EINVAL, "chi and S must not be NULL");
+    if (bc && (bc->bottom == RTS_BC_EXPLICIT || bc->top == RTS_BC_EXPLICIT))
+        return fail(h, RTS_EINVAL, "rts_solve_host_async does not take explicit boundary arrays");
+    rts_status s = check_bc(h, bc);
+    if (s) return s;
+    const int k = h->a_next;
+    h->a_next ^= 1;
+    void *const *in = h->a_in[k];
+    void *const *out = h->a_out[k];
+    const size_t in_bytes = (size_t)h->B * h->N * h->esize;
+    const size_t plane = (size_t)h->g.nx * h->g.ny;
+    const size_t out_bytes[4] = {(size_t)h->B * h->n_up * plane * h->esize, (size_t)h->N * 8, (size_t)3 * h->N * 8,
+                                 (size_t)h->N * 8};
+    void *const host_out[4] = {I_top, J, F, Q};
+    // inputs: wait until the solve that last read this set has finished
+    if (h->a_used[k]) CUDA_TRY(h, cudaStreamWaitEvent(h->s_h2d, h->ev_comp[k], 0));
+    CUDA_TRY(h, cudaMemcpyAsync(in[0], chi, in_bytes, cudaMemcpyHostToDevice, h->s_h2d));
+    CUDA_TRY(h, cudaMemcpyAsync(in[1], S, in_bytes, cudaMemcpyHostToDevice, h->s_h2d));
+    CUDA_TRY(h, cudaEventRecord(h->ev_h2d[k], h->s_h2d));
+    // solve: after the inputs arrived and the outputs of this set were copied out
+    CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_h2d[k], 0));
+    if (h->a_used[k]) CUDA_TRY(h, cudaStreamWaitEvent(h->stream, h->ev_d2h[k], 0));
+    s = rts_solve(h, in[0], in[1], bc, I_top ? out[0] : nullptr, J ? (double *)out[1] : nullptr,
+                  F ? (double *)out[2] : nullptr, Q ? (double *)out[3] : nullptr);
+    if (s) return s;
+    CUDA_TRY(h, cudaEventRecord(h->ev_comp[k], h->stream));
+    // outputs
+    CUDA_TRY(h, cudaStreamWaitEvent(h->s_d2h, h->ev_comp[k], 0));
+    for (int i = 0; i < 4; ++i)
+        if (host_out[i]) CUDA_TRY(h, cudaMemcpyAsync(host_out[i], out[i], out_bytes[i], cudaMemcpyDeviceToHost, h->s_d2h));
+    CUDA_TRY(h, cudaEventRecord(h->ev_d2h[k], h->s_d2h));
+    h->a_used[k] = true;
+    return RTS_OK;
+}
+
+rts_status rts_host_wait(rts_handle *h)
+{
+    if (!h || !h->dmem) return RTS_EINVAL;
+    if (h->s_h2d) CUDA_TRY(h, cudaStreamSynchronize(h->s_h2d));
+    if (h->s_d2h) CUDA_TRY(h, cudaStreamSynchronize(h->s_d2h));
     return rts_check(h);
 }
 
