@@ -194,15 +194,16 @@ def sweep_algorithmic_bytes(prec, nb=NB, ndir=NDIR):
     return units * n * (2 * es + 4 * es) + nb * (ndir // 2) * NX * NY * es
 
 
-def _adjoint_timing(rts, torch, workload, name, grid, prec, stream, steps):
-    """Mean ms of rts_solve and of rts_adjoint (loss on I_top and Q_rad, one
-    band per checkpoint) on one workload, CUDA events on the solver's stream."""
+def _adjoint_timing(rts, torch, workload, name, grid, prec, stream, steps, chunk=0):
+    """Mean ms of rts_solve and of rts_adjoint (loss on I_top and Q_rad; one
+    band per checkpoint, or `chunk` bands) on one workload, CUDA events on the
+    solver's stream."""
     import numpy as np
 
     nx, ny, nz = grid
     chi64, S64 = workload(name, nx=nx, ny=ny, nz=nz)
     nb = chi64.shape[0]
-    s = rts.Solver(nx, ny, nz, nb, precision=prec, stream=stream, adjoint=True)
+    s = rts.Solver(nx, ny, nz, nb, precision=prec, stream=stream, adjoint=True, adjoint_chunk_bands=chunk)
     dev = torch.device("cuda", torch.cuda.current_device())
     chi = torch.as_tensor(chi64, dtype=s.dtype, device=dev)
     S = torch.as_tensor(S64, dtype=s.dtype, device=dev)
@@ -229,7 +230,8 @@ def _adjoint_timing(rts, torch, workload, name, grid, prec, stream, steps):
     s.check()
     upd = nx * ny * nz * NDIR * nb
     r = {"forward_ms": round(fwd, 3), "adjoint_ms": round(bwd, 3), "adjoint_over_forward": round(bwd / fwd, 3),
-         "adjoint_gupd_s": round(upd / (bwd * 1e-3) / 1e9, 3), "checkpoint": "1 band", "steps": steps,
+         "adjoint_gupd_s": round(upd / (bwd * 1e-3) / 1e9, 3),
+         "checkpoint": f"{chunk} bands" if chunk > 1 else "1 band", "steps": steps,
          "loss": "sum gI*I_top + 1e-3 sum Q^2 cotangents"}
     del s, chi, S, out, grads
     torch.cuda.empty_cache()
@@ -308,6 +310,57 @@ def _batched_timing(rts, torch, steps):
             "separate": "768 rts_solve calls (one per subdomain and band), same precision",
             "tile_rows": best, "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
             "units": st["n_units"], "tiles": st["n_tiles"], "grid": st["grid"], "launch": "cuda graph"}
+
+
+def _large_timing(rts, torch):
+    """The large anisotropic workload: 512 x 512 x 256, 16 bands, FP32 sweep
+    with compensated accumulation; forward solve and the per-band-checkpoint
+    adjoint (loss on I_top and Q_rad). Runs last: about 230 GB on the device."""
+    from workloads import stratified_atmosphere
+    from workloads.atmosphere import _bands
+
+    nx, ny, nz, nb = 512, 512, 256, 16
+    T, _, chi0 = stratified_atmosphere(nx, ny, nz, 0)
+    cs, ss = _bands("sixteen", nb)
+    S4 = T ** 4
+    torch.cuda.empty_cache()
+    s = rts.Solver(nx, ny, nz, nb, precision="fp32_compensated", adjoint=True, timing=True)
+    c = torch.empty((nb, nz, ny, nx), dtype=torch.float32, device="cuda")
+    Sd = torch.empty_like(c)
+    for b in range(nb):
+        c[b] = torch.as_tensor(chi0 * cs[b], dtype=torch.float32)
+        Sd[b] = torch.as_tensor(S4 * ss[b], dtype=torch.float32)
+    del T, chi0, S4
+    out = s.solve(c, Sd)
+    gI = torch.randn(out["I_top"].shape, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(0))
+    gQ = 1e-3 * out["Q"]
+    g = s.adjoint(c, Sd, gI_top=gI, gQ=gQ)
+    s.stats()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(2):
+        s.solve(c, Sd, out=out, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / 2
+    st = s.stats()
+    e0.record()
+    s.adjoint(c, Sd, gI_top=gI, gQ=gQ, out=g, check=False)
+    e1.record()
+    torch.cuda.synchronize()
+    s.check()
+    adj = e0.elapsed_time(e1)
+    sa = s.stats()
+    upd = nx * ny * nz * NDIR * nb
+    r = {"workload": "512x512x256, 16 bands (chi x 10^(4b/15), S = T^4/16), FP32 sweep, compensated accumulation",
+         "forward_ms": round(fwd, 2), "gupd_s": round(upd / (fwd * 1e-3) / 1e9, 3),
+         "phases_ms": {k: round(st[k], 2) for k in ("ms_transpose", "ms_sweep", "ms_reduce", "ms_qstep")},
+         "adjoint_ms": round(adj, 2), "adjoint_over_forward": round(adj / fwd, 3),
+         "adjoint_phases_ms": [round(x, 2) for x in sa["ms_adjoint"]], "checkpoint": "1 band",
+         "wrap": {"mean_warmup_planes": st["mean_warmup_steps"], "max_warmup_planes": st["max_warmup_steps"]}}
+    del s, c, Sd, out, g, gI, gQ
+    torch.cuda.empty_cache()
+    return r
 
 
 def run_ours(args):
@@ -452,6 +505,9 @@ def run_ours(args):
         adj = {}
         for name, grid in (("adj96x4", (96, 96, 96)), (WORKLOAD, (NX, NY, NZ))):
             adj[name] = _adjoint_timing(rts, torch, workload, name, grid, prec, stream, max(3, min(args.steps, 10)))
+            # all four bands in one checkpoint: more sweep units at once, 4x the scratch
+            adj[name + "_all_bands_checkpoint"] = _adjoint_timing(rts, torch, workload, name, grid, prec, stream,
+                                                                 max(3, min(args.steps, 10)), chunk=4)
         ratio = adj[WORKLOAD]["adjoint_over_forward"]
     else:
         ratio = None
@@ -459,6 +515,12 @@ def run_ours(args):
     batched = None
     if not args.skip_batched:
         batched = _batched_timing(rts, torch, max(3, min(args.steps, 10)))
+
+    large = None
+    if not args.skip_large:
+        del s, chi, S, out  # the headline solver's ~25 GB, before the ~230 GB large run
+        torch.cuda.empty_cache()
+        large = _large_timing(rts, torch)
 
     cpu = None
     if rank == 0 and not args.skip_cpu_baseline:
@@ -471,7 +533,7 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": st["kernels_per_solve"] * args.steps,
             "phases_ms": phases,
             "wrap": {"max_warmup_planes": st["max_warmup_steps"], "mean_warmup_planes": st["mean_warmup_steps"]},
-            "adjoint_over_forward": ratio, "adjoint": adj, "batched": batched}
+            "adjoint_over_forward": ratio, "adjoint": adj, "batched": batched, "large": large}
     line.update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -562,6 +624,7 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-adjoint", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--grid", default="288,288,288",
                     help="NX,NY,NZ override (profiling of smaller cases); the metric is quoted at 288^3")
