@@ -154,6 +154,107 @@ __device__ __forceinline__ double accT(double *, double v) { return v; }
 __device__ __forceinline__ double accT(double *, float v) { return (double)v; }
 __device__ __forceinline__ df32 accT(df32 *, float v) { return df_make(v); }
 
+// Accumulator of the Q step at one point over the bands, in band order: the
+// band sums J, F and Q_rad = sum_b [om_b 4 pi chi_b (J_b - S_b) +
+// (1 - om_b)(-div F_b)]. add() takes band b's J_b, its own F_b and the six
+// neighbour values of the divergence (x+-1, y+-1, z+ / z-, with cz the z
+// coefficient: central, one-sided at the bottom and top levels).
+template <typename T, typename Acc>
+struct QAccum {
+    Acc Jt, Fx, Fy, Fz, Qt, cx, cy, cz, four_pi;
+    T thin;
+    __device__ __forceinline__ QAccum(const QParams &P, Acc czv)
+    {
+        Acc *tag = nullptr;
+        Jt = Fx = Fy = Fz = Qt = acc_zero(tag);
+        cx = acc_from(tag, P.inv2dx);
+        cy = acc_from(tag, P.inv2dy);
+        cz = czv;
+        four_pi = acc_from(tag, 12.566370614359172953850573533118);
+        thin = (T)P.thin;
+    }
+    __device__ __forceinline__ void add(Acc Jb, Acc fx, Acc fy, Acc fz, Acc fxp, Acc fxm, Acc fyp, Acc fym, Acc fzp,
+                                        Acc fzm, T c, T s)
+    {
+        Acc *tag = nullptr;
+        const Acc dvx = acc_mul(acc_sub(fxp, fxm), cx);
+        const Acc dvy = acc_mul(acc_sub(fyp, fym), cy);
+        const Acc dvz = acc_mul(acc_sub(fzp, fzm), cz);
+        const Acc negdiv = acc_sub(acc_zero(tag), acc_add(acc_add(dvx, dvy), dvz));
+        const Acc qj = acc_mul(acc_mul(four_pi, accT(tag, c)), acc_sub(Jb, accT(tag, s)));
+        T om, omc;
+        blend_weights(c, thin, om, omc);
+        const Acc qb = acc_add(acc_mul(accT(tag, om), qj), acc_mul(accT(tag, omc), negdiv));
+        Jt = acc_add(Jt, Jb);
+        Fx = acc_add(Fx, fx);
+        Fy = acc_add(Fy, fy);
+        Fz = acc_add(Fz, fz);
+        Qt = acc_add(Qt, qb);
+    }
+    __device__ __forceinline__ void store(double *J, double *F, double *Q, long long p, long long N) const
+    {
+        if (J) J[p] = acc_to_double(Jt);
+        if (F) {
+            F[p] = acc_to_double(Fx);
+            F[N + p] = acc_to_double(Fy);
+            F[2 * N + p] = acc_to_double(Fz);
+        }
+        if (Q) Q[p] = acc_to_double(Qt);
+    }
+};
+
+// FP32 sweep with the FP64 Q step: FP64 for the cancelling parts -- the band
+// and direction sums, J_b - S_b, the flux differences and their sum, and the
+// sum of Q over bands; the products with chi and the blend weights (no
+// cancellation) in FP32, which B300 runs at many times its FP64 rate.
+template <>
+struct QAccum<float, double> {
+    double Jd, Fxd, Fyd, Fzd, Qd, dcx, dcy, dcz;
+    float thin_f;
+    __device__ __forceinline__ QAccum(const QParams &P, double czv)
+    {
+        Jd = Fxd = Fyd = Fzd = Qd = 0.0;
+        dcx = P.inv2dx;
+        dcy = P.inv2dy;
+        dcz = czv;
+        thin_f = (float)P.thin;
+    }
+    __device__ __forceinline__ void add(double Jb, double fx, double fy, double fz, double fxp, double fxm,
+                                        double fyp, double fym, double fzp, double fzm, float c, float sv)
+    {
+        const float four_pi_f = 12.566370614359172953850573533118f;
+        Jd += Jb;
+        Fxd += fx;
+        Fyd += fy;
+        Fzd += fz;
+        const double div = (fxp - fxm) * dcx + (fyp - fym) * dcy + (fzp - fzm) * dcz;
+        const float dJ = (float)(Jb - (double)sv);
+        float om, omc;
+        blend_weights(c, thin_f, om, omc);
+        Qd += (double)(om * (four_pi_f * c * dJ) + omc * (float)(-div));
+    }
+    __device__ __forceinline__ void store(double *J, double *F, double *Q, long long p, long long N) const
+    {
+        if (J) J[p] = Jd;
+        if (F) {
+            F[p] = Fxd;
+            F[N + p] = Fyd;
+            F[2 * N + p] = Fzd;
+        }
+        if (Q) Q[p] = Qd;
+    }
+};
+
+// z coefficient of the divergence at level k
+template <typename Acc>
+__device__ __forceinline__ Acc z_coef(const QParams &P, int k)
+{
+    Acc *tag = nullptr;
+    if (P.nz == 1) return acc_zero(tag);
+    if (k == 0 || k == P.nz - 1) return acc_from(tag, P.invdz);
+    return acc_from(tag, P.inv2dz);
+}
+
 // Q step at point (i, j, k) of one grid (pointers at that grid's data)
 template <typename T, typename Acc>
 __device__ __forceinline__ void qstep_point(const Acc *__restrict__ JF, const T *__restrict__ chi,
@@ -167,76 +268,17 @@ __device__ __forceinline__ void qstep_point(const Acc *__restrict__ JF, const T 
     const long long xp = p - i + (i + 1 == nx ? 0 : i + 1), xm = p - i + (i == 0 ? nx - 1 : i - 1);
     const long long yp = p + ((j + 1 == ny ? 0 : j + 1) - j) * nx, ym = p + ((j == 0 ? ny - 1 : j - 1) - j) * nx;
     long long zp, zm;
-    Acc cz;
-    Acc *tag = nullptr;
-    if (nz == 1) { zp = zm = p; cz = acc_zero(tag); }
-    else if (k == 0) { zp = p + nx * ny; zm = p; cz = acc_from(tag, P.invdz); }
-    else if (k == nz - 1) { zp = p; zm = p - nx * ny; cz = acc_from(tag, P.invdz); }
-    else { zp = p + nx * ny; zm = p - nx * ny; cz = acc_from(tag, P.inv2dz); }
-    const Acc cx = acc_from(tag, P.inv2dx), cy = acc_from(tag, P.inv2dy);
-    const Acc four_pi = acc_from(tag, 12.566370614359172953850573533118);
-
-    if constexpr (std::is_same<T, float>::value && std::is_same<Acc, double>::value) {
-        // FP32 sweep with the FP64 Q step: FP64 for the cancelling parts -- the
-        // band and direction sums, J_b - S_b, the flux differences and their
-        // sum, and the sum of Q over bands; the products with chi and the
-        // blend weights (no cancellation) in FP32, which B300 runs at many
-        // times its FP64 rate.
-        const double dcx = P.inv2dx, dcy = P.inv2dy, dcz = acc_to_double(cz);
-        const float four_pi_f = 12.566370614359172953850573533118f, thin_f = (float)P.thin;
-        double Jd = 0.0, Fxd = 0.0, Fyd = 0.0, Fzd = 0.0, Qd = 0.0;
-        for (int b = 0; b < P.nbands; ++b) {
-            const double *jf = (const double *)JF + (long long)b * 4 * N;
-            const double Jb = jf[p];
-            Jd += Jb;
-            Fxd += jf[N + p];
-            Fyd += jf[2 * N + p];
-            Fzd += jf[3 * N + p];
-            const double div = (jf[N + xp] - jf[N + xm]) * dcx + (jf[2 * N + yp] - jf[2 * N + ym]) * dcy +
-                               (jf[3 * N + zp] - jf[3 * N + zm]) * dcz;
-            const float c = chi[(long long)b * N + p], sv = S[(long long)b * N + p];
-            const float dJ = (float)(Jb - (double)sv);
-            float om, omc;
-            blend_weights(c, thin_f, om, omc);
-            Qd += (double)(om * (four_pi_f * c * dJ) + omc * (float)(-div));
-        }
-        if (J) J[p] = Jd;
-        if (F) {
-            F[p] = Fxd;
-            F[N + p] = Fyd;
-            F[2 * N + p] = Fzd;
-        }
-        if (Q) Q[p] = Qd;
-        return;
-    }
-    Acc Jt = acc_zero(tag), Fx = acc_zero(tag), Fy = acc_zero(tag), Fz = acc_zero(tag), Qt = acc_zero(tag);
+    if (nz == 1) { zp = zm = p; }
+    else if (k == 0) { zp = p + nx * ny; zm = p; }
+    else if (k == nz - 1) { zp = p; zm = p - nx * ny; }
+    else { zp = p + nx * ny; zm = p - nx * ny; }
+    QAccum<T, Acc> qa(P, z_coef<Acc>(P, k));
     for (int b = 0; b < P.nbands; ++b) {
         const Acc *jf = JF + (long long)b * 4 * N;
-        const Acc Jb = jf[p];
-        const Acc fx = jf[N + p], fy = jf[2 * N + p], fz = jf[3 * N + p];
-        // -div F_b
-        const Acc dvx = acc_mul(acc_sub(jf[N + xp], jf[N + xm]), cx);
-        const Acc dvy = acc_mul(acc_sub(jf[2 * N + yp], jf[2 * N + ym]), cy);
-        const Acc dvz = acc_mul(acc_sub(jf[3 * N + zp], jf[3 * N + zm]), cz);
-        const Acc negdiv = acc_sub(acc_zero(tag), acc_add(acc_add(dvx, dvy), dvz));
-        const T c = chi[(long long)b * N + p], s = S[(long long)b * N + p];
-        const Acc qj = acc_mul(acc_mul(four_pi, accT(tag, c)), acc_sub(Jb, accT(tag, s)));
-        T om, omc;
-        blend_weights(c, (T)P.thin, om, omc);
-        const Acc qb = acc_add(acc_mul(accT(tag, om), qj), acc_mul(accT(tag, omc), negdiv));
-        Jt = acc_add(Jt, Jb);
-        Fx = acc_add(Fx, fx);
-        Fy = acc_add(Fy, fy);
-        Fz = acc_add(Fz, fz);
-        Qt = acc_add(Qt, qb);
+        qa.add(jf[p], jf[N + p], jf[2 * N + p], jf[3 * N + p], jf[N + xp], jf[N + xm], jf[2 * N + yp],
+               jf[2 * N + ym], jf[3 * N + zp], jf[3 * N + zm], chi[(long long)b * N + p], S[(long long)b * N + p]);
     }
-    if (J) J[p] = acc_to_double(Jt);
-    if (F) {
-        F[p] = acc_to_double(Fx);
-        F[N + p] = acc_to_double(Fy);
-        F[2 * N + p] = acc_to_double(Fz);
-    }
-    if (Q) Q[p] = acc_to_double(Qt);
+    qa.store(J, F, Q, p, N);
 }
 
 template <typename T, typename Acc>

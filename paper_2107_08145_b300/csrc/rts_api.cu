@@ -814,13 +814,14 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     kernels += 1;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
     if (J || F || Q) {
-        dim3 rb(32, 8), rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
-        rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
-        if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
+        dim3 rb(32, 8);
         rts::QParams P;
         P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
         P.inv2dx = 0.5 / g.dx; P.inv2dy = 0.5 / g.dy; P.inv2dz = 0.5 / g.dz; P.invdz = 1.0 / g.dz;
         P.thin = std::min(g.dx, std::min(g.dy, g.dz)) / h->opt.tau_switch;
+        dim3 rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
+        rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
+        if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
         dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
         rts::qstep_kernel<T, Acc><<<qg, rb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, P, J, F, Q);
         CUDA_TRY(h, cudaGetLastError());
