@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(256) transpose_x_kernel(const T *__restrict__ 
 }
 
 struct RedUnit {
-    const void *partial;  // [4][N] in the unit's layout
+    const void *partial;  // [N][4] in the unit's layout
     int axis;             // 0: transposed layout [i][k][j]; else natural
 };
 
@@ -76,6 +76,18 @@ __device__ __forceinline__ double part_out(const PartSum<double> &s, double *) {
 __device__ __forceinline__ double part_out(const PartSum<float> &s, double *) { return s.as_double(); }
 __device__ __forceinline__ df32 part_out(const PartSum<float> &s, df32 *) { return s.as_df32(); }
 
+// the 4 partial sums of one point (16 / 32 bytes, aligned)
+__device__ __forceinline__ void ld_part(const float *p, float (&v)[4])
+{
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ void ld_part(const double *p, double (&v)[4])
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 // JF[b][c][N] (c = J, Fx, Fy, Fz) from the band's sweep-unit partials. A CTA
 // covers a 32 x 32 (i, j) tile of one level k of one band. Units in natural
 // layout are read along i; units of the x groups, stored [i][k][j], are read
@@ -101,7 +113,9 @@ __device__ __forceinline__ void reduce_tile(const RedUnit *__restrict__ ru, int 
             const int i = i0 + ii, j = j0 + tx;
             if (i >= nx || j >= ny) continue;
             const long long off = ((long long)i * nz + k) * ny + j;
-            for (int c = 0; c < 4; ++c) tile[c][ii][tx].add(pt[c * N + off]);
+            T v[4];
+            ld_part(pt + off * 4, v);
+            for (int c = 0; c < 4; ++c) tile[c][ii][tx].add(v[c]);
         }
     }
     __syncthreads();
@@ -114,7 +128,9 @@ __device__ __forceinline__ void reduce_tile(const RedUnit *__restrict__ ru, int 
         for (int u = u0; u < u1; ++u) {
             if (ru[u].axis == 0) continue;
             const T *pn = (const T *)ru[u].partial;
-            for (int c = 0; c < 4; ++c) s[c].add(pn[c * N + noff]);
+            T v[4];
+            ld_part(pn + noff * 4, v);
+            for (int c = 0; c < 4; ++c) s[c].add(v[c]);
         }
         for (int c = 0; c < 4; ++c) JFb[c * N + noff] = part_out(s[c], (Acc *)nullptr);
     }

@@ -43,6 +43,8 @@
 // is swept and accumulated. Unlike a residual test this needs no second pass
 // to confirm convergence.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace rts {
@@ -55,8 +57,10 @@ constexpr int HALO_CH = MAXD + 2;  // ring channels: I of each ray, g of up / do
 // along P and Q have signs sP = (s & 1 ? -1 : +1), sQ = (s & 2 ? -1 : +1), so
 // its upwind corners are the compile-time offsets (0,0), (-sP,0), (0,-sQ),
 // (-sP,-sQ). A slot without a ray is inactive (zero weights, not exported).
+// In the x and y groups Q is z, so slots 0 and 1 hold rising rays and slots
+// 2 and 3 descending ones.
 struct SweepUnit {
-    void *partial;              // [4][N] J, Fx, Fy, Fz of this unit, unit layout
+    void *partial;              // [N][4] J, Fx, Fy, Fz of this unit, unit layout
     long long sQ, sM, N;        // strides of Q and M (elements), points
     long long halo_off;         // element offset of tile 0's halo block
     long long in_off;           // offset of this unit's band in chi, S (and their x-transposed copies)
@@ -224,19 +228,62 @@ __device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U,
 // Shared memory of a tile, NPP = NP + 2 columns per row: column c = p + 1,
 // columns 0 and NP+1 repeat p = NP-1 and p = 0 (periodic padding), so a P
 // neighbour is always the next column. Each field has RW = TQ+2 rows (halo
-// row, TQ own rows, halo row). The previous plane's intensities (4 slots)
-// and seed-error bounds (up / down rays, float) are kept once: a plane's new
+// row, TQ own rows, halo row) and stores the values of a point together, so
+// one vector load brings all of them:
+//   sI  [RW][NPP][4]      the previous plane's intensities of the 4 slots
+//   sXS [2][RW][NPP][2]   chi and S of plane t at parity t & 1
+//   sG  [RW][NPP][2]      seed-error bounds of the up and down rays (float)
+// The previous plane's intensities and bounds are kept once: a plane's new
 // values stay in registers until every thread has read the previous plane.
-// chi and S are kept for two planes (by plane parity): the previous plane for
-// the upwind interpolation, the current one for the own points, and the slot
-// of the plane before is refilled with cp.async a whole plane ahead.
-enum { SF_I = 4, SF_XS = 4, SF_G = 2 };
-
+// chi and S are kept for two planes: the previous plane for the upwind
+// interpolation, the current one for the own points; the slot of the plane
+// before is refilled with cp.async a whole plane ahead.
 template <typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int tq, int np)
 {
-    return (size_t)(tq + 2) * (np + 2) * ((SF_I + SF_XS) * sizeof(T) + SF_G * sizeof(float));
+    return (size_t)(tq + 2) * (np + 2) * (8 * sizeof(T) + 2 * sizeof(float));
 }
+
+// vector accesses to 2 or 4 consecutive values (8 / 16 / 32-byte aligned)
+__device__ __forceinline__ void ld2(const float *p, float &a, float &b)
+{
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    a = v.x; b = v.y;
+}
+__device__ __forceinline__ void ld2(const double *p, double &a, double &b)
+{
+    const double2 v = *reinterpret_cast<const double2 *>(p);
+    a = v.x; b = v.y;
+}
+__device__ __forceinline__ void st2(float *p, float a, float b) { *reinterpret_cast<float2 *>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(double *p, double a, double b)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+}
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double *p, double a, double b, double c, double d)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(a, b);
+    *reinterpret_cast<double2 *>(p + 2) = make_double2(c, d);
+}
+
+// New values of one point of a plane: the 4 slots' intensities and, during
+// the periodic warm-up, the seed-error bounds of the up / down rays.
+template <typename T, bool ACC>
+struct RowVals {
+    T v[MAXD];
+    float g[2];
+};
+template <typename T>
+struct RowVals<T, true> {
+    T v[MAXD];
+};
+
+template <bool B>
+using Flag = std::integral_constant<bool, B>;
 
 // One tile of one sweep unit, from its first plane to the last. Thread p
 // owns column p (p < NP) of rows q0 .. q0+nrows-1.
@@ -268,13 +315,11 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const bool act = p < NP;
     const int c = p + 1;                        // smem column
     const int npp = NP + 2;
-    const int FL = RW * npp;                    // one field
-    T *const sI = (T *)smem;                    // I of slot d: sI + d * FL
-    T *const sX = sI + SF_I * FL;               // chi of plane t: sX + (t & 1) * FL
-    T *const sS = sX + 2 * FL;                  // S of plane t:   sS + (t & 1) * FL
-    float *const sG = (float *)(sS + 2 * FL);   // bound of the up (0) / down (1) rays
-    auto fX = [&](int t) -> T * { return sX + (t & 1) * FL; };
-    auto fS = [&](int t) -> T * { return sS + (t & 1) * FL; };
+    const int FL = RW * npp;                    // points of one field
+    T *const sI = (T *)smem;                    // [FL][4]
+    T *const sXS = sI + 4 * FL;                 // [2][FL][2]
+    float *const sG = (float *)(sXS + 4 * FL);  // [FL][2]
+    auto fXS = [&](int t) -> T * { return sXS + (t & 1) * 2 * FL; };
 
     __shared__ DirConst<T> D;
     __shared__ float s_wmax[32];
@@ -306,41 +351,48 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const bool has_lower = qper || r > 0;
     const bool has_upper = qper || r < ntl - 1;
 
-    // store v at column p + 1 of row k of field f, and its periodic copy; only
-    // the warps holding column 0 or NP-1 take the (warp-uniform) copy branch
-    const bool edge_warp = warp == 0 || warp == (NP - 1) >> 5;
-    auto put = [&](auto *f, int k, auto v) {
-        f[k * npp + c] = v;
-        if (edge_warp) {
-            if (p == 0) f[k * npp + NP + 1] = v;
-            if (p == NP - 1) f[k * npp] = v;
-        }
+    // periodic padding: thread p = 0 also writes column NP + 1 and thread
+    // p = NP - 1 column 0 (with NP == 1 the one thread writes both)
+    const bool padA = act && (p == 0 || p == NP - 1), padB = act && NP == 1;
+    const int pc = p == 0 ? NP + 1 : 0;
+    auto put4 = [&](int k, T v0, T v1, T v2, T v3) {
+        st4(sI + (k * npp + c) * 4, v0, v1, v2, v3);
+        if (padA) st4(sI + (k * npp + pc) * 4, v0, v1, v2, v3);
+        if (padB) st4(sI + (k * npp) * 4, v0, v1, v2, v3);
+    };
+    auto putG = [&](int k, float gu, float gd) {
+        st2(sG + (k * npp + c) * 2, gu, gd);
+        if (padA) st2(sG + (k * npp + pc) * 2, gu, gd);
+        if (padB) st2(sG + (k * npp) * 2, gu, gd);
+    };
+    auto putXS = [&](T *f, int k, T x, T s) {
+        st2(f + (k * npp + c) * 2, x, s);
+        if (padA) st2(f + (k * npp + pc) * 2, x, s);
+        if (padB) st2(f + (k * npp) * 2, x, s);
     };
     // asynchronous copy of this thread's column of the chi/S rows of plane t
     // into slot t & 1
     auto prefetch = [&](int t) {
         if (act) {
             const long long mo = (long long)plane_of(t, NM, sa) * sM + p;
-            T *dx = fX(t), *ds = fS(t);
+            T *f = fXS(t);
             for (int k = 0; k < nrows + 2; ++k) {
                 const int q = s_q[k];
-                if (q < 0) { put(dx, k, T(0)); put(ds, k, T(0)); continue; }
+                if (q < 0) { putXS(f, k, T(0), T(0)); continue; }
                 const T *gx = chi + mo + (long long)q * sQ, *gs = Sg + mo + (long long)q * sQ;
-                cp_async(dx + k * npp + c, gx);
-                cp_async(ds + k * npp + c, gs);
-                if (p == 0) { cp_async(dx + k * npp + NP + 1, gx); cp_async(ds + k * npp + NP + 1, gs); }
-                if (p == NP - 1) { cp_async(dx + k * npp, gx); cp_async(ds + k * npp, gs); }
+                T *d0 = f + (k * npp + c) * 2;
+                cp_async(d0, gx);
+                cp_async(d0 + 1, gs);
+                if (padA) { T *d1 = f + (k * npp + pc) * 2; cp_async(d1, gx); cp_async(d1 + 1, gs); }
+                if (padB) { T *d1 = f + (k * npp) * 2; cp_async(d1, gx); cp_async(d1 + 1, gs); }
             }
         }
         cp_async_commit();
     };
 
     __syncthreads();
-    int upm = 0, actm = 0;  // slot bit masks: upward ray, slot holds a ray
-    for (int d = 0; d < MAXD; ++d) {
-        upm |= D.up[d] ? 1 << d : 0;
-        actm |= D.active[d] ? 1 << d : 0;
-    }
+    int actm = 0;  // slot bit mask: slot holds a ray
+    for (int d = 0; d < MAXD; ++d) actm |= D.active[d] ? 1 << d : 0;
 
     // ---------------- prologue: the plane before the first integrated one ----
     const int tp = t_first - 1;
@@ -354,34 +406,34 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             const long long off = mo + (long long)(ok ? q : 0) * sQ;
             const T x = ok ? chi[off] : T(0);
             const T s = ok ? Sg[off] : T(0);
-            put(fX(tp), k, x);
-            put(fS(tp), k, s);
+            putXS(fXS(tp), k, x, s);
             float gu = 0.f, gd = 0.f;
+            T v[MAXD];
             for (int d = 0; d < MAXD; ++d) {
-                T v = T(0);
+                v[d] = T(0);
                 const bool bcrow = wrap ? ((D.up[d] && q == 0) || (!D.up[d] && q == NQ - 1)) : true;
                 if (ok && D.active[d]) {
-                    if (bcrow) v = bc_value(a, *Ug, D, d, p, q, m, s);
+                    if (bcrow) v[d] = bc_value(a, *Ug, D, d, p, q, m, s);
                     else {  // seed: I = S, unit seed-error bound
-                        v = s;
+                        v[d] = s;
                         if (D.up[d]) gu = 1.f; else gd = 1.f;
                     }
                 }
-                put(sI + d * FL, k, v);
             }
-            put(sG, k, gu);
-            put(sG + FL, k, gd);
+            put4(k, v[0], v[1], v[2], v[3]);
+            putG(k, gu, gd);
         }
         // z groups: the boundary plane is the first of the NM accumulated planes
         if (!wrap) {
             for (int k = 1; k <= nrows; ++k) {
+                T v[MAXD];
+                ld4(sI + (k * npp + c) * 4, v[0], v[1], v[2], v[3]);
                 T aJ = 0, aX = 0, aY = 0, aZ = 0;
                 for (int d = 0; d < MAXD; ++d) {
-                    const T v = sI[d * FL + k * npp + c];
-                    aJ += D.cJ[d] * v; aX += D.cF[0][d] * v; aY += D.cF[1][d] * v; aZ += D.cF[2][d] * v;
+                    aJ += D.cJ[d] * v[d]; aX += D.cF[0][d] * v[d]; aY += D.cF[1][d] * v[d]; aZ += D.cF[2][d] * v[d];
                 }
                 const long long off = (long long)m * sM + (long long)s_q[k] * sQ + p;
-                part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
+                st4(part + off * 4, aJ, aX, aY, aZ);
                 if (CKPT) {  // boundary plane: set points, no segment
                     T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + off;
                     for (int d = 0; d < STORE_CH * MAXD; ++d) st[(long long)d * N] = T(0);
@@ -397,35 +449,24 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const int warm_cap = a.max_periods * NM + a.L;
     const int dec_thread = NT > 32 ? 32 : 0;
 
-    for (int t = t_first;; ++t) {
-        const int m = plane_of(t, NM, sa);
-        // decision taken during the previous plane
-        if (t_acc < 0 && s_ctl[1]) {
-            t_acc = t;
-            if (r == 0 && tid == 0) a.unit_tacc[uidx] = t;
-        }
-        if (wrap && t_acc < 0 && t >= warm_cap) {
-            if (tid == 0) atomicOr(a.status, ST_NOCONV);
-            cp_async_wait_all();
-            return;  // every tile of the unit stops at the same plane; nothing in flight
-        }
-        const bool acc = t_acc >= 0;
+    // One plane t (m its index along M). ACC: the plane is accumulated (the
+    // periodic warm-up is over, or the unit has none). Returns 0 to go on,
+    // 1 after the last plane, 2 to abandon the tile (a wait failed).
+    auto plane_step = [&](auto ACC, int t, int m) __attribute__((always_inline)) -> int {
+        constexpr bool acc = decltype(ACC)::value;
+        using Row = RowVals<T, acc>;
         const bool last = acc && (t - t_acc == NM - 1);
         cp_async_wait_all();  // this thread's chi/S of plane t (read only by this thread in this step)
 
-        const T *Xp = fX(t + 1), *Sp = fS(t + 1), *Xc = fX(t), *Sc = fS(t);  // (t+1) & 1 == (t-1) & 1
+        const T *XSp = fXS(t + 1), *XSc = fXS(t);  // (t+1) & 1 == (t-1) & 1
         const bool top_plane = axis == 2 && t == NM - 1 && sa > 0;
         float gmax = 0.f;
 
-        // new values of row k (1..nrows) from the previous plane in shared memory
-        struct Row {
-            T v[MAXD];      // intensities of the 4 slots
-            float g[2];     // seed-error bounds of the up / down rays (warm-up only)
-        };
-        // the plane's new rows, kept in registers until the previous plane is no
-        // longer read: rows 1 .. nrows-1 in nR (constant indices only), the last in rl
-        Row nR[TQ], rl;
-        auto do_row = [&](int k) -> Row {
+        // new values of row k (1..nrows) from the previous plane in shared
+        // memory; EDGE: a first or last row, the only ones that can lie on
+        // the boundary layer of the x/y groups
+        auto do_row = [&](int k, auto EDGE) __attribute__((always_inline)) -> Row {
+            constexpr bool edge = decltype(EDGE)::value;
             Row out;
             T *v = out.v;
             const int q = q0 + k - 1;
@@ -435,95 +476,106 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
 #pragma unroll
             for (int dq = 0; dq < 3; ++dq)
 #pragma unroll
-                for (int dp = 0; dp < 3; ++dp) {
-                    xs[dq][dp] = Xp[o + (dq - 1) * npp + dp - 1];
-                    ss[dq][dp] = Sp[o + (dq - 1) * npp + dp - 1];
-                }
-            const T xp = Xc[o], sp = Sc[o];
+                for (int dp = 0; dp < 3; ++dp) ld2(XSp + (o + (dq - 1) * npp + dp - 1) * 2, xs[dq][dp], ss[dq][dp]);
+            T xp, sp;
+            ld2(XSc + o * 2, xp, sp);
+            // previous plane's I and bounds: slot d (signs sP = d & 1 ? -1 : 1,
+            // sQ = d & 2 ? -1 : 1) interpolates at (q, p), (q, p - sP), (q - sQ, p),
+            // (q - sQ, p - sP); the bounds of the x/y groups' rising rays (slots
+            // 0, 1) are the first value of a point's pair, the descending ones'
+            // (slots 2, 3) the second
+            const T *Ib = sI + o * 4;
+            const int ir = npp * 4;
+            [[maybe_unused]] const float *Gb = sG + o * 2;
+            [[maybe_unused]] const int gr = npp * 2;
             T hd[MAXD];
             ld4(D.hds, hd[0], hd[1], hd[2], hd[3]);
-            float g[MAXD];
-            T ck[STORE_CH][MAXD];
+            [[maybe_unused]] float g[MAXD];
+            [[maybe_unused]] T ck[STORE_CH][MAXD];
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) {
                 const int SP = (d & 1) ? -1 : 1, SQ = (d & 2) ? -1 : 1;  // compile time after unrolling
                 T b0, b1, b2, b3;
                 ld4(D.beta[d], b0, b1, b2, b3);
-                const T *Ip = sI + d * FL + o;
-                const int oq = -SQ * npp;
-                const T Iup = b0 * Ip[0] + b1 * Ip[-SP] + b2 * Ip[oq] + b3 * Ip[oq - SP];
+                const T *Id = Ib + d;
+                const int oq = -SQ * ir;
+                const T Iup = b0 * Id[0] + b1 * Id[-4 * SP] + b2 * Id[oq] + b3 * Id[oq - 4 * SP];
                 const T xup = b0 * xs[1][1] + b1 * xs[1][1 - SP] + b2 * xs[1 - SQ][1] + b3 * xs[1 - SQ][1 - SP];
                 const T sup = b0 * ss[1][1] + b1 * ss[1][1 - SP] + b2 * ss[1 - SQ][1] + b3 * ss[1 - SQ][1 - SP];
                 T e, wu, wp;
                 const T x = hd[d] * (xup + xp);
                 seg_weights(x, e, wu, wp);
                 v[d] = Iup + wu * (sup - Iup) + wp * (sp - Iup);
-                if (CKPT && acc) {  // checkpoint for the adjoint: dI/dx of the segment
+                if constexpr (CKPT && acc) {  // checkpoint for the adjoint: dI/dx of the segment
                     T dwu, dwp;
                     seg_derivs(x, e, dwu, dwp);
                     ck[0][d] = -e * Iup + dwu * sup + dwp * sp;
                 }
-                g[d] = 0.f;
-                if (!acc) {
-                    const float *Gp = sG + (((upm >> d) & 1) ? 0 : FL) + o;
-                    g[d] = (float)e * ((float)b0 * Gp[0] + (float)b1 * Gp[-SP] + (float)b2 * Gp[oq] +
-                                       (float)b3 * Gp[oq - SP]);
+                if constexpr (!acc) {
+                    const float *Gd = Gb + (d >> 1);
+                    const int gq = -SQ * gr;
+                    g[d] = (float)e * ((float)b0 * Gd[0] + (float)b1 * Gd[-2 * SP] + (float)b2 * Gd[gq] +
+                                       (float)b3 * Gd[gq - 2 * SP]);
                 }
             }
             float gu = 0.f, gd = 0.f;
-            if (!acc) {
-#pragma unroll
-                for (int d = 0; d < MAXD; ++d) {
-                    if ((upm >> d) & 1) gu = fmaxf(gu, g[d]);
-                    else gd = fmaxf(gd, g[d]);
-                }
+            if constexpr (!acc) {
+                gu = fmaxf(g[0], g[1]);
+                gd = fmaxf(g[2], g[3]);
             }
             // boundary layer of the x/y groups: set, not integrated
-            const bool bnd = wrap && (q == 0 || q == NQ - 1);
-            if (bnd) {
-                for (int d = 0; d < MAXD; ++d)
-                    if (((upm >> d) & 1) ? q == 0 : q == NQ - 1) v[d] = bc_value(a, *Ug, D, d, p, q, m, sp);
-                if (q == 0) gu = 0.f;
-                if (q == NQ - 1) gd = 0.f;
+            bool bnd = false;
+            if constexpr (edge) {
+                bnd = wrap && (q == 0 || q == NQ - 1);
+                if (bnd) {
+                    for (int d = 0; d < MAXD; ++d)
+                        if (d < 2 ? q == 0 : q == NQ - 1) v[d] = bc_value(a, *Ug, D, d, p, q, m, sp);
+                    if (q == 0) gu = 0.f;
+                    if (q == NQ - 1) gd = 0.f;
+                }
             }
 #pragma unroll
             for (int d = 0; d < MAXD; ++d)
                 if (!((actm >> d) & 1)) v[d] = T(0);
-            if (CKPT && acc) {
+            if constexpr (CKPT && acc) {
                 T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + (long long)m * sM +
                         (long long)q * sQ + p;
 #pragma unroll
                 for (int d = 0; d < MAXD; ++d) {
-                    const bool set = bnd && (((upm >> d) & 1) ? q == 0 : q == NQ - 1);
+                    const bool set = bnd && (d < 2 ? q == 0 : q == NQ - 1);
                     const bool live = ((actm >> d) & 1) && !set;
 #pragma unroll
                     for (int ch = 0; ch < STORE_CH; ++ch) st[(long long)(ch * MAXD + d) * N] = live ? ck[ch][d] : T(0);
                 }
             }
-            out.g[0] = gu;
-            out.g[1] = gd;
-            if (!acc) gmax = fmaxf(gmax, fmaxf(gu, gd));
+            if constexpr (!acc) {
+                out.g[0] = gu;
+                out.g[1] = gd;
+                gmax = fmaxf(gmax, fmaxf(gu, gd));
+            }
             return out;
         };
 
         // first and last rows go to the neighbours through the global ring
-        auto to_ring = [&](int sd, Row rw) {
+        auto to_ring = [&](int sd, const Row &rw) __attribute__((always_inline)) {
             T *dst = myhalo + ((long long)((t & 1) * 2 + sd) * HALO_CH) * NP + p;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) dst[(long long)d * NP] = rw.v[d];
-            if (!acc) {
+            if constexpr (!acc) {
                 dst[(long long)MAXD * NP] = (T)rw.g[0];
                 dst[(long long)(MAXD + 1) * NP] = (T)rw.g[1];
             }
         };
 
-
+        // the plane's new rows, kept in registers until the previous plane is no
+        // longer read: rows 1 .. nrows-1 in nR (constant indices only), the last in rl
+        Row nR[TQ], rl;
         // ---- interior rows need only this tile's own rows of the previous
         //      plane; meanwhile the neighbours finish their edge rows ----
         if (act) {
 #pragma unroll
             for (int k = 2; k < TQ; ++k)
-                if (k < nrows) nR[k - 1] = do_row(k);
+                if (k < nrows) nR[k - 1] = do_row(k, Flag<false>{});
         }
         // ---- one thread waits for the neighbours' plane t-1 (acquire); after
         //      the barrier every thread loads its column of their edge rows
@@ -549,52 +601,48 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
 #pragma unroll
                     for (int ch = 0; ch < HALO_CH; ++ch)
                         hv[ch] = (ch < MAXD || !acc) ? ld_cg(src + (long long)ch * NP) : T(0);
-#pragma unroll
-                    for (int d = 0; d < MAXD; ++d) put(sI + d * FL, row, hv[d]);
-                    if (!acc) {
-                        put(sG, row, (float)hv[MAXD]);
-                        put(sG + FL, row, (float)hv[MAXD + 1]);
-                    }
+                    put4(row, hv[0], hv[1], hv[2], hv[3]);
+                    if constexpr (!acc) putG(row, (float)hv[MAXD], (float)hv[MAXD + 1]);
                 }
             }
         }
         __syncthreads();  // B1: halo rows of plane t-1 are in place
         if (s_ctl[0]) {
             cp_async_wait_all();
-            return;
+            return 2;
         }
         if (act) {
-            nR[0] = do_row(1);
+            nR[0] = do_row(1, Flag<true>{});
             to_ring(0, nR[0]);
-            rl = nrows == 1 ? nR[0] : do_row(nrows);
+            rl = nrows == 1 ? nR[0] : do_row(nrows, Flag<true>{});
             to_ring(1, rl);
         }
-        if (!acc) {
+        if constexpr (!acc) {
             for (int o = 16; o; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
             if (lane == 0) s_wmax[warp] = gmax;
-        }
-        // decision for plane t+1 (its bound is L planes old: normally already complete)
-        if (tid == dec_thread && t_acc < 0 && t + 1 - a.L >= 0) {
-            const int ts = t + 1 - a.L;
-            const int slot = ts % a.R;
-            const unsigned want = (unsigned)ntl * (unsigned)(ts / a.R + 1);
-            bool ok = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
-            if (ok) {
-                const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
-                if ((unsigned)(v >> 32) != (unsigned)(ts + 1)) {
-                    atomicOr(a.status, ST_BADARG);  // ring overrun: never expected
-                    ok = false;
-                } else {
-                    s_ctl[1] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.tol ? 1 : 0;
+            // decision for plane t+1 (its bound is L planes old: normally already complete)
+            if (tid == dec_thread && t + 1 - a.L >= 0) {
+                const int ts = t + 1 - a.L;
+                const int slot = ts % a.R;
+                const unsigned want = (unsigned)ntl * (unsigned)(ts / a.R + 1);
+                bool ok = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
+                if (ok) {
+                    const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
+                    if ((unsigned)(v >> 32) != (unsigned)(ts + 1)) {
+                        atomicOr(a.status, ST_BADARG);  // ring overrun: never expected
+                        ok = false;
+                    } else {
+                        s_ctl[1] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.tol ? 1 : 0;
+                    }
                 }
+                if (!ok) s_ctl[0] = 1;
             }
-            if (!ok) s_ctl[0] = 1;
         }
         __syncthreads();  // B2: plane t's edge rows are in the ring; the previous plane is no longer read
         if (tid == 0) {
             // release the edge rows (the barrier orders the CTA's ring writes first)
             st_release(a.flags + gt, t + 1);
-            if (!acc) {
+            if constexpr (!acc) {
                 float g = 0.f;
                 for (int w = 0; w < (NT + 31) / 32; ++w) g = fmaxf(g, s_wmax[w]);
                 const int slot = t % a.R;
@@ -603,15 +651,13 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 red_release_add(a.gcnt + (long long)uidx * a.R + slot, 1u);
             }
         }
-        if (s_ctl[0]) return;
+        if (s_ctl[0]) return 2;
         // ---- plane t becomes the previous plane: own rows into shared memory;
         //      accumulated planes also go out as partial sums ----
-        auto write_row = [&](int kk, Row rw) {
-#pragma unroll
-            for (int d = 0; d < MAXD; ++d) put(sI + d * FL, kk + 1, rw.v[d]);
-            if (!acc) {
-                put(sG, kk + 1, rw.g[0]);
-                put(sG + FL, kk + 1, rw.g[1]);
+        auto write_row = [&](int kk, const Row &rw) __attribute__((always_inline)) {
+            put4(kk + 1, rw.v[0], rw.v[1], rw.v[2], rw.v[3]);
+            if constexpr (!acc) {
+                putG(kk + 1, rw.g[0], rw.g[1]);
             } else {
                 const int q = q0 + kk;
                 const long long off = (long long)m * sM + (long long)q * sQ + p;
@@ -625,7 +671,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                     const T v = rw.v[d];
                     aJ += cw[0][d] * v; aX += cw[1][d] * v; aY += cw[2][d] * v; aZ += cw[3][d] * v;
                 }
-                part[off] = aJ; part[N + off] = aX; part[2 * N + off] = aY; part[3 * N + off] = aZ;
+                st4(part + off * 4, aJ, aX, aY, aZ);
 
                 if (itop && (axis == 2 ? top_plane : q == NQ - 1)) {
                     int i, j;
@@ -641,9 +687,34 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 if (kk < nrows - 1) write_row(kk, nR[kk]);
             write_row(nrows - 1, rl);
         }
-        if (last) break;
+        if (last) return 1;
         prefetch(t + 1);  // into the slot of plane t-1 (no longer read)
         __syncthreads();  // B3: plane t is the previous plane for every thread
+        return 0;
+    };
+
+    // the periodic warm-up and the accumulated planes run as two loops, each
+    // compiled for its own phase
+    int t = t_first;
+    if (wrap) {
+        for (;; ++t) {
+            if (s_ctl[1]) {  // decision taken during the previous plane
+                t_acc = t;
+                if (r == 0 && tid == 0) a.unit_tacc[uidx] = t;
+                break;
+            }
+            if (t >= warm_cap) {
+                if (tid == 0) atomicOr(a.status, ST_NOCONV);
+                cp_async_wait_all();
+                return;  // every tile of the unit stops at the same plane; nothing in flight
+            }
+            if (plane_step(Flag<false>{}, t, plane_of(t, NM, sa)) == 2) return;
+        }
+    }
+    for (;; ++t) {
+        const int rc = plane_step(Flag<true>{}, t, plane_of(t, NM, sa));
+        if (rc == 2) return;
+        if (rc == 1) break;
     }
     cp_async_wait_all();
 }
