@@ -161,10 +161,11 @@ def _dist():
     return ws, rank, local
 
 
-def _traffic_from_profile(prec):
+def _traffic_from_profile(prec, grid, tile_rows):
     """DRAM bytes per sweep launch from the committed ncu summary
     (profiles/sweep_rts288x4_dram.md, "- key: value" lines), or None if the
-    sweep source changed since the counters were taken."""
+    sweep source changed since the counters were taken or the run is not the
+    summary's workload (grid, precision, tile height)."""
     path = os.path.join(ROOT, "profiles", "sweep_rts288x4_dram.md")
     rec = {}
     try:
@@ -177,6 +178,8 @@ def _traffic_from_profile(prec):
     src = os.path.join(ROOT, "paper_2107_08145_b300", "csrc", "sweep.cuh")
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if rec.get("sweep_source_sha256_16") != digest or rec.get("precision") != prec:
+        return None
+    if rec.get("grid") != "x".join(str(v) for v in grid) or rec.get("tile_rows") != str(tile_rows):
         return None
     try:
         return int(rec["dram_bytes_per_launch"])
@@ -428,7 +431,7 @@ def run_ours(args):
                 "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm if hbm else 6400.0,
                 "unit": "GB/s", "frac": round(achieved / (hbm if hbm else 6400.0), 5),
                 "peak_source": "of measured" if hbm else "of fallback",
-                "traffic": _traffic_from_profile(prec), "algorithmic_bytes_per_launch": alg,
+                "traffic": _traffic_from_profile(prec, (NX, NY, NZ), TILE_ROWS), "algorithmic_bytes_per_launch": alg,
                 "sweep_ms_mean": round(sweep_ms, 4), "launches_timed": st["timed_solves"]}
     phases = {k: round(st[k], 4) for k in ("ms_transpose", "ms_sweep", "ms_reduce", "ms_qstep")}
 
