@@ -195,6 +195,7 @@ struct rts_handle {
     std::vector<rts::SweepUnit> units;
     std::vector<int> unit_of_tile;
     int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, nt = 32, tq = 0, maxt = 0;  // maxt: register cap
+    unsigned carveout = 100;      // forward sweep's shared-memory carveout (percent)
     size_t smem = 0;
     // reverse sweep: the same units tiled for the adjoint kernel
     std::vector<rts::SweepUnit> adj_units;
@@ -328,6 +329,22 @@ struct Tiling {
     size_t smem = 0;
 };
 
+// Shared-memory carveout (percent of the SM's maximum) that holds `blocks`
+// CTAs of `smem` dynamic bytes each, with room for the kernel's static shared
+// memory and the per-CTA reservation. The rest of the SM's L1/shared storage
+// stays L1 cache, where register spills and the cp.async lines live.
+static unsigned carveout_percent(int blocks, size_t smem)
+{
+    int dev = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        per_sm <= 0)
+        return 100;
+    const double need = (double)blocks * ((double)smem + 3072.0);
+    const int pct = (int)std::ceil(100.0 * need / per_sm);
+    return (unsigned)std::min(100, std::max(1, pct));
+}
+
 template <typename T>
 static cudaError_t kernel_occupancy(SweepFn<T> kern, int nt, size_t smem, int *blocks)
 {
@@ -419,11 +436,13 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool 
     cfg.blockDim = dim3(h->nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = h->stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[1].val.sharedMemCarveout = reverse ? 100u : h->carveout;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
@@ -547,6 +566,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->nt = tl.nt;
     h->maxt = tl.maxt;
     h->smem = tl.smem;
+    h->carveout = carveout_percent(tl.blocks, tl.smem);
     const int max_units = nbands * 6 * h->ndir;
     const long long max_tiles = (long long)max_units * std::max(nx, std::max(ny, nz));  // tiles of >= 1 row
     h->units.resize(max_units);
@@ -1380,11 +1400,13 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     cfg.blockDim = dim3(nt);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[1].val.sharedMemCarveout = carveout_percent(blocks, smem);
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     NA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
     if (J || F || Q) {
         dim3 rb(32, 8), rg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)(g->nz * B));
@@ -1526,6 +1548,7 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     h->nt = tl.nt;
     h->maxt = tl.maxt;
     h->smem = tl.smem;
+    h->carveout = carveout_percent(tl.blocks, tl.smem);
 
     std::vector<rts::SweepUnit> plan;       // plan order
     std::vector<int> plan_sub;              // subdomain of each planned unit

@@ -232,7 +232,9 @@ __device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U,
 // one vector load brings all of them:
 //   sI  [RW][NPP][4]      the previous plane's intensities of the 4 slots
 //   sXS [2][RW][NPP][2]   chi and S of plane t at parity t & 1
-//   sG  [RW][NPP][2]      seed-error bounds of the up and down rays (float)
+//   sG  [RW][NPP][2]      seed-error bounds of the up and down rays, bf16
+//                         rounded up (still bounds; half the bytes, which
+//                         leaves the SM more L1 cache)
 // The previous plane's intensities and bounds are kept once: a plane's new
 // values stay in registers until every thread has read the previous plane.
 // chi and S are kept for two planes: the previous plane for the upwind
@@ -241,8 +243,17 @@ __device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U,
 template <typename T>
 __host__ __device__ constexpr size_t tile_smem_bytes(int tq, int np)
 {
-    return (size_t)(tq + 2) * (np + 2) * (8 * sizeof(T) + 2 * sizeof(float));
+    return (size_t)(tq + 2) * (np + 2) * (8 * sizeof(T) + 2 * sizeof(unsigned short));
 }
+
+// bf16 of a non-negative bound, rounded up, and back
+__device__ __forceinline__ unsigned bound16(float g)
+{
+    unsigned b = __float_as_uint(g);
+    if (b & 0xffffu) b += 0x10000u;
+    return b >> 16;
+}
+__device__ __forceinline__ float bound32(unsigned short h) { return __uint_as_float((unsigned)h << 16); }
 
 // vector accesses to 2 or 4 consecutive values (8 / 16 / 32-byte aligned)
 __device__ __forceinline__ void ld2(const float *p, float &a, float &b)
@@ -318,7 +329,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     const int FL = RW * npp;                    // points of one field
     T *const sI = (T *)smem;                    // [FL][4]
     T *const sXS = sI + 4 * FL;                 // [2][FL][2]
-    float *const sG = (float *)(sXS + 4 * FL);  // [FL][2]
+    unsigned short *const sG = (unsigned short *)(sXS + 4 * FL);  // [FL][2]
     auto fXS = [&](int t) -> T * { return sXS + (t & 1) * 2 * FL; };
 
     __shared__ DirConst<T> D;
@@ -361,9 +372,11 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
         if (padB) st4(sI + (k * npp) * 4, v0, v1, v2, v3);
     };
     auto putG = [&](int k, float gu, float gd) {
-        st2(sG + (k * npp + c) * 2, gu, gd);
-        if (padA) st2(sG + (k * npp + pc) * 2, gu, gd);
-        if (padB) st2(sG + (k * npp) * 2, gu, gd);
+        const unsigned w = bound16(gu) | bound16(gd) << 16;
+        unsigned *const g32 = (unsigned *)sG;
+        g32[k * npp + c] = w;
+        if (padA) g32[k * npp + pc] = w;
+        if (padB) g32[k * npp] = w;
     };
     auto putXS = [&](T *f, int k, T x, T s) {
         st2(f + (k * npp + c) * 2, x, s);
@@ -486,7 +499,7 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             // (slots 2, 3) the second
             const T *Ib = sI + o * 4;
             const int ir = npp * 4;
-            [[maybe_unused]] const float *Gb = sG + o * 2;
+            [[maybe_unused]] const unsigned short *Gb = sG + o * 2;
             [[maybe_unused]] const int gr = npp * 2;
             T hd[MAXD];
             ld4(D.hds, hd[0], hd[1], hd[2], hd[3]);
@@ -512,10 +525,10 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                     ck[0][d] = -e * Iup + dwu * sup + dwp * sp;
                 }
                 if constexpr (!acc) {
-                    const float *Gd = Gb + (d >> 1);
+                    const unsigned short *Gd = Gb + (d >> 1);
                     const int gq = -SQ * gr;
-                    g[d] = (float)e * ((float)b0 * Gd[0] + (float)b1 * Gd[-2 * SP] + (float)b2 * Gd[gq] +
-                                       (float)b3 * Gd[gq - 2 * SP]);
+                    g[d] = (float)e * ((float)b0 * bound32(Gd[0]) + (float)b1 * bound32(Gd[-2 * SP]) +
+                                       (float)b2 * bound32(Gd[gq]) + (float)b3 * bound32(Gd[gq - 2 * SP]));
                 }
             }
             float gu = 0.f, gd = 0.f;
