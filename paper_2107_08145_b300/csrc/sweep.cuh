@@ -149,6 +149,31 @@ __device__ __forceinline__ void seg_weights(double x, double &e, double &wu, dou
     }
 }
 
+// The same segment in the form the sweep evaluates. With q = (1 - e)/x the
+// weights are w_up = q - e and w_p = 1 - q, so
+//   I = I_up + w_up (S_up - I_up) + w_p (S_p - I_up) = S_p + e (I_up - S_up) + q (S_up - S_p),
+// which needs e and q only. Below the switch point, where 1 - e cancels, q
+// is a polynomial: in FP64 its Taylor series (sum over n of (-x)^n / (n+1)!),
+// in FP32 the degree-4 polynomial interpolating q at the 5 Chebyshev nodes of
+// [0, 1/4] (relative error below 3e-9 there, under the FP32 rounding of its
+// evaluation); FP32 evaluates both forms and selects, without a branch.
+__device__ __forceinline__ void seg_eq(float x, float &e, float &q)
+{
+    e = __expf(-x);
+    const float qd = __fdividef(1.f - e, x);
+    const float qs =
+        0.99999999758f + x * (-0.49999951482f + x * (0.16665108207f + x * (-0.04149065410f + x * 0.00751360622f)));
+    q = x < 0.25f ? qs : qd;
+}
+__device__ __forceinline__ void seg_eq(double x, double &e, double &q)
+{
+    e = exp(-x);
+    if (x < 0.01)
+        q = 1.0 - x * (0.5 - x * (1.0 / 6.0 - x * (1.0 / 24.0 - x * (1.0 / 120.0 - x * (1.0 / 720.0 - x * (1.0 / 5040.0))))));
+    else
+        q = -expm1(-x) / x;
+}
+
 // d w_up / dx and d w_p / dx of the linear-in-tau weights
 __device__ __forceinline__ void seg_derivs(double x, double e, double &dwu, double &dwp)
 {
@@ -515,10 +540,10 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 const T Iup = b0 * Id[0] + b1 * Id[-4 * SP] + b2 * Id[oq] + b3 * Id[oq - 4 * SP];
                 const T xup = b0 * xs[1][1] + b1 * xs[1][1 - SP] + b2 * xs[1 - SQ][1] + b3 * xs[1 - SQ][1 - SP];
                 const T sup = b0 * ss[1][1] + b1 * ss[1][1 - SP] + b2 * ss[1 - SQ][1] + b3 * ss[1 - SQ][1 - SP];
-                T e, wu, wp;
+                T e, qw;
                 const T x = hd[d] * (xup + xp);
-                seg_weights(x, e, wu, wp);
-                v[d] = Iup + wu * (sup - Iup) + wp * (sp - Iup);
+                seg_eq(x, e, qw);
+                v[d] = sp + e * (Iup - sup) + qw * (sup - sp);
                 if constexpr (CKPT && acc) {  // checkpoint for the adjoint: dI/dx of the segment
                     T dwu, dwp;
                     seg_derivs(x, e, dwu, dwp);
