@@ -571,14 +571,13 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 bnd = wrap && (q == 0 || q == NQ - 1);
                 if (bnd) {
                     for (int d = 0; d < MAXD; ++d)
-                        if (d < 2 ? q == 0 : q == NQ - 1) v[d] = bc_value(a, *Ug, D, d, p, q, m, sp);
+                        if (d < 2 ? q == 0 : q == NQ - 1) v[d] = (actm >> d) & 1 ? bc_value(a, *Ug, D, d, p, q, m, sp) : T(0);
                     if (q == 0) gu = 0.f;
                     if (q == NQ - 1) gd = 0.f;
                 }
             }
-#pragma unroll
-            for (int d = 0; d < MAXD; ++d)
-                if (!((actm >> d) & 1)) v[d] = T(0);
+            // an empty slot has zero weights and path length (e = q = 1, I_up =
+            // S_up = 0), so its intensity stays exactly 0 without a mask
             if constexpr (CKPT && acc) {
                 T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + (long long)m * sM +
                         (long long)q * sQ + p;
@@ -714,20 +713,34 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                     aJ += cw[0][d] * v; aX += cw[1][d] * v; aY += cw[2][d] * v; aZ += cw[3][d] * v;
                 }
                 st4(part + off * 4, aJ, aX, aY, aZ);
-
-                if (itop && (axis == 2 ? top_plane : q == NQ - 1)) {
-                    int i, j;
-                    natural_ij(axis, p, q, m, i, j);
-                    for (int d = 0; d < MAXD; ++d)
-                        if (D.up[d] && D.active[d]) itop[((long long)D.udx[d] * uny + j) * unx + i] = rw.v[d];
-                }
             }
+        };
+        // upward intensities leaving the top: the whole top plane of a z
+        // group, the last row of an x/y group
+        auto write_top = [&](int kk, const Row &rw) {
+            const int q = q0 + kk;
+            int i, j;
+            natural_ij(axis, p, q, m, i, j);
+            for (int d = 0; d < MAXD; ++d)
+                if (D.up[d] && D.active[d]) itop[((long long)D.udx[d] * uny + j) * unx + i] = rw.v[d];
         };
         if (act) {
 #pragma unroll
             for (int kk = 0; kk < TQ - 1; ++kk)
                 if (kk < nrows - 1) write_row(kk, nR[kk]);
             write_row(nrows - 1, rl);
+            if constexpr (acc) {
+                if (itop) {
+                    if (axis == 2 && top_plane) {
+#pragma unroll
+                        for (int kk = 0; kk < TQ - 1; ++kk)
+                            if (kk < nrows - 1) write_top(kk, nR[kk]);
+                        write_top(nrows - 1, rl);
+                    } else if (axis != 2 && q0 + nrows == NQ) {
+                        write_top(nrows - 1, rl);
+                    }
+                }
+            }
         }
         if (last) return 1;
         prefetch(t + 1);  // into the slot of plane t-1 (no longer read)

@@ -54,6 +54,23 @@ def test_ragged_fp64(rts, shape, B, spacing):
     _compare(got, ref, FP64_TOL, shape)
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", FP64_TOL), ("fp32", FP32_TOL)])
+def test_quadrature_with_empty_slots(rts, prec, tol):
+    """A 19-ray subset of the default set: five direction groups keep only 3
+    of their 4 sign slots, so those sweep units run with an empty slot."""
+    import oracle
+
+    n, w = oracle.a4_quadrature()
+    keep = [d for d in range(24) if d not in (1, 6, 11, 12, 21)]
+    n, w = np.ascontiguousarray(n[keep]), np.ascontiguousarray(w[keep] / w[keep].sum())
+    nx, ny, nz, B = 20, 18, 16, 2
+    chi, S = random_case(nx, ny, nz, B, seed=11)
+    s = rts.Solver(nx, ny, nz, B, precision=prec, n=n, w=w)
+    got = gpu_solve(s, chi, S)
+    ref = oracle_solve(chi, S, n=n, w=w)
+    _compare(got, ref, tol, "19 rays")
+
+
 def test_explicit_boundaries_fp64(rts):
     nx, ny, nz, B = 12, 10, 14, 2
     chi, S = random_case(nx, ny, nz, B, seed=3)
