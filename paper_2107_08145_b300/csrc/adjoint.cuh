@@ -134,11 +134,13 @@ __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restric
 // ---------------------------------------------------------------------------
 // 3. Reverse sweep of one tile (cotangent lam of the rays of one unit)
 // ---------------------------------------------------------------------------
-// Shared memory of a reverse tile: A = e lam of the 4 slots (the downwind
-// plane, kept once: new rows stay in registers until every thread has read
-// it), the two seed-error bounds (float), and chi of three planes (the own
-// plane, its forward-upwind plane and the next one in flight).
-enum { AF_A = 4, AF_X = 3, AF_G = 2 };
+// Shared memory of a reverse tile, (TQ+2) rows x (NP+2) columns per field like
+// the forward tile: A = e lam of the 4 slots of a point stored together
+// ([row][col][4]; the downwind plane, kept once: new rows stay in registers
+// until every thread has read it), chi of three planes (the own plane, its
+// forward-upwind plane and the next one in flight), and the two seed-error
+// bounds of a point as bf16 rounded up.
+enum { AF_A = 4, AF_X = 3 };
 // gradient terms written by the reverse sweep per point of a unit: B of the 4
 // slots, C of the 4 slots, the own chi and S terms
 constexpr int GRAD_CH = 2 * MAXD + 2;
@@ -146,10 +148,22 @@ constexpr int GRAD_CH = 2 * MAXD + 2;
 template <typename T>
 __host__ __device__ constexpr size_t adj_tile_smem_bytes(int tq, int np)
 {
-    return (size_t)(tq + 2) * (np + 2) * ((AF_A + AF_X) * sizeof(T) + AF_G * sizeof(float));
+    return (size_t)(tq + 2) * (np + 2) * ((AF_A + AF_X) * sizeof(T) + 2 * sizeof(unsigned short));
 }
 
 __device__ __forceinline__ void cp_async_wait_newest_pending() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// new values of one point of the reverse plane: e lam of the 4 slots and,
+// during the periodic warm-up, the carried bounds of the up / down rays
+template <typename T, bool ACC>
+struct AdjRow {
+    T A[MAXD];
+    float g[2];
+};
+template <typename T>
+struct AdjRow<T, true> {
+    T A[MAXD];
+};
 
 template <typename T, int TQ>
 __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug, int uidx, int r, int gt,
@@ -180,9 +194,9 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     const int c = p + 1;
     const int npp = NP + 2;
     const int FL = RW * npp;
-    T *const sA = (T *)smem;                    // A of slot d: sA + d * FL
-    T *const sX = sA + AF_A * FL;               // chi of reverse step t: sX + (t % 3) * FL
-    float *const sG = (float *)(sX + AF_X * FL);
+    T *const sA = (T *)smem;                                   // [FL][4]
+    T *const sX = sA + AF_A * FL;                              // chi of reverse step t: sX + (t % 3) * FL
+    unsigned short *const sG = (unsigned short *)(sX + AF_X * FL);  // [FL][2]
     auto fX = [&](int t) -> T * { return sX + (t % 3) * FL; };
 
     __shared__ DirConst<T> D;
@@ -214,10 +228,26 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     const bool has_lower = qper || r > 0;
     const bool has_upper = qper || r < ntl - 1;
 
-    auto put = [&](auto *f, int k, auto v) {
+    // periodic padding: thread p = 0 also writes column NP + 1 and thread
+    // p = NP - 1 column 0 (with NP == 1 the one thread writes both)
+    const bool padA = act && (p == 0 || p == NP - 1), padB = act && NP == 1;
+    const int pc = p == 0 ? NP + 1 : 0;
+    auto putA = [&](int k, T v0, T v1, T v2, T v3) {
+        st4(sA + (k * npp + c) * 4, v0, v1, v2, v3);
+        if (padA) st4(sA + (k * npp + pc) * 4, v0, v1, v2, v3);
+        if (padB) st4(sA + (k * npp) * 4, v0, v1, v2, v3);
+    };
+    auto putG = [&](int k, float gu, float gd) {
+        const unsigned w = bound16(gu) | bound16(gd) << 16;
+        unsigned *const g32 = (unsigned *)sG;
+        g32[k * npp + c] = w;
+        if (padA) g32[k * npp + pc] = w;
+        if (padB) g32[k * npp] = w;
+    };
+    auto putX = [&](T *f, int k, T v) {
         f[k * npp + c] = v;
-        if (p == 0) f[k * npp + NP + 1] = v;
-        if (p == NP - 1) f[k * npp] = v;
+        if (padA) f[k * npp + pc] = v;
+        if (padB) f[k * npp] = v;
     };
     // chi rows of reverse step t into slot t % 3
     auto prefetch = [&](int t) {
@@ -226,11 +256,11 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
             T *dx = fX(t);
             for (int k = 0; k < nrows + 2; ++k) {
                 const int q = s_q[k];
-                if (q < 0) { put(dx, k, T(0)); continue; }
+                if (q < 0) { putX(dx, k, T(0)); continue; }
                 const T *gx = chi + mo + (long long)q * sQ;
                 cp_async(dx + k * npp + c, gx);
-                if (p == 0) cp_async(dx + k * npp + NP + 1, gx);
-                if (p == NP - 1) cp_async(dx + k * npp, gx);
+                if (padA) cp_async(dx + k * npp + pc, gx);
+                if (padB) cp_async(dx + k * npp, gx);
             }
         }
         cp_async_commit();
@@ -249,14 +279,13 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     if (act) {
         for (int k = 0; k < nrows + 2; ++k) {
             const int q = s_q[k];
-            for (int d = 0; d < MAXD; ++d) put(sA + d * FL, k, T(0));
+            putA(k, T(0), T(0), T(0), T(0));
             float gu = 0.f, gd = 0.f;
             if (wrap && q >= 0) {
                 if (q != 0) gu = 1.f;
                 if (q != NQ - 1) gd = 1.f;
             }
-            put(sG, k, gu);
-            put(sG + FL, k, gd);
+            putG(k, gu, gd);
         }
     }
     prefetch(0);
@@ -269,18 +298,13 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
     const int warm_cap = a.max_periods * NM + a.L;
     const int dec_thread = NT > 32 ? 32 : 0;
 
-    for (int t = 0;; ++t) {
+    // One reverse step t. ACC: the plane is in the converged period (its
+    // gradient terms are written). Returns 0 to go on, 1 after the last
+    // plane, 2 to abandon the tile (a wait failed).
+    auto plane_step = [&](auto ACC, int t) __attribute__((always_inline)) -> int {
+        constexpr bool acc = decltype(ACC)::value;
+        using Row = AdjRow<T, acc>;
         const int m = plane_of(t, NM, msa);
-        if (t_acc < 0 && s_ctl[1]) {
-            t_acc = t;
-            if (r == 0 && tid == 0) a.unit_tacc[uidx] = t;
-        }
-        if (wrap && t_acc < 0 && t >= warm_cap) {
-            if (tid == 0) atomicOr(a.status, ST_NOCONV);
-            cp_async_wait_all();
-            return;
-        }
-        const bool acc = t_acc >= 0;
         const bool last = acc && (t - t_acc == NM - 1);
         const T *Xc = fX(t), *Xn = fX(t + 1);  // chi of this plane and of its forward-upwind plane
         // a z group's last reverse plane is its boundary layer (set points)
@@ -288,15 +312,9 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
         const bool top_plane = axis == 2 && t == 0 && sa > 0;
         float gmax = 0.f;
 
-        struct Row {
-            T A[MAXD];      // e lam of the 4 slots (zero at set points)
-            float g[2];     // bounds of the up / down rays (warm-up only)
-        };
-        Row nR[TQ], rl;
-
         // row k (1..nrows): lam from the downwind plane in shared memory, the
         // point's own cotangents, then A = e lam for the upwind plane
-        auto do_row = [&](int k) -> Row {
+        auto do_row = [&](int k) __attribute__((always_inline)) -> Row {
             Row out;
             const int q = q0 + k - 1;
             const int o = k * npp + c;
@@ -315,17 +333,21 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
             ld4(D.cJ, cw[0][0], cw[0][1], cw[0][2], cw[0][3]);
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) ld4(D.cF[cc], cw[cc + 1][0], cw[cc + 1][1], cw[cc + 1][2], cw[cc + 1][3]);
+            const T *Ab = sA + o * 4;
+            const int ar = npp * 4;
+            [[maybe_unused]] const unsigned short *Gb = sG + o * 2;
+            [[maybe_unused]] const int gr = npp * 2;
             float gu = 0.f, gd = 0.f, egu = 0.f, egd = 0.f;
-            T own_chi = 0, own_S = 0;
+            [[maybe_unused]] T own_chi = 0, own_S = 0;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) {
                 const int SP = (d & 1) ? -1 : 1, SQ = (d & 2) ? -1 : 1;  // compile time after unrolling
                 T b0, b1, b2, b3;
                 ld4(D.beta[d], b0, b1, b2, b3);
                 // downwind points r_c whose corner c is this point: offsets (+SP, +SQ)
-                const T *Ap = sA + d * FL + o;
-                const int oq = SQ * npp;
-                T lam = b0 * Ap[0] + b1 * Ap[SP] + b2 * Ap[oq] + b3 * Ap[oq + SP];
+                const T *Ap = Ab + d;
+                const int oq = SQ * ar;
+                T lam = b0 * Ap[0] + b1 * Ap[4 * SP] + b2 * Ap[oq] + b3 * Ap[oq + 4 * SP];
                 lam += cw[0][d] * gJ + cw[1][d] * gFx + cw[2][d] * gFy + cw[3][d] * gFz;
                 const bool isup = (upm >> d) & 1;
                 if (gitop && top && isup && ((actm >> d) & 1)) {
@@ -341,7 +363,7 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
                     seg_weights(hd[d] * (xup + xp), e, wu, wp);
                 }
                 out.A[d] = e * lam;
-                if (acc) {
+                if constexpr (acc) {
                     // gradient terms of this point's segment (lam known now):
                     // B = lam dI/dx ds/2 (to chi here and at the corners), C = lam w_up
                     // (to S at the corners), lam w_p (to S here); set points with
@@ -358,38 +380,43 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
                     }
                     gout[(long long)d * N + goff] = Bv;
                     gout[(long long)(MAXD + d) * N + goff] = Cv;
-                }
-                if (!acc) {
-                    const float *Gp = sG + (isup ? 0 : FL) + o;
-                    const float gg = (float)b0 * Gp[0] + (float)b1 * Gp[SP] + (float)b2 * Gp[oq] + (float)b3 * Gp[oq + SP];
+                } else {
+                    // bounds of the downwind points this point's ray d feeds (the
+                    // x/y groups' rising rays are the first value of a pair)
+                    const unsigned short *Gd = Gb + (isup ? 0 : 1);
+                    const int gq = SQ * gr;
+                    const float gg = (float)b0 * bound32(Gd[0]) + (float)b1 * bound32(Gd[2 * SP]) +
+                                     (float)b2 * bound32(Gd[gq]) + (float)b3 * bound32(Gd[gq + 2 * SP]);
                     if (isup) { gu = fmaxf(gu, gg); egu = fmaxf(egu, (float)e); }
                     else { gd = fmaxf(gd, gg); egd = fmaxf(egd, (float)e); }
                 }
             }
-            if (acc) {
+            if constexpr (acc) {
                 gout[(long long)(2 * MAXD) * N + goff] = own_chi;
                 gout[(long long)(2 * MAXD + 1) * N + goff] = own_S;
+            } else {
+                // the bound carried to the upwind plane: e * g (max over the rays of each set)
+                gu *= egu;
+                gd *= egd;
+                if (wrap && q == 0) gu = 0.f;
+                if (wrap && q == NQ - 1) gd = 0.f;
+                out.g[0] = gu;
+                out.g[1] = gd;
+                gmax = fmaxf(gmax, fmaxf(gu, gd));
             }
-            // the bound carried to the upwind plane: e * g (max over the rays of each set)
-            gu *= egu;
-            gd *= egd;
-            if (wrap && q == 0) gu = 0.f;
-            if (wrap && q == NQ - 1) gd = 0.f;
-            out.g[0] = gu;
-            out.g[1] = gd;
-            if (!acc) gmax = fmaxf(gmax, fmaxf(gu, gd));
             return out;
         };
-        auto to_ring = [&](int sd, Row rw) {
+        auto to_ring = [&](int sd, const Row &rw) __attribute__((always_inline)) {
             T *dst = myhalo + ((long long)((t & 1) * 2 + sd) * HALO_CH) * NP + p;
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) dst[(long long)d * NP] = rw.A[d];
-            if (!acc) {
+            if constexpr (!acc) {
                 dst[(long long)MAXD * NP] = (T)rw.g[0];
                 dst[(long long)(MAXD + 1) * NP] = (T)rw.g[1];
             }
         };
 
+        Row nR[TQ], rl;
         if (act) {
 #pragma unroll
             for (int k = 2; k < TQ; ++k)
@@ -415,19 +442,15 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
 #pragma unroll
                     for (int ch = 0; ch < HALO_CH; ++ch)
                         hv[ch] = (ch < MAXD || !acc) ? ld_cg(src + (long long)ch * NP) : T(0);
-#pragma unroll
-                    for (int d = 0; d < MAXD; ++d) put(sA + d * FL, row, hv[d]);
-                    if (!acc) {
-                        put(sG, row, (float)hv[MAXD]);
-                        put(sG + FL, row, (float)hv[MAXD + 1]);
-                    }
+                    putA(row, hv[0], hv[1], hv[2], hv[3]);
+                    if constexpr (!acc) putG(row, (float)hv[MAXD], (float)hv[MAXD + 1]);
                 }
             }
         }
         __syncthreads();  // B1
         if (s_ctl[0]) {
             cp_async_wait_all();
-            return;
+            return 2;
         }
         if (act) {
             nR[0] = do_row(1);
@@ -435,30 +458,30 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
             rl = nrows == 1 ? nR[0] : do_row(nrows);
             to_ring(1, rl);
         }
-        if (!acc) {
+        if constexpr (!acc) {
             for (int o = 16; o; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
             if (lane == 0) s_wmax[warp] = gmax;
-        }
-        if (tid == dec_thread && t_acc < 0 && t + 1 - a.L >= 0) {
-            const int ts = t + 1 - a.L;
-            const int slot = ts % a.R;
-            const unsigned want = (unsigned)ntl * (unsigned)(ts / a.R + 1);
-            bool ok = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
-            if (ok) {
-                const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
-                if ((unsigned)(v >> 32) != (unsigned)(ts + 1)) {
-                    atomicOr(a.status, ST_BADARG);
-                    ok = false;
-                } else {
-                    s_ctl[1] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.tol ? 1 : 0;
+            if (tid == dec_thread && t + 1 - a.L >= 0) {
+                const int ts = t + 1 - a.L;
+                const int slot = ts % a.R;
+                const unsigned want = (unsigned)ntl * (unsigned)(ts / a.R + 1);
+                bool ok = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
+                if (ok) {
+                    const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
+                    if ((unsigned)(v >> 32) != (unsigned)(ts + 1)) {
+                        atomicOr(a.status, ST_BADARG);
+                        ok = false;
+                    } else {
+                        s_ctl[1] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.tol ? 1 : 0;
+                    }
                 }
+                if (!ok) s_ctl[0] = 1;
             }
-            if (!ok) s_ctl[0] = 1;
         }
         __syncthreads();  // B2: step t's edge rows are in the ring; the downwind plane is no longer read
         if (tid == 0) {
             st_release(a.flags + gt, t + 1);
-            if (!acc) {
+            if constexpr (!acc) {
                 float g = 0.f;
                 for (int w = 0; w < (NT + 31) / 32; ++w) g = fmaxf(g, s_wmax[w]);
                 const int slot = t % a.R;
@@ -469,15 +492,11 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
         }
         if (s_ctl[0]) {
             cp_async_wait_all();
-            return;
+            return 2;
         }
-        auto write_row = [&](int kk, Row rw) {
-#pragma unroll
-            for (int d = 0; d < MAXD; ++d) put(sA + d * FL, kk + 1, rw.A[d]);
-            if (!acc) {
-                put(sG, kk + 1, rw.g[0]);
-                put(sG + FL, kk + 1, rw.g[1]);
-            }
+        auto write_row = [&](int kk, const Row &rw) __attribute__((always_inline)) {
+            putA(kk + 1, rw.A[0], rw.A[1], rw.A[2], rw.A[3]);
+            if constexpr (!acc) putG(kk + 1, rw.g[0], rw.g[1]);
         };
         if (act) {
 #pragma unroll
@@ -485,12 +504,37 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
                 if (kk < nrows - 1) write_row(kk, nR[kk]);
             write_row(nrows - 1, rl);
         }
-        if (last) break;
+        if (last) return 1;
         // chi of step t+3 into the slot of step t; step t+2's copy (issued a
         // step ago) must be complete before the barrier
         prefetch(t + 3);
         cp_async_wait_newest_pending();
         __syncthreads();  // B3
+        return 0;
+    };
+
+    // the periodic warm-up and the converged period run as two loops, each
+    // compiled for its own phase
+    int t = 0;
+    if (wrap) {
+        for (;; ++t) {
+            if (s_ctl[1]) {  // decision taken during the previous step
+                t_acc = t;
+                if (r == 0 && tid == 0) a.unit_tacc[uidx] = t;
+                break;
+            }
+            if (t >= warm_cap) {
+                if (tid == 0) atomicOr(a.status, ST_NOCONV);
+                cp_async_wait_all();
+                return;
+            }
+            if (plane_step(Flag<false>{}, t) == 2) return;
+        }
+    }
+    for (;; ++t) {
+        const int rc = plane_step(Flag<true>{}, t);
+        if (rc == 2) return;
+        if (rc == 1) break;
     }
     cp_async_wait_all();
 }

@@ -196,6 +196,7 @@ struct rts_handle {
     std::vector<int> unit_of_tile;
     int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, nt = 32, tq = 0, maxt = 0;  // maxt: register cap
     unsigned carveout = 100;      // forward sweep's shared-memory carveout (percent)
+    unsigned adj_carveout = 100;  // reverse sweep's
     size_t smem = 0;
     // reverse sweep: the same units tiled for the adjoint kernel
     std::vector<rts::SweepUnit> adj_units;
@@ -440,7 +441,7 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool 
     attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident
     attr[0].val.cooperative = 1;
     attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
-    attr[1].val.sharedMemCarveout = reverse ? 100u : h->carveout;
+    attr[1].val.sharedMemCarveout = reverse ? h->adj_carveout : h->carveout;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, a);
@@ -599,6 +600,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         h->adj_tq = ta.tq;
         h->adj_maxr = ta.maxt;
         h->adj_smem = ta.smem;
+        h->adj_carveout = carveout_percent(ta.blocks, ta.smem);
         h->adj_units.resize(max_units);
         h->adj_unit_of_tile.resize(max_tiles);
         PlanOut pa;
