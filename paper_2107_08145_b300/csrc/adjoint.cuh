@@ -593,7 +593,7 @@ __device__ __forceinline__ void load_pass_const(const SweepUnit &U, PassConst<T>
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) adj_gather_kernel(GradArgs<T> g, int maxNM)
+__global__ void __launch_bounds__(512) adj_gather_kernel(GradArgs<T> g, int maxNM)
 {
     const int uu = blockIdx.z / maxNM, m = blockIdx.z % maxNM;
     const SweepUnit &U = g.units[g.unit_base + uu];
@@ -611,17 +611,29 @@ __global__ void __launch_bounds__(128) adj_gather_kernel(GradArgs<T> g, int maxN
     if (U.wrap) md = md < 0 ? md + NM : (md >= NM ? md - NM : md);
     T gx = G[off], gs = G[N + off];
     if (md >= 0 && md < NM) {
+        // the 3 x 3 neighbourhood of (p, q) in the downwind plane: columns
+        // periodic in P, rows periodic or cut off in Q
+        const int col[3] = {p == 0 ? NP - 1 : p - 1, p, p + 1 == NP ? 0 : p + 1};
+        long long row[3];
+        bool rok[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int qr = q + k - 1;
+            rok[k] = true;
+            if (U.qper) qr = qr < 0 ? qr + NQ : (qr >= NQ ? qr - NQ : qr);
+            else rok[k] = qr >= 0 && qr < NQ;
+            row[k] = (long long)md * sM + (long long)qr * sQ;
+        }
+#pragma unroll
         for (int d = 0; d < MAXD; ++d) {
             if (!((K.active >> d) & 1)) continue;
-            const int sP = (d & 1) ? -1 : 1, sQd = (d & 2) ? -1 : 1;
+            const int sP = (d & 1) ? -1 : 1, sQd = (d & 2) ? -1 : 1;  // compile time after unrolling
+#pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
                 // the downwind point whose corner cc is this point
-                int pr = p + ((cc & 1) ? sP : 0);
-                pr = pr < 0 ? pr + NP : (pr >= NP ? pr - NP : pr);
-                int qr = q + ((cc & 2) ? sQd : 0);
-                if (U.qper) qr = qr < 0 ? qr + NQ : (qr >= NQ ? qr - NQ : qr);
-                else if (qr < 0 || qr >= NQ) continue;
-                const long long orr = (long long)md * sM + (long long)qr * sQ + pr;
+                const int kp = 1 + ((cc & 1) ? sP : 0), kq = 1 + ((cc & 2) ? sQd : 0);
+                if (!rok[kq]) continue;
+                const long long orr = row[kq] + col[kp];
                 const T bt = K.beta[d][cc];
                 gx += bt * B[(long long)d * N + orr];
                 gs += bt * C[(long long)d * N + orr];

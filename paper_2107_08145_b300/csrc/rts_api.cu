@@ -993,8 +993,10 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
             rts::GradArgs<T> gs = ga;
             gs.unit_base = us;
             gs.grad = ga.grad + (long long)(us - u0) * rts::GRAD_CH * N;
-            const dim3 gg((np + 127) / 128, nq, (unsigned)(nm * (ue - us)));
-            rts::adj_gather_kernel<T><<<gg, 128, 0, st>>>(gs, nm);
+            // a row of the plane per block (up to 512 columns)
+            const int gt = std::min(512, 32 * ((np + 31) / 32));
+            const dim3 gg((np + gt - 1) / gt, nq, (unsigned)(nm * (ue - us)));
+            rts::adj_gather_kernel<T><<<gg, gt, 0, st>>>(gs, nm);
             CUDA_TRY(h, cudaGetLastError());
             kernels += 1;
         }
