@@ -58,13 +58,31 @@ __device__ __forceinline__ double coef_z(int q, int k, const QAdjParams &P)
 // QJ_b = 4 pi chi_b (J_b - S_b), QF_b = -div F_b, D the divergence stencil.
 // The blend weights are evaluated exactly as the forward Q step does (in the
 // sweep precision, blend_weights), so this is the derivative of the computed
-// function. Bands b0 .. b1-1; JF, lam0, direct are indexed by band.
+// function. Bands b0 .. b1-1; JF, lam0, direct are indexed by band; u
+// ([b1-b0][N], from qstep_adjoint_u_kernel) only when gQ is given.
+template <typename T>
+__global__ void __launch_bounds__(256) qstep_adjoint_u_kernel(const T *__restrict__ chi,
+                                                               const double *__restrict__ gQ, QAdjParams P, int b0,
+                                                               int b1, T *__restrict__ u)
+{
+    const long long N = (long long)P.nx * P.ny * P.nz, total = (long long)(b1 - b0) * N;
+    const T thin = (T)P.thin;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long bb = idx / N, p = idx - bb * N;
+        T om, omc;
+        blend_weights(chi[(b0 + bb) * N + p], thin, om, omc);
+        u[idx] = (T)gQ[p] * omc;
+    }
+}
+
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restrict__ JF, const T *__restrict__ chi,
                                                              const T *__restrict__ S, const double *__restrict__ gJ,
                                                              const double *__restrict__ gF,
-                                                             const double *__restrict__ gQ, QAdjParams P, int b0,
-                                                             int b1, T *__restrict__ lam0, T *__restrict__ direct)
+                                                             const double *__restrict__ gQ, const T *__restrict__ u,
+                                                             QAdjParams P, int b0, int b1, T *__restrict__ lam0,
+                                                             T *__restrict__ direct)
 {
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
@@ -83,12 +101,8 @@ __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restric
         const T *cb = chi + (long long)b * N;
         const Acc *jf = JF + (long long)b * 4 * N;
         // cancelling differences in FP64, the rest in the sweep precision T
-        auto u_at = [&](long long q) -> T {  // gQ (1 - om_b) at point q
-            if (!gQ) return T(0);
-            T om, omc;
-            blend_weights(cb[q], thin, om, omc);
-            return (T)gQ[q] * omc;
-        };
+        const T *ub = gQ ? u + (long long)(b - b0) * N : nullptr;
+        auto u_at = [&](long long q) -> T { return ub ? ub[q] : T(0); };  // gQ (1 - om_b) at point q
         T om, omc;
         blend_weights(cb[p], thin, om, omc);
         const T c = cb[p];

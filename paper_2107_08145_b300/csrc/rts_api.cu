@@ -942,8 +942,19 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
         if (rts_status ms = mark(1)) return ms;
         {  // Q step transposed for the chunk's bands
             const dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
+            // gQ (1 - om_b) of the chunk's bands, read by the divergence
+            // transpose at the neighbours; the gradient scratch is free here
+            T *u = nullptr;
+            if (gQ) {
+                u = (T *)h->d_grad;
+                const long long total = (long long)(b1 - b0) * N;
+                const int ub = (int)std::min<long long>((total + 255) / 256, 148LL * 16);
+                rts::qstep_adjoint_u_kernel<T><<<ub, 256, 0, st>>>((const T *)chi, gQ, QP, b0, b1, u);
+                CUDA_TRY(h, cudaGetLastError());
+                kernels += 1;
+            }
             rts::qstep_adjoint_kernel<T, Acc><<<qg, tb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S,
-                                                                gJ, gF, gQ, QP, b0, b1, (T *)h->d_lam0,
+                                                                gJ, gF, gQ, u, QP, b0, b1, (T *)h->d_lam0,
                                                                 (T *)h->d_direct);
             CUDA_TRY(h, cudaGetLastError());
             kernels += 1;
