@@ -602,12 +602,20 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
         // the plane's new rows, kept in registers until the previous plane is no
         // longer read: rows 1 .. nrows-1 in nR (constant indices only), the last in rl
         Row nR[TQ], rl;
+        // a full tile (every tile but a short last one) takes the rows
+        // without per-row guards, so their code can interleave
+        const bool full = nrows == TQ;
         // ---- interior rows need only this tile's own rows of the previous
         //      plane; meanwhile the neighbours finish their edge rows ----
         if (act) {
+            if (full) {
 #pragma unroll
-            for (int k = 2; k < TQ; ++k)
-                if (k < nrows) nR[k - 1] = do_row(k, Flag<false>{});
+                for (int k = 2; k < TQ; ++k) nR[k - 1] = do_row(k, Flag<false>{});
+            } else {
+#pragma unroll
+                for (int k = 2; k < TQ; ++k)
+                    if (k < nrows) nR[k - 1] = do_row(k, Flag<false>{});
+            }
         }
         // ---- one thread waits for the neighbours' plane t-1 (acquire); after
         //      the barrier every thread loads its column of their edge rows
@@ -646,7 +654,8 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
         if (act) {
             nR[0] = do_row(1, Flag<true>{});
             to_ring(0, nR[0]);
-            rl = nrows == 1 ? nR[0] : do_row(nrows, Flag<true>{});
+            if (full) rl = TQ == 1 ? nR[0] : do_row(TQ, Flag<true>{});
+            else rl = nrows == 1 ? nR[0] : do_row(nrows, Flag<true>{});
             to_ring(1, rl);
         }
         if constexpr (!acc) {
@@ -716,10 +725,16 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 if (D.up[d] && D.active[d]) itop[((long long)D.udx[d] * uny + j) * unx + i] = rw.v[d];
         };
         if (act) {
+            if (full) {
 #pragma unroll
-            for (int kk = 0; kk < TQ - 1; ++kk)
-                if (kk < nrows - 1) write_row(kk, nR[kk]);
-            write_row(nrows - 1, rl);
+                for (int kk = 0; kk < TQ - 1; ++kk) write_row(kk, nR[kk]);
+                write_row(TQ - 1, rl);
+            } else {
+#pragma unroll
+                for (int kk = 0; kk < TQ - 1; ++kk)
+                    if (kk < nrows - 1) write_row(kk, nR[kk]);
+                write_row(nrows - 1, rl);
+            }
             if constexpr (acc) {
                 if (itop) {
                     if (axis == 2 && top_plane) {
