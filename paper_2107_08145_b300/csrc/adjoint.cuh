@@ -353,6 +353,9 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
             [[maybe_unused]] const int gr = npp * 2;
             float gu = 0.f, gd = 0.f, egu = 0.f, egd = 0.f;
             [[maybe_unused]] T own_chi = 0, own_S = 0;
+            // the checkpoint's D of the 4 slots of this point (converged period only)
+            [[maybe_unused]] T ckv[MAXD];
+            if constexpr (acc) ld_part(ck + goff * MAXD, ckv);
 #pragma unroll
             for (int d = 0; d < MAXD; ++d) {
                 const int SP = (d & 1) ? -1 : 1, SQ = (d & 2) ? -1 : 1;  // compile time after unrolling
@@ -384,7 +387,7 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
                     // I = S pass lam to S
                     T Bv = 0, Cv = 0;
                     if (((actm >> d) & 1) && !set) {
-                        const T dI = ck[(long long)d * N + goff];
+                        const T dI = ckv[d];
                         Bv = lam * dI * hd[d];
                         Cv = lam * wu;
                         own_chi += Bv;

@@ -221,7 +221,7 @@ struct rts_handle {
     int *d_ru_begin = nullptr;
     // adjoint scratch (RTS_FLAG_ADJOINT): lam0 [B][4][N] natural and
     // x-transposed, direct Q-step terms [B][2][N], and per checkpoint chunk of
-    // at most chunk_units units: the checkpoint [u][STORE_CH*4][N] and the
+    // at most chunk_units units: the checkpoint [u][N][STORE_CH*4] and the
     // gradient terms [u][GRAD_CH][N]
     void *d_lam0 = nullptr, *d_lam0T = nullptr, *d_direct = nullptr;
     void *d_ckpt = nullptr, *d_grad = nullptr;

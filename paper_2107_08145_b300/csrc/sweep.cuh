@@ -85,10 +85,11 @@ struct SweepArgs {
     const int *unit_of_tile;
     int total_tiles;            // tiles of this launch: tile_base .. tile_base+total_tiles-1
     int tile_base, unit_base;   // first tile and first unit of this launch
-    // optional (forward: checkpoint for the adjoint): per accumulated point and
-    // slot d of unit u, at store + (u-unit_base)*STORE_CH*MAXD*N + d*N, the
-    // segment's D = dI/d(dtau) (0 at set points). Reverse sweep: the gradient
-    // terms, see adjoint.cuh.
+    // optional (forward: checkpoint for the adjoint): per accumulated point
+    // (offset off in the unit's layout) and slot d of unit u, at
+    // store + (u-unit_base)*STORE_CH*MAXD*N + off*MAXD + d (the 4 slots of a
+    // point together), the segment's D = dI/d(dtau) (0 at set points).
+    // Reverse sweep: the gradient terms, see adjoint.cuh.
     T *store;
     // reverse (adjoint) sweep only
     const T *lam0, *lam0T;      // [B][4][N] cotangents of J_b, F_b (natural / x-transposed layout)
@@ -471,8 +472,8 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
                 const long long off = (long long)m * sM + (long long)s_q[k] * sQ + p;
                 st4(part + off * 4, aJ, aX, aY, aZ);
                 if (CKPT) {  // boundary plane: set points, no segment
-                    T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + off;
-                    for (int d = 0; d < STORE_CH * MAXD; ++d) st[(long long)d * N] = T(0);
+                    st4(a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + off * MAXD, T(0), T(0), T(0),
+                        T(0));
                 }
             }
         }
@@ -570,15 +571,16 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
             // an empty slot has zero weights and path length (e = q = 1, I_up =
             // S_up = 0), so its intensity stays exactly 0 without a mask
             if constexpr (CKPT && acc) {
-                T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N + (long long)m * sM +
-                        (long long)q * sQ + p;
+                T *st = a.store + (long long)(uidx - a.unit_base) * STORE_CH * MAXD * N +
+                        ((long long)m * sM + (long long)q * sQ + p) * MAXD;
+                T cv[MAXD];
 #pragma unroll
                 for (int d = 0; d < MAXD; ++d) {
                     const bool set = bnd && (d < 2 ? q == 0 : q == NQ - 1);
                     const bool live = ((actm >> d) & 1) && !set;
-#pragma unroll
-                    for (int ch = 0; ch < STORE_CH; ++ch) st[(long long)(ch * MAXD + d) * N] = live ? ck[ch][d] : T(0);
+                    cv[d] = live ? ck[0][d] : T(0);
                 }
+                st4(st, cv[0], cv[1], cv[2], cv[3]);
             }
             if constexpr (!acc) {
                 out.g[0] = gu;
