@@ -134,11 +134,8 @@ __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restric
             if (cf != T(0)) dTz += u_at((long long)q * pl + (long long)j * nx + i) * cf;
         }
         const double gFz = (gF ? gF[2 * N + p] : 0.0) - (double)dTz;
-        T *l0 = lam0 + (long long)b * 4 * N;
-        l0[p] = (T)gJb;
-        l0[N + p] = (T)gFx;
-        l0[2 * N + p] = (T)gFy;
-        l0[3 * N + p] = (T)gFz;
+        // lam0 of a point together ([b][N][4]), one vector store
+        st4(lam0 + ((long long)b * N + p) * 4, (T)gJb, (T)gFx, (T)gFy, (T)gFz);
         T *dr = direct + (long long)b * 2 * N;
         dr[p] = (T)gchi;
         dr[N + p] = (T)gs;
@@ -333,7 +330,9 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
             const int q = q0 + k - 1;
             const int o = k * npp + c;
             const long long goff = (long long)m * sM + (long long)q * sQ + p;
-            const T gJ = l0[goff], gFx = l0[N + goff], gFy = l0[2 * N + goff], gFz = l0[3 * N + goff];
+            T lv[4];
+            ld_part(l0 + goff * 4, lv);
+            const T gJ = lv[0], gFx = lv[1], gFy = lv[2], gFz = lv[3];
             const bool top = axis == 2 ? top_plane : q == NQ - 1;
             // forward-upwind plane's chi on the 3 x 3 neighbourhood, shared by the rays
             T xs[3][3];

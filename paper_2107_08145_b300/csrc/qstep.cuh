@@ -38,6 +38,12 @@ __device__ __forceinline__ void transpose_tile(const T *__restrict__ in, T *__re
     }
 }
 
+// four values moved as one element (the adjoint's lam0 of a point)
+template <typename T>
+struct __align__(16) Vec4 {
+    T v[4];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(256) transpose_x_kernel(const T *__restrict__ in, T *__restrict__ out,
                                                             int nx, int ny, int nz)

@@ -219,7 +219,7 @@ struct rts_handle {
     unsigned long long *d_gmax = nullptr;
     rts::RedUnit *d_ru = nullptr;
     int *d_ru_begin = nullptr;
-    // adjoint scratch (RTS_FLAG_ADJOINT): lam0 [B][4][N] natural and
+    // adjoint scratch (RTS_FLAG_ADJOINT): lam0 [B][N][4] natural and
     // x-transposed, direct Q-step terms [B][2][N], and per checkpoint chunk of
     // at most chunk_units units: the checkpoint [u][N][STORE_CH*4] and the
     // gradient terms [u][GRAD_CH][N]
@@ -959,10 +959,11 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
             CUDA_TRY(h, cudaGetLastError());
             kernels += 1;
             if (h->has_x) {
-                const dim3 lg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * nbc * 4));
-                rts::transpose_x_kernel<T><<<lg, tb, 0, st>>>((const T *)h->d_lam0 + (long long)b0 * 4 * N,
-                                                             (T *)h->d_lam0T + (long long)b0 * 4 * N, g.nx, g.ny,
-                                                             g.nz);
+                // lam0 [b][N][4]: the 4 values of a point move as one element
+                const dim3 lg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * nbc));
+                rts::transpose_x_kernel<rts::Vec4<T>><<<lg, tb, 0, st>>>(
+                    (const rts::Vec4<T> *)((const T *)h->d_lam0 + (long long)b0 * 4 * N),
+                    (rts::Vec4<T> *)((T *)h->d_lam0T + (long long)b0 * 4 * N), g.nx, g.ny, g.nz);
                 CUDA_TRY(h, cudaGetLastError());
                 kernels += 1;
             }

@@ -92,7 +92,7 @@ struct SweepArgs {
     // Reverse sweep: the gradient terms, see adjoint.cuh.
     T *store;
     // reverse (adjoint) sweep only
-    const T *lam0, *lam0T;      // [B][4][N] cotangents of J_b, F_b (natural / x-transposed layout)
+    const T *lam0, *lam0T;      // [B][N][4] cotangents of J_b, F_b (natural / x-transposed layout)
     const T *gitop;             // [B][n_up][ny][nx] cotangent of I_top, or null
     const T *ckpt;              // the checkpoint sweep's store (layout of `store`, forward)
     // per-call data
