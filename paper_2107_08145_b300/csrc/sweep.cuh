@@ -409,19 +409,28 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
     };
     // asynchronous copy of this thread's column of the chi/S rows of plane t
     // into slot t & 1
+    auto prefetch_row = [&](T *f, long long mo, int k) __attribute__((always_inline)) {
+        const int q = s_q[k];
+        if (q < 0) {
+            putXS(f, k, T(0), T(0));
+            return;
+        }
+        const T *gx = chi + mo + (long long)q * sQ, *gs = Sg + mo + (long long)q * sQ;
+        T *d0 = f + (k * npp + c) * 2;
+        cp_async(d0, gx);
+        cp_async(d0 + 1, gs);
+        if (padA) { T *d1 = f + (k * npp + pc) * 2; cp_async(d1, gx); cp_async(d1 + 1, gs); }
+        if (padB) { T *d1 = f + (k * npp) * 2; cp_async(d1, gx); cp_async(d1 + 1, gs); }
+    };
     auto prefetch = [&](int t) {
         if (act) {
             const long long mo = (long long)plane_of(t, NM, sa) * sM + p;
             T *f = fXS(t);
-            for (int k = 0; k < nrows + 2; ++k) {
-                const int q = s_q[k];
-                if (q < 0) { putXS(f, k, T(0), T(0)); continue; }
-                const T *gx = chi + mo + (long long)q * sQ, *gs = Sg + mo + (long long)q * sQ;
-                T *d0 = f + (k * npp + c) * 2;
-                cp_async(d0, gx);
-                cp_async(d0 + 1, gs);
-                if (padA) { T *d1 = f + (k * npp + pc) * 2; cp_async(d1, gx); cp_async(d1 + 1, gs); }
-                if (padB) { T *d1 = f + (k * npp) * 2; cp_async(d1, gx); cp_async(d1 + 1, gs); }
+            if (nrows == TQ) {  // full tile: the TQ + 2 rows unrolled
+#pragma unroll
+                for (int k = 0; k < TQ + 2; ++k) prefetch_row(f, mo, k);
+            } else {
+                for (int k = 0; k < nrows + 2; ++k) prefetch_row(f, mo, k);
             }
         }
         cp_async_commit();
