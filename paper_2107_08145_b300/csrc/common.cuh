@@ -71,6 +71,32 @@ __device__ __forceinline__ bool wait_flag_geq(const int *flag, int want, int *st
     }
 }
 
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ void st_relaxed(int *p, int v)
+{
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until pair[0] >= w0 and pair[1] >= w1 (8-byte aligned pair), both
+// read by one 8-byte acquire load per poll; limits as wait_flag_geq.
+__device__ __forceinline__ bool wait_pair_geq(const int *pair, int w0, int w1, int *status, uint64_t limit_ns)
+{
+    const unsigned long long *p64 = reinterpret_cast<const unsigned long long *>(pair);
+    auto ready = [&](unsigned long long v) { return (int)(unsigned)(v & 0xffffffffu) >= w0 && (int)(unsigned)(v >> 32) >= w1; };
+    if (ready(ld_acquire64(p64))) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        __nanosleep(64);
+        if (ready(ld_acquire64(p64))) return true;
+        if (ld_relaxed(status) != 0) return false;
+        if (global_ns() - t0 > limit_ns) {
+            atomicOr(status, ST_TIMEOUT);
+            return false;
+        }
+    }
+}
+
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
 {
     unsigned v;

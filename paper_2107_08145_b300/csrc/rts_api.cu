@@ -204,7 +204,7 @@ struct rts_handle {
     rts::SweepUnit *d_adj_units = nullptr;
     int *d_adj_uot = nullptr;
     int adj_tq = 0, adj_maxr = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
-    int flag_tiles = 0;           // ready flags allocated (max over both tilings)
+    int flag_tiles = 0;           // ready flags allocated (forward pairs, reverse singles: the max)
     size_t adj_smem = 0;
     bool has_x = false;
     long long N = 0;
@@ -588,7 +588,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->band_unit.assign(nbands + 1, 0);
     for (size_t u = 0; u < h->units.size(); ++u) h->band_unit[h->units[u].band + 1]++;
     for (int b = 0; b < nbands; ++b) h->band_unit[b + 1] += h->band_unit[b];
-    int flag_tiles = h->total_tiles, max_nt = h->max_ntiles;
+    int flag_tiles = 2 * h->total_tiles, max_nt = h->max_ntiles;  // forward: a pair per tile
     if (adjoint) {
         h->chunk_bands = std::min(nbands, std::max(1, o.adjoint_chunk_bands));
         for (int b = 0; b < nbands; b += h->chunk_bands) {
@@ -791,7 +791,7 @@ static rts::SweepArgs<T> sweep_args(rts_handle *h, const void *chi, const void *
 static rts_status reset_sweep_state(rts_handle *h, cudaStream_t st)
 {
     CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * std::max(h->flag_tiles, h->total_tiles), st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * std::max(h->flag_tiles, 2 * h->total_tiles), st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
     return RTS_OK;
@@ -806,7 +806,7 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     cudaStream_t st = h->stream;
     CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * h->total_tiles, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * 2 * h->total_tiles, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
@@ -1328,7 +1328,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     const size_t o_uot = take(sizeof(int) * ntile);
     const size_t o_ru = take(sizeof(rts::RedUnit) * nunits);
     const size_t o_rub = take(sizeof(int) * (B + 1));
-    const size_t o_flags = take(sizeof(int) * ntile);
+    const size_t o_flags = take(sizeof(int) * 2 * ntile);  // a pair per tile
     const size_t o_gcnt = take(sizeof(unsigned int) * nunits * R);
     const size_t o_gmax = take(sizeof(unsigned long long) * nunits * R);
     const size_t o_ctl = take(sizeof(int) * 8);  // ticket, status
@@ -1373,7 +1373,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     NA_TRY(cudaMemcpyAsync(base + o_uot, unit_of_tile, sizeof(int) * ntile, cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemcpyAsync(base + o_ru, ru, sizeof(rts::RedUnit) * nunits, cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemcpyAsync(base + o_rub, rub, sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
-    NA_TRY(cudaMemsetAsync(base + o_flags, 0, sizeof(int) * ntile, st));
+    NA_TRY(cudaMemsetAsync(base + o_flags, 0, sizeof(int) * 2 * ntile, st));
     NA_TRY(cudaMemsetAsync(base + o_gcnt, 0, sizeof(unsigned int) * nunits * R, st));
     NA_TRY(cudaMemsetAsync(base + o_gmax, 0, sizeof(unsigned long long) * nunits * R, st));
     NA_TRY(cudaMemsetAsync(base + o_ctl, 0, sizeof(int) * 8, st));
@@ -1658,7 +1658,7 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     h->R = R;
 
     h->grid = std::min(h->total_tiles, tl.blocks * nsm);
-    h->flag_tiles = h->total_tiles;
+    h->flag_tiles = 2 * h->total_tiles;  // a pair per tile
 
     // ---- device memory ----
     const size_t es = h->esize;
@@ -1671,7 +1671,7 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     const size_t o_ST = h->has_x ? take((size_t)h->in_total * es) : 0;
     const size_t o_JF = take((size_t)jf_off * 8);
     const size_t o_halo = take((size_t)halo * es);
-    const size_t o_flags = take(sizeof(int) * h->total_tiles);
+    const size_t o_flags = take(sizeof(int) * 2 * h->total_tiles);
     const size_t o_gcnt = take(sizeof(unsigned int) * nunits * R);
     const size_t o_gmax = take(sizeof(unsigned long long) * nunits * R);
     const size_t o_ticket = take(sizeof(int) * 4);

@@ -12,8 +12,9 @@
 //    CTA owns one tile for the whole sweep and keeps the previous plane (I
 //    and the seed-error bound g, by plane parity) and three planes of chi
 //    and S (the next one prefetched a whole plane ahead with cp.async) in
-//    shared memory. Each plane: integrate the interior rows; each thread
-//    acquires the neighbours' flags and loads its column of their edge rows
+//    shared memory. Each plane: integrate the interior rows; one thread
+//    acquires the neighbours' flags (one 8-byte load: each tile keeps the
+//    pair its two neighbours write) and every thread loads its column of their edge rows
 //    into the halo rows; barrier; integrate the edge rows and write them to
 //    the ring; barrier; release the tile's flag; only then store the
 //    plane's partial sums, so the release never waits for those stores. Only the
@@ -43,6 +44,7 @@
 // is swept and accumulated. Unlike a residual test this needs no second pass
 // to confirm convergence.
 #pragma once
+#include <climits>
 #include <type_traits>
 
 #include "common.cuh"
@@ -104,7 +106,10 @@ struct SweepArgs {
     int n_up, n_dn;
     // scratch
     int *ticket;
-    int *flags;                 // [total_tiles] published plane + 1
+    // forward: [total_tiles][2] per tile the planes (+1) its lower and its
+    // upper neighbour have published, read together; reverse: [total_tiles]
+    // the plane (+1) the tile has published
+    int *flags;
     T *halo;                    // per tile: [2 slots][2 sides][HALO_CH][NP]
     unsigned int *gcnt;         // [units][R] tiles that posted a plane (cumulative per slot)
     unsigned long long *gmax;   // [units][R] (plane+1)<<32 | bits(max g), atomic max
@@ -634,8 +639,8 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
         if (t > t_first) {
             if (tid == 0) {
                 bool ok = true;
-                if (has_lower) ok = wait_flag_geq(a.flags + tile0 + lower, t, a.status, a.timeout_ns);
-                if (ok && has_upper) ok = wait_flag_geq(a.flags + tile0 + upper, t, a.status, a.timeout_ns);
+                ok = wait_pair_geq(a.flags + 2 * gt, has_lower ? t : INT_MIN, has_upper ? t : INT_MIN, a.status,
+                                   a.timeout_ns);
                 if (!ok) s_ctl[0] = 1;
             }
             __syncthreads();  // B0: the neighbours' rows of plane t-1 are published (or the wait failed)
@@ -692,8 +697,12 @@ __device__ void run_tile(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug
         }
         __syncthreads();  // B2: plane t's edge rows are in the ring; the previous plane is no longer read
         if (tid == 0) {
-            // release the edge rows (the barrier orders the CTA's ring writes first)
-            st_release(a.flags + gt, t + 1);
+            // release the edge rows (the barrier orders the CTA's ring writes
+            // before the fence) to the tile above, as its lower neighbour's,
+            // and to the tile below, as its upper neighbour's
+            fence_acq_rel_gpu();
+            if (has_upper) st_relaxed(a.flags + 2 * (tile0 + upper), t + 1);
+            if (has_lower) st_relaxed(a.flags + 2 * (tile0 + lower) + 1, t + 1);
             if constexpr (!acc) {
                 float g = 0.f;
                 for (int w = 0; w < (NT + 31) / 32; ++w) g = fmaxf(g, s_wmax[w]);
