@@ -441,8 +441,8 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
         if (t > 0) {
             if (tid == 0) {
                 bool ok = true;
-                if (has_lower) ok = wait_flag_geq(a.flags + tile0 + lower, t, a.status, a.timeout_ns);
-                if (ok && has_upper) ok = wait_flag_geq(a.flags + tile0 + upper, t, a.status, a.timeout_ns);
+                ok = wait_pair_geq(a.flags + 2 * gt, has_lower ? t : INT_MIN, has_upper ? t : INT_MIN, a.status,
+                                   a.timeout_ns);
                 if (!ok) s_ctl[0] = 1;
             }
             __syncthreads();  // B0: the neighbours' rows of step t-1 are published (or the wait failed)
@@ -496,7 +496,10 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
         }
         __syncthreads();  // B2: step t's edge rows are in the ring; the downwind plane is no longer read
         if (tid == 0) {
-            st_release(a.flags + gt, t + 1);
+            // to the tile above (as its lower neighbour) and the tile below (as its upper)
+            fence_acq_rel_gpu();
+            if (has_upper) st_relaxed(a.flags + 2 * (tile0 + upper), t + 1);
+            if (has_lower) st_relaxed(a.flags + 2 * (tile0 + lower) + 1, t + 1);
             if constexpr (!acc) {
                 float g = 0.f;
                 for (int w = 0; w < (NT + 31) / 32; ++w) g = fmaxf(g, s_wmax[w]);

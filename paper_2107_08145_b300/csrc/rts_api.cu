@@ -204,7 +204,7 @@ struct rts_handle {
     rts::SweepUnit *d_adj_units = nullptr;
     int *d_adj_uot = nullptr;
     int adj_tq = 0, adj_maxr = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
-    int flag_tiles = 0;           // ready flags allocated (forward pairs, reverse singles: the max)
+    int flag_tiles = 0;           // ready flags allocated (a pair per tile, max over both tilings)
     size_t adj_smem = 0;
     bool has_x = false;
     long long N = 0;
@@ -614,7 +614,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         h->adj_max_ntiles = pa.max_ntiles;
         h->grid_adj = std::min(pa.ntiles, ta.blocks * nsm);
         halo_elems = std::max(halo_elems, pa.halo_elems);
-        flag_tiles = std::max(flag_tiles, pa.ntiles);
+        flag_tiles = std::max(flag_tiles, 2 * pa.ntiles);
         max_nt = std::max(max_nt, pa.max_ntiles);
     }
     h->flag_tiles = flag_tiles;

@@ -106,9 +106,8 @@ struct SweepArgs {
     int n_up, n_dn;
     // scratch
     int *ticket;
-    // forward: [total_tiles][2] per tile the planes (+1) its lower and its
-    // upper neighbour have published, read together; reverse: [total_tiles]
-    // the plane (+1) the tile has published
+    // [total_tiles][2]: per tile the planes (+1) its lower and its upper
+    // neighbour have published, read together
     int *flags;
     T *halo;                    // per tile: [2 slots][2 sides][HALO_CH][NP]
     unsigned int *gcnt;         // [units][R] tiles that posted a plane (cumulative per slot)
