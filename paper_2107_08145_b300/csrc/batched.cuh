@@ -57,6 +57,21 @@ __global__ void __launch_bounds__(256) transpose_x_batched(const SubDesc *__rest
     transpose_tile(in + sd.in_off, out + sd.in_off, sd.nx, sd.ny, sd.nz, bx * 32, by * 32, bk / sd.nz, bk % sd.nz);
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_x2_batched(const SubDesc *__restrict__ d, int nsub, int B,
+                                                              const T *__restrict__ in0, const T *__restrict__ in1,
+                                                              T *__restrict__ out0, T *__restrict__ out1)
+{
+    const int s = find_sub(d, nsub, 0, blockIdx.x);
+    const SubDesc &sd = d[s];
+    const int r = blockIdx.x - sd.blk[0];
+    const int tx = (sd.nx + 31) / 32, ty = (sd.ny + 31) / 32;
+    const int bx = r % tx, by = (r / tx) % ty;
+    const long long bk = r / (tx * ty);
+    transpose_tile2(in0 + sd.in_off, in1 + sd.in_off, out0 + sd.in_off, out1 + sd.in_off, sd.nx, sd.ny, sd.nz, bx * 32,
+                    by * 32, bk / sd.nz, bk % sd.nz);
+}
+
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) reduce_units_batched(const SubDesc *__restrict__ d, int nsub,
                                                             const RedUnit *__restrict__ ru,

@@ -38,6 +38,45 @@ __device__ __forceinline__ void transpose_tile(const T *__restrict__ in, T *__re
     }
 }
 
+// the same tile of two arrays at once (chi and S: all 8 loads of a thread
+// in flight together, one launch for both)
+template <typename T>
+__device__ __forceinline__ void transpose_tile2(const T *__restrict__ in0, const T *__restrict__ in1,
+                                                T *__restrict__ out0, T *__restrict__ out1, int nx, int ny, int nz,
+                                                int i0, int j0, long long b, long long k)
+{
+    __shared__ T tile[2][32][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const long long so = (b * nz + k) * (long long)ny * nx;
+#pragma unroll
+    for (int jj = ty; jj < 32; jj += 8) {
+        const int i = i0 + tx, j = j0 + jj;
+        if (i < nx && j < ny) {
+            tile[0][jj][tx] = in0[so + (long long)j * nx + i];
+            tile[1][jj][tx] = in1[so + (long long)j * nx + i];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ii = ty; ii < 32; ii += 8) {
+        const int i = i0 + ii, j = j0 + tx;
+        if (i < nx && j < ny) {
+            const long long o = ((b * nx + i) * nz + k) * (long long)ny + j;
+            out0[o] = tile[0][tx][ii];
+            out1[o] = tile[1][tx][ii];
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) transpose_x2_kernel(const T *__restrict__ in0, const T *__restrict__ in1,
+                                                             T *__restrict__ out0, T *__restrict__ out1, int nx,
+                                                             int ny, int nz)
+{
+    const long long bk = blockIdx.z;
+    transpose_tile2(in0, in1, out0, out1, nx, ny, nz, blockIdx.x * 32, blockIdx.y * 32, bk / nz, bk % nz);
+}
+
 // four values moved as one element (the adjoint's lam0 of a point)
 template <typename T>
 struct __align__(16) Vec4 {

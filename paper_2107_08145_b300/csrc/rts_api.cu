@@ -823,10 +823,10 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     int kernels = 0;
     if (h->has_x) {
         dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
-        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)h->d_chiT, g.nx, g.ny, g.nz);
-        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)h->d_ST, g.nx, g.ny, g.nz);
+        rts::transpose_x2_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (const T *)S, (T *)h->d_chiT, (T *)h->d_ST,
+                                                      g.nx, g.ny, g.nz);
         CUDA_TRY(h, cudaGetLastError());
-        kernels += 2;
+        kernels += 1;
     }
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[1], st));
     rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
@@ -905,10 +905,10 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
         ++h->adj_calls;
     }
     if (h->has_x) {
-        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)h->d_chiT, g.nx, g.ny, g.nz);
-        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)h->d_ST, g.nx, g.ny, g.nz);
+        rts::transpose_x2_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (const T *)S, (T *)h->d_chiT, (T *)h->d_ST,
+                                                      g.nx, g.ny, g.nz);
         CUDA_TRY(h, cudaGetLastError());
-        kernels += 2;
+        kernels += 1;
     }
     if (rts_status ms = mark(0)) return ms;
     rts::QAdjParams QP;
@@ -1381,8 +1381,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
 
     if (has_x) {
         dim3 tb(32, 8), tg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)(g->nz * B));
-        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (T *)(base + o_chiT), g->nx, g->ny, g->nz);
-        rts::transpose_x_kernel<T><<<tg, tb, 0, st>>>((const T *)S, (T *)(base + o_ST), g->nx, g->ny, g->nz);
+        rts::transpose_x2_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (const T *)S, (T *)(base + o_chiT),
+                                                      (T *)(base + o_ST), g->nx, g->ny, g->nz);
         NA_TRY(cudaGetLastError());
     }
     rts::SweepArgs<T> a;
@@ -1742,12 +1742,11 @@ static rts_status solve_batched_impl(rts_handle *h, const void *chi, const void 
     }
     int kernels = 0;
     if (h->has_x) {
-        rts::transpose_x_batched<T><<<(unsigned)h->nblk[0], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->B, (const T *)chi,
-                                                                                 (T *)h->d_chiT);
-        rts::transpose_x_batched<T><<<(unsigned)h->nblk[0], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->B, (const T *)S,
-                                                                                 (T *)h->d_ST);
+        rts::transpose_x2_batched<T><<<(unsigned)h->nblk[0], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->B, (const T *)chi,
+                                                                                  (const T *)S, (T *)h->d_chiT,
+                                                                                  (T *)h->d_ST);
         CUDA_TRY(h, cudaGetLastError());
-        kernels += 2;
+        kernels += 1;
     }
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[1], st));
     rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
