@@ -196,6 +196,14 @@ struct rts_handle {
     std::vector<int> unit_of_tile;
     int total_tiles = 0, max_ntiles = 0, R = 0, grid = 0, nt = 32, tq = 0, maxt = 0;  // maxt: register cap
     unsigned carveout = 100;      // forward sweep's shared-memory carveout (percent)
+    // batched: one forward launch per CTA-width class (units of plane
+    // extents that round up to the same number of warps), tiles contiguous
+    struct SweepClass {
+        int tile_base = 0, ntiles = 0, nt = 0, grid = 0;
+        size_t smem = 0;
+        unsigned carveout = 100;
+    };
+    std::vector<SweepClass> classes;
     unsigned adj_carveout = 100;  // reverse sweep's
     size_t smem = 0;
     // reverse sweep: the same units tiled for the adjoint kernel
@@ -445,6 +453,54 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool 
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// Batched forward sweep: one cooperative launch per CTA-width class (a single
+// class is the plain launch). Each class's CTA has as many threads as its
+// widest plane needs, so narrow subdomains leave no idle warps; the ticket is
+// cleared between the launches, flags and counters are per tile and unit.
+template <typename T>
+static cudaError_t launch_sweep_classes(rts_handle *h, const rts::SweepArgs<T> &a, int *launches)
+{
+    if (h->classes.size() <= 1) {
+        *launches = 1;
+        return launch_sweep<T>(h, a);
+    }
+    SweepFn<T> kern = fwd_kernel<T>(h->tq, h->maxt, false);
+    if (!kern) return cudaErrorInvalidValue;
+    *launches = 0;
+    for (size_t c = 0; c < h->classes.size(); ++c) {
+        const rts_handle::SweepClass &C = h->classes[c];
+        cudaError_t e;
+        if (c > 0 && (e = cudaMemsetAsync(h->d_ticket, 0, sizeof(int), h->stream)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C.smem)) != cudaSuccess)
+            return e;
+        rts::SweepArgs<T> ac = a;
+        ac.tile_base = C.tile_base;
+        ac.total_tiles = C.ntiles;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(std::min(C.grid, C.ntiles));
+        cfg.blockDim = dim3(C.nt);
+        cfg.dynamicSmemBytes = C.smem;
+        cfg.stream = h->stream;
+        cudaLaunchAttribute attr[2];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+        attr[1].val.sharedMemCarveout = C.carveout;
+        cfg.attrs = attr;
+        cfg.numAttrs = 2;
+        if ((e = cudaLaunchKernelEx(&cfg, kern, ac)) != cudaSuccess) return e;
+        ++*launches;
+    }
+    return cudaSuccess;
+}
+
+// occupancy of the forward kernel (tq, register cap) with nt threads and smem bytes
+static cudaError_t class_blocks(int esize, int tq, int maxt, int nt, size_t smem, int *blocks)
+{
+    return esize == 8 ? kernel_occupancy<double>(fwd_kernel<double>(tq, maxt, false), nt, smem, blocks)
+                      : kernel_occupancy<float>(fwd_kernel<float>(tq, maxt, false), nt, smem, blocks);
 }
 
 extern "C" {
@@ -1633,8 +1689,11 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     const int nunits = (int)plan.size();
     std::vector<int> order(nunits);
     for (int u = 0; u < nunits; ++u) order[u] = u;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return unit_weight(plan[a]) > unit_weight(plan[b]); });
+    auto warps_of = [&](int u) { return (plan[u].NP + 31) / 32; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (warps_of(a) != warps_of(b)) return warps_of(a) > warps_of(b);
+        return unit_weight(plan[a]) > unit_weight(plan[b]);
+    });
     std::vector<int> pos(nunits);
     h->units.resize(nunits);
     h->unit_of_tile.clear();
@@ -1659,6 +1718,31 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
 
     h->grid = std::min(h->total_tiles, tl.blocks * nsm);
     h->flag_tiles = 2 * h->total_tiles;  // a pair per tile
+    // CTA-width classes (units are ordered by class): each class gets a CTA of
+    // its own width, shared memory for its widest plane and its occupancy;
+    // every unit's tiles must still fit on the GPU at once within its class
+    for (int k = 0; k < nunits;) {
+        const int w = (h->units[k].NP + 31) / 32;
+        rts_handle::SweepClass C;
+        C.tile_base = h->units[k].tile0;
+        int npc = 0, maxnt = 0;
+        int k1 = k;
+        for (; k1 < nunits && (h->units[k1].NP + 31) / 32 == w; ++k1) {
+            npc = std::max(npc, h->units[k1].NP);
+            maxnt = std::max(maxnt, h->units[k1].ntiles);
+            C.ntiles += h->units[k1].ntiles;
+        }
+        C.nt = 32 * w;
+        C.smem = fwd_smem(tq, npc, (int)h->esize);
+        int blocks = 0;
+        if (class_blocks((int)h->esize, tq, h->maxt, C.nt, C.smem, &blocks) != cudaSuccess || blocks < 1 ||
+            (long long)blocks * nsm < maxnt)
+            return bail(fail(h, RTS_EINVAL, "no co-resident launch for the subdomains of plane width %d", npc));
+        C.grid = std::min(C.ntiles, blocks * nsm);
+        C.carveout = carveout_percent(blocks, C.smem);
+        h->classes.push_back(C);
+        k = k1;
+    }
 
     // ---- device memory ----
     const size_t es = h->esize;
@@ -1751,9 +1835,10 @@ static rts_status solve_batched_impl(rts_handle *h, const void *chi, const void 
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[1], st));
     rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
     a.itop = (T *)I_top;
-    cudaError_t e = launch_sweep<T>(h, a);
+    int launches = 0;
+    cudaError_t e = launch_sweep_classes<T>(h, a, &launches);
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
-    kernels += 1;
+    kernels += launches;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
     if (J || F || Q) {
         rts::reduce_units_batched<T, Acc><<<(unsigned)h->nblk[1], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->d_ru,
