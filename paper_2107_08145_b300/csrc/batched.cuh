@@ -45,19 +45,6 @@ __host__ __device__ inline long long sub_blocks(int which, int nx, int ny, int n
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) transpose_x_batched(const SubDesc *__restrict__ d, int nsub, int B,
-                                                           const T *__restrict__ in, T *__restrict__ out)
-{
-    const int s = find_sub(d, nsub, 0, blockIdx.x);
-    const SubDesc &sd = d[s];
-    const int r = blockIdx.x - sd.blk[0];
-    const int tx = (sd.nx + 31) / 32, ty = (sd.ny + 31) / 32;
-    const int bx = r % tx, by = (r / tx) % ty;
-    const long long bk = r / (tx * ty);
-    transpose_tile(in + sd.in_off, out + sd.in_off, sd.nx, sd.ny, sd.nz, bx * 32, by * 32, bk / sd.nz, bk % sd.nz);
-}
-
-template <typename T>
 __global__ void __launch_bounds__(256) transpose_x2_batched(const SubDesc *__restrict__ d, int nsub, int B,
                                                               const T *__restrict__ in0, const T *__restrict__ in1,
                                                               T *__restrict__ out0, T *__restrict__ out1)

@@ -11,18 +11,6 @@ namespace rts {
 // Device status bits (mapped to rts_status on the host).
 enum : int { ST_TIMEOUT = 1, ST_NOCONV = 2, ST_BADARG = 4 };
 
-__device__ __forceinline__ int ld_acquire(const int *p)
-{
-    int v;
-    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release(int *p, int v)
-{
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
 {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -33,11 +21,6 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void st_release64(unsigned long long *p, unsigned long long v)
-{
-    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_relaxed(const int *p)
@@ -54,23 +37,6 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-// Wait until *flag >= want. Returns false (and records why) if the device
-// status already carries an error or the time limit expires.
-__device__ __forceinline__ bool wait_flag_geq(const int *flag, int want, int *status, uint64_t limit_ns)
-{
-    if (ld_acquire(flag) >= want) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        __nanosleep(64);
-        if (ld_acquire(flag) >= want) return true;
-        if (ld_relaxed(status) != 0) return false;
-        if (global_ns() - t0 > limit_ns) {
-            atomicOr(status, ST_TIMEOUT);
-            return false;
-        }
-    }
-}
-
 __device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ void st_relaxed(int *p, int v)
@@ -79,7 +45,8 @@ __device__ __forceinline__ void st_relaxed(int *p, int v)
 }
 
 // Wait until pair[0] >= w0 and pair[1] >= w1 (8-byte aligned pair), both
-// read by one 8-byte acquire load per poll; limits as wait_flag_geq.
+// read by one 8-byte acquire load per poll. Returns false (and records why)
+// if the device status already carries an error or the time limit expires.
 __device__ __forceinline__ bool wait_pair_geq(const int *pair, int w0, int w1, int *status, uint64_t limit_ns)
 {
     const unsigned long long *p64 = reinterpret_cast<const unsigned long long *>(pair);
@@ -104,7 +71,7 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
     return v;
 }
 
-// Wait until *cnt >= want (same limits as wait_flag_geq).
+// Wait until *cnt >= want (same limits as wait_pair_geq).
 __device__ __forceinline__ bool wait_count_geq(const unsigned *cnt, unsigned want, int *status, uint64_t limit_ns)
 {
     if (ld_acquire_u32(cnt) >= want) return true;
