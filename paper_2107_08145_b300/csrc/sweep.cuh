@@ -240,7 +240,7 @@ __device__ __forceinline__ void ld4(const double *p, double &a, double &b, doubl
 }
 
 template <typename T>
-__device__ __forceinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U, const DirConst<T> &D, int d,
+__device__ __noinline__ T bc_value(const SweepArgs<T> &a, const SweepUnit &U, const DirConst<T> &D, int d,
                                      int p, int q, int m, T Sp)
 {
     const int kind = D.bck[d];
