@@ -176,6 +176,17 @@ struct AdjRow<T, true> {
     T A[MAXD];
 };
 
+// cotangent of the upward intensity of slot d leaving the top at (p, q) of
+// plane m (out of line: only the top row or plane takes it)
+template <typename T>
+__device__ __noinline__ T top_cotangent(const T *gitop, const DirConst<T> &D, int d, int axis, int p, int q, int m,
+                                        int unx, int uny)
+{
+    int i, j;
+    natural_ij(axis, p, q, m, i, j);
+    return gitop[((long long)D.udx[d] * uny + j) * unx + i];
+}
+
 template <typename T, int TQ>
 __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict__ Ug, int uidx, int r, int gt,
                              unsigned char *smem)
@@ -366,11 +377,7 @@ __device__ void run_tile_adj(const SweepArgs<T> &a, const SweepUnit *__restrict_
                 T lam = b0 * Ap[0] + b1 * Ap[4 * SP] + b2 * Ap[oq] + b3 * Ap[oq + 4 * SP];
                 lam += cw[0][d] * gJ + cw[1][d] * gFx + cw[2][d] * gFy + cw[3][d] * gFz;
                 const bool isup = (upm >> d) & 1;
-                if (gitop && top && isup && ((actm >> d) & 1)) {
-                    int i, j;
-                    natural_ij(axis, p, q, m, i, j);
-                    lam += gitop[((long long)D.udx[d] * uny + j) * unx + i];
-                }
+                if (gitop && top && isup && ((actm >> d) & 1)) lam += top_cotangent(gitop, D, d, axis, p, q, m, unx, uny);
                 if (!((actm >> d) & 1)) lam = T(0);
                 const bool set = wrap ? (isup ? q == 0 : q == NQ - 1) : bnd_plane;
                 T e = T(0), wu = T(0), wp = T(0);
