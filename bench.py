@@ -149,8 +149,11 @@ class ClockSampler:
 
     def summary(self):
         names = [n for b, n in self.REASONS.items() if self.reasons & b and n != "gpu_idle"]
-        return {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
-                "reasons": names, "samples": len(self.samples), "source": self.mode, "error": self.err}
+        out = {"sm_mhz": statistics.median(self.samples) if self.samples else None, "sm_max_mhz": self.max_mhz,
+               "reasons": names, "samples": len(self.samples), "source": self.mode}
+        if not self.samples:  # why the clocks are missing (an NVML miss with nvidia-smi samples is no error)
+            out["error"] = self.err
+        return out
 
 
 # ----------------------------------------------------------------------------
