@@ -1,0 +1,17 @@
+// adj_f64.cu -- instantiations of the reverse (adjoint) sweep kernel for double
+// (see adjoint.cuh); looked up by configuration through kernels.h.
+#include "adjoint.cuh"
+#include "kernels.h"
+
+namespace rts {
+
+SweepFn<double> adj_kernel_f64(int tq, int maxr)
+{
+#define RTS_CFG(A, B)                                                                                              \
+    if (tq == A && maxr == B) return sweep_adj_kernel<double, A, B>;
+    RTS_CFG(4, 72) RTS_CFG(2, 56) RTS_CFG(1, 56) RTS_CFG(4, 64) RTS_CFG(2, 64) RTS_CFG(1, 64)
+#undef RTS_CFG
+    return nullptr;
+}
+
+}  // namespace rts

@@ -26,6 +26,7 @@
 #include "batched.cuh"
 #include "qstep.cuh"
 #include "sweep.cuh"
+#include "kernels.h"
 
 namespace {
 
@@ -287,11 +288,13 @@ static rts_status fail(rts_handle *h, rts_status s, const char *fmt, ...)
     } while (0)
 
 template <typename T>
-using SweepFn = void (*)(rts::SweepArgs<T>);
+using SweepFn = rts::SweepFn<T>;
 
 // Forward sweep kernels instantiated: (rows per tile, register cap per thread).
 // The caps let 2 to 4 CTAs of up to 288 threads share an SM; the last three
-// serve CTAs of up to 1024 threads (plane extents above 384).
+// serve CTAs of up to 1024 threads (plane extents above 384). The kernels are
+// compiled in their own translation units (sweep_f32.cu, sweep_f64.cu,
+// adj_f32.cu, adj_f64.cu) and looked up here by configuration.
 struct FwdCfg {
     int tq, maxr;
 };
@@ -299,28 +302,29 @@ static const FwdCfg kFwdCfg[] = {{16, 168}, {12, 168}, {8, 112}, {7, 112}, {6, 1
                                  {4, 64}, {2, 64}, {1, 64}};
 static const int kNumFwdCfg = sizeof(kFwdCfg) / sizeof(kFwdCfg[0]);
 template <typename T>
-static SweepFn<T> fwd_kernel(int tq, int maxr, bool ckpt = false)
+static SweepFn<T> fwd_kernel(int tq, int maxr, bool ckpt = false);
+template <>
+SweepFn<float> fwd_kernel<float>(int tq, int maxr, bool ckpt)
 {
-#define RTS_CFG(A, B)                                                                                              \
-    if (tq == A && maxr == B) return ckpt ? nullptr : rts::sweep_kernel<T, A, B, false>;
-    RTS_CFG(16, 168) RTS_CFG(12, 168) RTS_CFG(8, 112) RTS_CFG(7, 112) RTS_CFG(6, 104)
-#undef RTS_CFG
-    // the small tiles also exist with the adjoint's checkpoint
-#define RTS_CFG(A, B)                                                                                              \
-    if (tq == A && maxr == B) return ckpt ? rts::sweep_kernel<T, A, B, true> : rts::sweep_kernel<T, A, B, false>;
-    RTS_CFG(4, 72) RTS_CFG(2, 56) RTS_CFG(1, 56) RTS_CFG(4, 64) RTS_CFG(2, 64) RTS_CFG(1, 64)
-#undef RTS_CFG
-    return nullptr;
+    return rts::fwd_kernel_f32(tq, maxr, ckpt);
+}
+template <>
+SweepFn<double> fwd_kernel<double>(int tq, int maxr, bool ckpt)
+{
+    return rts::fwd_kernel_f64(tq, maxr, ckpt);
 }
 
 template <typename T>
-static SweepFn<T> adj_kernel(int tq, int maxr)
+static SweepFn<T> adj_kernel(int tq, int maxr);
+template <>
+SweepFn<float> adj_kernel<float>(int tq, int maxr)
 {
-#define RTS_CFG(A, B)                                                                                              \
-    if (tq == A && maxr == B) return rts::sweep_adj_kernel<T, A, B>;
-    RTS_CFG(4, 72) RTS_CFG(2, 56) RTS_CFG(1, 56) RTS_CFG(4, 64) RTS_CFG(2, 64) RTS_CFG(1, 64)
-#undef RTS_CFG
-    return nullptr;
+    return rts::adj_kernel_f32(tq, maxr);
+}
+template <>
+SweepFn<double> adj_kernel<double>(int tq, int maxr)
+{
+    return rts::adj_kernel_f64(tq, maxr);
 }
 
 static size_t fwd_smem(int tq, int np, int esize)
