@@ -107,7 +107,18 @@ typedef struct {
                              and keeps at a time (the checkpoint unit;
                              0 = 1 band); larger chunks run more sweep units
                              at once and need proportionally more scratch */
+    int sweep_kernel;     /* forward sweep of the FP32 modes: RTS_SWEEP_AUTO (0),
+                             RTS_SWEEP_SHARED (1) or RTS_SWEEP_REGISTER (2) */
 } rts_options;
+
+enum {
+    RTS_SWEEP_AUTO = 0,     /* the register-resident sweep where it applies, else the shared one */
+    RTS_SWEEP_SHARED = 1,   /* tile rows and chi/S in shared memory, any grid and quadrature */
+    RTS_SWEEP_REGISTER = 2  /* two columns per thread in registers, packed FP32 arithmetic;
+                               needs FP32, even nx and ny, and one bilinear stencil
+                               per direction group (any 3-rays-per-octant set);
+                               rts_create fails with RTS_EINVAL otherwise */
+};
 
 typedef struct {
     int n_units;          /* sweep units of the last solve (band x direction group) */
@@ -129,6 +140,7 @@ typedef struct {
      * timed_adjoints calls */
     int timed_adjoints;
     float ms_adjoint[4];
+    int sweep_kernel;     /* forward sweep rts_solve runs: RTS_SWEEP_SHARED or RTS_SWEEP_REGISTER */
 } rts_stats;
 
 typedef struct {

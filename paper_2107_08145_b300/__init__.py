@@ -23,6 +23,8 @@ FLAG_HOST_IO_ASYNC = 8
 
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED, "fp32_compensated": FP32_COMPENSATED}
 _BC = {"zero": BC_ZERO, "equal_s": BC_EQUAL_S}
+SWEEP_AUTO, SWEEP_SHARED, SWEEP_REGISTER = 0, 1, 2
+_SWEEP = {"auto": SWEEP_AUTO, "shared": SWEEP_SHARED, "register": SWEEP_REGISTER}
 
 
 class Grid(C.Structure):
@@ -38,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("prec", C.c_int), ("tau_switch", C.c_double), ("wrap_tol", C.c_double),
                 ("max_wrap_iters", C.c_int), ("tile_rows", C.c_int), ("threads", C.c_int),
                 ("flags", C.c_int), ("timeout_s", C.c_double), ("stream", C.c_void_p),
-                ("adjoint_chunk_bands", C.c_int)]
+                ("adjoint_chunk_bands", C.c_int), ("sweep_kernel", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -46,7 +48,8 @@ class Stats(C.Structure):
                 ("mean_warmup_steps", C.c_double), ("device_status", C.c_int), ("grid", C.c_int),
                 ("tile_rows", C.c_int), ("kernels_per_solve", C.c_int), ("timed_solves", C.c_int),
                 ("ms_transpose", C.c_float), ("ms_sweep", C.c_float), ("ms_reduce", C.c_float),
-                ("ms_qstep", C.c_float), ("timed_adjoints", C.c_int), ("ms_adjoint", C.c_float * 4)]
+                ("ms_qstep", C.c_float), ("timed_adjoints", C.c_int), ("ms_adjoint", C.c_float * 4),
+                ("sweep_kernel", C.c_int)]
 
 
 class Boundary(C.Structure):
@@ -145,7 +148,7 @@ class Solver:
     def __init__(self, nx, ny, nz, nbands=1, dx=1.0, dy=1.0, dz=1.0, precision="fp64", n=None, w=None,
                  tau_switch=0.1, wrap_tol=0.0, max_wrap_iters=64, tile_rows=0, timeout_s=2.0,
                  host_io=False, timing=False, stream=None, adjoint=False, adjoint_chunk_bands=0,
-                 host_io_async=False):
+                 host_io_async=False, sweep_kernel="auto"):
         import torch
 
         L = load()
@@ -165,6 +168,7 @@ class Solver:
         o.flags = ((FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0) | (FLAG_ADJOINT if adjoint else 0)
                    | (FLAG_HOST_IO_ASYNC if host_io_async else 0))
         o.adjoint_chunk_bands = adjoint_chunk_bands
+        o.sweep_kernel = _SWEEP[sweep_kernel]
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

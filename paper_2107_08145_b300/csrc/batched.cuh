@@ -62,7 +62,8 @@ __global__ void __launch_bounds__(256) transpose_x2_batched(const SubDesc *__res
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) reduce_units_batched(const SubDesc *__restrict__ d, int nsub,
                                                             const RedUnit *__restrict__ ru,
-                                                            const int *__restrict__ ru_begin, Acc *__restrict__ JF)
+                                                            const int *__restrict__ ru_begin, Acc *__restrict__ JF,
+                                                            int raw)
 {
     const int s = find_sub(d, nsub, 1, blockIdx.x);
     const SubDesc &sd = d[s];
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256) reduce_units_batched(const SubDesc *__res
     const int bk = r / (tx * ty);
     const int b = bk / sd.nz, k = bk % sd.nz;
     reduce_tile<T, Acc>(ru, ru_begin[sd.ru0 + b], ru_begin[sd.ru0 + b + 1], JF + sd.jf_off + (long long)b * 4 * sd.N,
-                        sd.nx, sd.ny, sd.nz, bx * 32, by * 32, k);
+                        sd.nx, sd.ny, sd.nz, bx * 32, by * 32, k, raw != 0);
 }
 
 template <typename T, typename Acc>

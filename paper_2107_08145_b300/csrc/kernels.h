@@ -14,6 +14,8 @@ using SweepFn = void (*)(SweepArgs<T>);
 // forward sweep (ckpt: the instantiation that keeps the adjoint's checkpoint)
 SweepFn<float> fwd_kernel_f32(int tq, int maxr, bool ckpt);
 SweepFn<double> fwd_kernel_f64(int tq, int maxr, bool ckpt);
+// register-resident FP32 forward sweep (sweep_reg.cuh)
+SweepFn<float> reg_kernel_f32(int tq, int maxr);
 // reverse (adjoint) sweep
 SweepFn<float> adj_kernel_f32(int tq, int maxr);
 SweepFn<double> adj_kernel_f64(int tq, int maxr);

@@ -94,7 +94,40 @@ __global__ void __launch_bounds__(256) transpose_x_kernel(const T *__restrict__ 
 struct RedUnit {
     const void *partial;  // [N][4] in the unit's layout
     int axis;             // 0: transposed layout [i][k][j]; else natural
+    // raw partials (the slot intensities I_0..I_3 of a point, from
+    // sweep_reg_kernel): J = sum_d c[0][d] I_d and F_x, F_y, F_z with
+    // c[1..3][d] = 4 pi w_d n_d; qpair[c] selects the slot pairing of the
+    // exact differences (0: (0,1)+(2,3), 1: (0,2)+(1,3))
+    float c[4][4];
+    int qpair[4];
 };
+
+// a x + b y with one rounding relative to the result, however much the two
+// products cancel: p = b y rounded, b y - p exactly (FMA), a x + p rounded
+__device__ __forceinline__ float pair_sum(float a, float x, float b, float y)
+{
+    const float p = b * y;
+    return fmaf(a, x, p) + fmaf(b, y, -p);
+}
+
+// J, F_x, F_y, F_z of one point of one unit from its 4 slot intensities. The
+// flux components across the unit's dominant axis cancel between slots of
+// opposite sign; they are summed as two exact pair differences (the pairs of
+// slots that differ only in that component's sign), so their error is
+// relative to the component itself.
+__device__ __forceinline__ void unit_moments(const RedUnit &u, const float (&I)[4], float (&v)[4])
+{
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float *k = u.c[c];
+        v[c] = u.qpair[c] ? pair_sum(k[0], I[0], k[2], I[2]) + pair_sum(k[1], I[1], k[3], I[3])
+                          : pair_sum(k[0], I[0], k[1], I[1]) + pair_sum(k[2], I[2], k[3], I[3]);
+    }
+}
+__device__ __forceinline__ void unit_moments(const RedUnit &, const double (&I)[4], double (&v)[4])
+{
+    for (int c = 0; c < 4; ++c) v[c] = I[c];  // FP64 partials are never raw
+}
 
 // Sums of sweep-unit partials. FP32 partials are summed in double-float
 // arithmetic (error-free TwoSum), which for a handful of terms is exact to
@@ -142,7 +175,7 @@ __device__ __forceinline__ void ld_part(const double *p, double (&v)[4])
 // one band, into JFb = JF of that band ([4][N])
 template <typename T, typename Acc>
 __device__ __forceinline__ void reduce_tile(const RedUnit *__restrict__ ru, int u0, int u1, Acc *__restrict__ JFb,
-                                            int nx, int ny, int nz, int i0, int j0, int k)
+                                            int nx, int ny, int nz, int i0, int j0, int k, bool raw)
 {
     __shared__ PartSum<T> tile[4][32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -160,6 +193,10 @@ __device__ __forceinline__ void reduce_tile(const RedUnit *__restrict__ ru, int 
             const long long off = ((long long)i * nz + k) * ny + j;
             T v[4];
             ld_part(pt + off * 4, v);
+            if (raw) {
+                T I[4] = {v[0], v[1], v[2], v[3]};
+                unit_moments(ru[u], I, v);
+            }
             for (int c = 0; c < 4; ++c) tile[c][ii][tx].add(v[c]);
         }
     }
@@ -175,6 +212,10 @@ __device__ __forceinline__ void reduce_tile(const RedUnit *__restrict__ ru, int 
             const T *pn = (const T *)ru[u].partial;
             T v[4];
             ld_part(pn + noff * 4, v);
+            if (raw) {
+                T I[4] = {v[0], v[1], v[2], v[3]};
+                unit_moments(ru[u], I, v);
+            }
             for (int c = 0; c < 4; ++c) s[c].add(v[c]);
         }
         for (int c = 0; c < 4; ++c) JFb[c * N + noff] = part_out(s[c], (Acc *)nullptr);
@@ -184,12 +225,12 @@ __device__ __forceinline__ void reduce_tile(const RedUnit *__restrict__ ru, int 
 template <typename T, typename Acc>
 __global__ void __launch_bounds__(256) reduce_units_kernel(const RedUnit *__restrict__ ru,
                                                             const int *__restrict__ ru_begin,
-                                                            Acc *__restrict__ JF, int nx, int ny, int nz)
+                                                            Acc *__restrict__ JF, int nx, int ny, int nz, int raw)
 {
     const int b = blockIdx.z / nz, k = blockIdx.z % nz;
     const long long N = (long long)nx * ny * nz;
     reduce_tile<T, Acc>(ru, ru_begin[b], ru_begin[b + 1], JF + (long long)b * 4 * N, nx, ny, nz, blockIdx.x * 32,
-                        blockIdx.y * 32, k);
+                        blockIdx.y * 32, k, raw != 0);
 }
 
 struct QParams {

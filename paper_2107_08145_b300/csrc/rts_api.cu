@@ -27,6 +27,7 @@
 #include "qstep.cuh"
 #include "sweep.cuh"
 #include "kernels.h"
+#include "sweep_reg.cuh"
 
 namespace {
 
@@ -175,7 +176,9 @@ bool plan_units(const DirGeo *geo, const int *udx, const double *n, const double
                 for (int t = 0; t < U.ntiles; ++t) unit_of_tile[po.ntiles + t] = po.nunits;
                 po.ntiles += U.ntiles;
                 po.max_ntiles = std::max(po.max_ntiles, U.ntiles);
-                po.halo_elems += (long long)U.ntiles * 4 * rts::HALO_CH * U.NP;
+                // per tile: the shared-memory sweep's ring (4 x HALO_CH x NP) or the
+                // register sweep's tagged ring, whichever is larger
+                po.halo_elems += (long long)U.ntiles * std::max<long long>(4 * rts::HALO_CH * U.NP, rts::reg_ring_elems(U.NP));
                 ++po.nunits;
             }
         }
@@ -213,7 +216,16 @@ struct rts_handle {
     rts::SweepUnit *d_adj_units = nullptr;
     int *d_adj_uot = nullptr;
     int adj_tq = 0, adj_maxr = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
-    int flag_tiles = 0;           // ready flags allocated (a pair per tile, max over both tilings)
+    // register-resident FP32 forward sweep (sweep_reg.cuh): its own tiling of the same units
+    bool use_reg = false;
+    std::vector<rts::SweepUnit> reg_units;
+    std::vector<int> reg_unit_of_tile;
+    rts::SweepUnit *d_reg_units = nullptr;
+    int *d_reg_uot = nullptr;
+    int reg_tq = 0, reg_maxr = 0, reg_total_tiles = 0, reg_grid = 0, reg_nt = 32;
+    size_t reg_smem = 0;
+    unsigned reg_carveout = 100;
+    int flag_tiles = 0;           // ready flags allocated (a pair per tile, max over all tilings)
     size_t adj_smem = 0;
     bool has_x = false;
     long long N = 0;
@@ -436,6 +448,85 @@ static Tiling choose_adj(int npmax, int nqmax, int nsm)
     return best;
 }
 
+// reduction table entry of a unit: its partial array, layout and the per-slot
+// coefficients of J and F (used when the partials are raw slot intensities)
+static rts::RedUnit red_unit(const rts::SweepUnit &U)
+{
+    rts::RedUnit r;
+    std::memset(&r, 0, sizeof(r));
+    r.partial = U.partial;
+    r.axis = U.axis;
+    for (int d = 0; d < rts::MAXD; ++d) {
+        if (!U.active[d]) continue;
+        r.c[0][d] = (float)U.cJ[d];
+        for (int c = 0; c < 3; ++c) r.c[1 + c][d] = (float)U.cF[c][d];
+    }
+    // the flux component along the unit's Q axis pairs the slots that differ in sQ
+    const int b2 = U.axis == 2 ? 1 : 2;
+    r.qpair[1 + b2] = 1;
+    return r;
+}
+
+// The register-resident sweep serves a grid when every unit's active slots
+// share one stencil (path length and bilinear weights), every plane extent is
+// even and at most 2048, and (for the row tiles of the periodic z groups) the
+// tile height divides ny.
+static bool reg_eligible(const std::vector<rts::SweepUnit> &units)
+{
+    for (const rts::SweepUnit &U : units) {
+        if (U.NP % 2 != 0 || U.NP > 2048 || U.NM < 2) return false;
+        int f = -1;
+        for (int d = 0; d < rts::MAXD; ++d) {
+            if (!U.active[d]) continue;
+            if (f < 0) { f = d; continue; }
+            if (U.ds[d] != U.ds[f]) return false;
+            for (int c = 0; c < 4; ++c)
+                if (U.beta[d][c] != U.beta[f][c]) return false;
+        }
+    }
+    return true;
+}
+
+struct RegCfg {
+    int tq, maxr;
+};
+// (rows, register cap): measured at 288^3 x 4 bands, 4 rows at 128 registers
+// (3 CTAs of 160 threads per SM) is the fastest
+static const RegCfg kRegCfg[] = {{8, 255}, {4, 168}, {4, 128}, {2, 128}, {2, 96}};
+
+// Tiling of the register-resident sweep: among the instantiated (rows,
+// register cap) pairs whose tile height divides the periodic rows (nq_per),
+// whose CTA fits and whose units' tiles all fit on the GPU at once, the one
+// with the most plane rows resident per SM (requested > 0: the tallest not
+// above it).
+static Tiling choose_reg(int requested, int npmax, int nqmax, int nq_per, int nsm)
+{
+    Tiling best;
+    best.nt = 32 * ((npmax / 2 + 31) / 32);
+    double best_score = -1;
+    for (const RegCfg &c : kRegCfg) {
+        if (requested > 0 && c.tq > requested) continue;
+        if (nq_per % c.tq != 0) continue;
+        if ((long long)c.maxr * best.nt > 65536) continue;
+        const size_t smem = rts::reg_tile_smem_bytes(c.tq, npmax);
+        if (smem > 200 * 1024) continue;
+        rts::SweepFn<float> k = rts::reg_kernel_f32(c.tq, c.maxr);
+        int blocks = 0;
+        if (!k || kernel_occupancy<float>(k, best.nt, smem, &blocks) != cudaSuccess || blocks < 1) continue;
+        if ((long long)blocks * nsm < (nqmax + c.tq - 1) / c.tq) continue;
+        double score = (double)c.tq * blocks;
+        if (requested > 0) score = c.tq + 1e-3 * blocks;
+        if (score > best_score) {
+            best_score = score;
+            best.tq = c.tq;
+            best.maxt = c.maxr;
+            best.blocks = blocks;
+            best.smem = smem;
+        }
+    }
+    return best;
+}
+
 template <typename T>
 static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool reverse = false)
 {
@@ -454,6 +545,32 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool 
     attr[0].val.cooperative = 1;
     attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
     attr[1].val.sharedMemCarveout = reverse ? h->adj_carveout : h->carveout;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+// the register-resident FP32 forward sweep over all units (its own tiling)
+static cudaError_t launch_reg_sweep(rts_handle *h, rts::SweepArgs<float> a)
+{
+    rts::SweepFn<float> kern = rts::reg_kernel_f32(h->reg_tq, h->reg_maxr);
+    if (!kern) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->reg_smem);
+    if (e != cudaSuccess) return e;
+    a.units = h->d_reg_units;
+    a.unit_of_tile = h->d_reg_uot;
+    a.tile_base = 0;
+    a.total_tiles = h->reg_total_tiles;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::min(h->reg_grid, a.total_tiles));
+    cfg.blockDim = dim3(h->reg_nt);
+    cfg.dynamicSmemBytes = h->reg_smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[1].val.sharedMemCarveout = h->reg_carveout;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, a);
@@ -677,6 +794,42 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         flag_tiles = std::max(flag_tiles, 2 * pa.ntiles);
         max_nt = std::max(max_nt, pa.max_ntiles);
     }
+    // register-resident forward sweep (FP32): its own tiling of the same units
+    if (o.sweep_kernel < RTS_SWEEP_AUTO || o.sweep_kernel > RTS_SWEEP_REGISTER)
+        return bail(fail(h, RTS_EINVAL, "unknown sweep_kernel %d", o.sweep_kernel));
+    if (o.prec == RTS_FP64 && o.sweep_kernel == RTS_SWEEP_REGISTER)
+        return bail(fail(h, RTS_EINVAL, "the register sweep is FP32 only"));
+    if (o.prec != RTS_FP64 && o.sweep_kernel != RTS_SWEEP_SHARED) {
+        const bool elig = reg_eligible(h->units);
+        Tiling tr;
+        if (elig) tr = choose_reg(o.tile_rows, npmax, nqmax, (int)ny, nsm);
+        if (tr.tq >= 1) {
+            h->reg_units.resize(max_units);
+            h->reg_unit_of_tile.resize(max_tiles);
+            PlanOut pr;
+            if (!plan_units(geo.data(), udx.data(), h->n.data(), h->w.data(), h->ndir, nx, ny, nz, nbands, tr.tq,
+                            h->reg_units.data(), max_units, h->reg_unit_of_tile.data(), (int)max_tiles, pr) ||
+                pr.nunits != po.nunits)
+                return bail(fail(h, RTS_EINVAL, "too many register-sweep tiles"));
+            h->reg_units.resize(pr.nunits);
+            h->reg_unit_of_tile.resize(pr.ntiles);
+            h->reg_total_tiles = pr.ntiles;
+            h->reg_tq = tr.tq;
+            h->reg_maxr = tr.maxt;
+            h->reg_nt = tr.nt;
+            h->reg_smem = tr.smem;
+            h->reg_carveout = carveout_percent(tr.blocks, tr.smem);
+            h->reg_grid = std::min(pr.ntiles, tr.blocks * nsm);
+            halo_elems = std::max(halo_elems, pr.halo_elems);
+            flag_tiles = std::max(flag_tiles, 2 * pr.ntiles);
+            max_nt = std::max(max_nt, pr.max_ntiles);
+            h->use_reg = true;
+        } else if (o.sweep_kernel == RTS_SWEEP_REGISTER) {
+            return bail(fail(h, RTS_EINVAL,
+                             elig ? "no register-sweep tile fits this grid (the tile height must divide ny)"
+                                  : "the register sweep needs even nx, ny and one stencil per direction group"));
+        }
+    }
     h->flag_tiles = flag_tiles;
     int R = 8;
     while (R < 2 * (max_nt + kLag + 2)) R *= 2;
@@ -702,6 +855,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_tacc = take(sizeof(int) * h->units.size());
     const size_t o_ru = take(sizeof(rts::RedUnit) * h->units.size());
     const size_t o_rub = take(sizeof(int) * (nbands + 1));
+    const size_t o_regu = h->use_reg ? take(sizeof(rts::SweepUnit) * h->reg_units.size()) : 0;
+    const size_t o_reguot = h->use_reg ? take(sizeof(int) * h->reg_unit_of_tile.size()) : 0;
     size_t o_adj[9] = {0};
     if (adjoint) {
         o_adj[7] = take(sizeof(rts::SweepUnit) * h->adj_units.size());
@@ -756,6 +911,10 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->d_unit_tacc = (int *)(base + o_tacc);
     h->d_ru = (rts::RedUnit *)(base + o_ru);
     h->d_ru_begin = (int *)(base + o_rub);
+    if (h->use_reg) {
+        h->d_reg_units = (rts::SweepUnit *)(base + o_regu);
+        h->d_reg_uot = (int *)(base + o_reguot);
+    }
     if (adjoint) {
         h->d_adj_units = (rts::SweepUnit *)(base + o_adj[7]);
         h->d_adj_uot = (int *)(base + o_adj[8]);
@@ -790,8 +949,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     std::vector<int> rub(nbands + 1, 0);
     for (size_t u = 0; u < h->units.size(); ++u) {
         h->units[u].partial = (char *)h->d_partial + u * 4 * h->N * es;
-        ru[u].partial = h->units[u].partial;
-        ru[u].axis = h->units[u].axis;
+        ru[u] = red_unit(h->units[u]);
         rub[h->units[u].band + 1]++;
     }
     for (int b = 0; b < nbands; ++b) rub[b + 1] += rub[b];
@@ -799,6 +957,13 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     CUDA_TRY(h, cudaMemcpy(h->d_unit_of_tile, h->unit_of_tile.data(), sizeof(int) * h->unit_of_tile.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * ru.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, rub.data(), sizeof(int) * rub.size(), cudaMemcpyHostToDevice));
+    if (h->use_reg) {
+        for (size_t u = 0; u < h->reg_units.size(); ++u) h->reg_units[u].partial = h->units[u].partial;
+        CUDA_TRY(h, cudaMemcpy(h->d_reg_units, h->reg_units.data(), sizeof(rts::SweepUnit) * h->reg_units.size(),
+                               cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(h->d_reg_uot, h->reg_unit_of_tile.data(), sizeof(int) * h->reg_unit_of_tile.size(),
+                               cudaMemcpyHostToDevice));
+    }
     if (adjoint) {
         for (size_t u = 0; u < h->adj_units.size(); ++u) h->adj_units[u].partial = h->units[u].partial;
         CUDA_TRY(h, cudaMemcpy(h->d_adj_units, h->adj_units.data(), sizeof(rts::SweepUnit) * h->adj_units.size(),
@@ -806,6 +971,9 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         CUDA_TRY(h, cudaMemcpy(h->d_adj_uot, h->adj_unit_of_tile.data(), sizeof(int) * h->adj_unit_of_tile.size(),
                                cudaMemcpyHostToDevice));
     }
+    // a status word and warm-up record that read as "nothing ran yet"
+    CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(int) * 4));
+    CUDA_TRY(h, cudaMemset(h->d_unit_tacc, 0, sizeof(int) * h->units.size()));
     h->timing = (o.flags & RTS_FLAG_TIMING) != 0;
     *out = h;
     return RTS_OK;
@@ -866,7 +1034,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     cudaStream_t st = h->stream;
     CUDA_TRY(h, cudaMemsetAsync(h->d_status, 0, sizeof(int) * 4, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * 2 * h->total_tiles, st));
+    const bool reg = h->use_reg && sizeof(T) == 4;
+    CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * 2 * (reg ? h->reg_total_tiles : h->total_tiles), st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
@@ -891,7 +1060,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[1], st));
     rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
     a.itop = (T *)I_top;
-    cudaError_t e = launch_sweep<T>(h, a);
+    cudaError_t e = reg ? launch_reg_sweep(h, *reinterpret_cast<const rts::SweepArgs<float> *>(&a))
+                        : launch_sweep<T>(h, a);
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     kernels += 1;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
@@ -902,7 +1072,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
         P.inv2dx = 0.5 / g.dx; P.inv2dy = 0.5 / g.dy; P.inv2dz = 0.5 / g.dz; P.invdz = 1.0 / g.dz;
         P.thin = std::min(g.dx, std::min(g.dy, g.dz)) / h->opt.tau_switch;
         dim3 rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
-        rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz);
+        rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz,
+                                                           reg ? 1 : 0);
         if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
         dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
         rts::qstep_kernel<T, Acc><<<qg, rb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, P, J, F, Q);
@@ -995,7 +1166,7 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
             const dim3 rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * nbc));
             rts::reduce_units_kernel<T, Acc><<<rg, tb, 0, st>>>(h->d_ru, h->d_ru_begin + b0,
                                                                (Acc *)h->d_JF + (long long)b0 * 4 * N, g.nx, g.ny,
-                                                               g.nz);
+                                                               g.nz, 0);
             CUDA_TRY(h, cudaGetLastError());
             kernels += 1;
         }
@@ -1208,7 +1379,7 @@ rts_status rts_get_stats(rts_handle *h, rts_stats *out)
     if (!h || !h->dmem || !out) return RTS_EINVAL;
     std::memset(out, 0, sizeof(*out));
     out->n_units = (int)h->units.size();
-    out->n_tiles = h->total_tiles;
+    out->n_tiles = h->use_reg ? h->reg_total_tiles : h->total_tiles;
     rts_status s = rts_check(h);
     out->device_status = s;
     std::vector<int> tacc(h->units.size());
@@ -1222,8 +1393,9 @@ rts_status rts_get_stats(rts_handle *h, rts_stats *out)
         ++nw;
     }
     out->mean_warmup_steps = nw ? sum / nw : 0.0;
-    out->grid = h->grid;
-    out->tile_rows = h->tq;
+    out->sweep_kernel = h->use_reg ? RTS_SWEEP_REGISTER : RTS_SWEEP_SHARED;
+    out->grid = h->use_reg ? h->reg_grid : h->grid;
+    out->tile_rows = h->use_reg ? h->reg_tq : h->tq;
     out->kernels_per_solve = h->kernels_last;
     if (h->timing && h->nrec > 0) {
         double acc[4] = {0, 0, 0, 0};
@@ -1405,8 +1577,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     }
     for (int u = 0; u < nunits; ++u) {
         units[u].partial = base + o_part + (size_t)u * 4 * N * es;
-        ru[u].partial = units[u].partial;
-        ru[u].axis = units[u].axis;
+        ru[u] = red_unit(units[u]);
     }
 
     // residency of the persistent launch
@@ -1488,7 +1659,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
         dim3 rb(32, 8), rg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)(g->nz * B));
         rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>((const rts::RedUnit *)(base + o_ru),
                                                              (const int *)(base + o_rub), (Acc *)(base + o_JF),
-                                                             g->nx, g->ny, g->nz);
+                                                             g->nx, g->ny, g->nz, 0);
         rts::QParams P;
         P.nx = g->nx; P.ny = g->ny; P.nz = g->nz; P.nbands = B;
         P.inv2dx = 0.5 / g->dx; P.inv2dy = 0.5 / g->dy; P.inv2dz = 0.5 / g->dz; P.invdz = 1.0 / g->dz;
@@ -1793,8 +1964,7 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     std::vector<rts::RedUnit> ru(nunits);
     for (int k = 0; k < nunits; ++k) h->units[k].partial = (char *)h->d_partial + part_off[k] * es;
     for (int u = 0; u < nunits; ++u) {  // reduction table in plan order: (subdomain, band), then group
-        ru[u].partial = h->units[pos[u]].partial;
-        ru[u].axis = plan[u].axis;
+        ru[u] = red_unit(h->units[pos[u]]);
     }
     CUDA_TRY(h, cudaMemcpy(h->d_units, h->units.data(), sizeof(rts::SweepUnit) * nunits, cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_unit_of_tile, h->unit_of_tile.data(), sizeof(int) * h->unit_of_tile.size(),
@@ -1803,6 +1973,8 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, ru_begin.data(), sizeof(int) * ru_begin.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_subs, h->subs.data(), sizeof(rts::SubDesc) * nsub, cudaMemcpyHostToDevice));
     h->band_unit.assign(1, 0);
+    CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(int) * 4));
+    CUDA_TRY(h, cudaMemset(h->d_unit_tacc, 0, sizeof(int) * nunits));
     h->timing = (o.flags & RTS_FLAG_TIMING) != 0;
     *out = h;
     return RTS_OK;
@@ -1846,7 +2018,7 @@ static rts_status solve_batched_impl(rts_handle *h, const void *chi, const void 
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
     if (J || F || Q) {
         rts::reduce_units_batched<T, Acc><<<(unsigned)h->nblk[1], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->d_ru,
-                                                                                       h->d_ru_begin, (Acc *)h->d_JF);
+                                                                                       h->d_ru_begin, (Acc *)h->d_JF, 0);
         if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
         rts::qstep_batched<T, Acc><<<(unsigned)h->nblk[2], dim3(32, 8), 0, st>>>(
             h->d_subs, ns, (const Acc *)h->d_JF, (const T *)chi, (const T *)S, J, F, Q);

@@ -44,11 +44,13 @@ def _batched(rts, shapes, B, chis, Ss, precision, **kw):
 
 
 def _singles(rts, shapes, B, chis, Ss, precision, tile_rows=0):
+    """rts_solve on each grid with the sweep the batched handle runs (the
+    shared-memory tile sweep), so the results must be bit-identical."""
     import torch
 
     res = []
     for (nx, ny, nz), c, s in zip(shapes, chis, Ss):
-        so = rts.Solver(nx, ny, nz, B, precision=precision, tile_rows=tile_rows)
+        so = rts.Solver(nx, ny, nz, B, precision=precision, tile_rows=tile_rows, sweep_kernel="shared")
         o = so.solve(torch.as_tensor(c, dtype=so.dtype, device="cuda"), torch.as_tensor(s, dtype=so.dtype, device="cuda"))
         res.append({k: v.cpu().numpy() for k, v in o.items()})
     return res
