@@ -54,7 +54,8 @@ typedef enum {
     RTS_ECUDA = 3,       /* a CUDA runtime call failed */
     RTS_ETIMEOUT = 4,    /* a device-side wait gave up (no hang) */
     RTS_ENOCONV = 5,     /* the periodic wrap did not converge within the cap */
-    RTS_ENONFINITE = 6   /* reserved: non-finite input detected */
+    RTS_ENONFINITE = 6   /* a NaN or an infinity in chi or S (found on the device
+                            while the solve runs; reported by rts_check) */
 } rts_status;
 
 typedef enum {
@@ -87,8 +88,14 @@ enum {
                              reports their mean over the solves since the
                              previous rts_get_stats call */
     RTS_FLAG_ADJOINT = 4, /* allocate the scratch of rts_adjoint */
-    RTS_FLAG_HOST_IO_ASYNC = 8 /* two staging sets and two copy streams for
+    RTS_FLAG_HOST_IO_ASYNC = 8, /* two staging sets and two copy streams for
                              rts_solve_host_async */
+    RTS_FLAG_LOG_CHI = 16 /* the chi argument of rts_solve, rts_adjoint and
+                             rts_graph_create is log chi: the library forms
+                             chi = exp(log chi) in a scratch array of B x N
+                             elements first (one more kernel); the gradient
+                             rts_adjoint returns is the one w.r.t. log chi as
+                             always. Not accepted by batched handles. */
 };
 
 typedef struct {
@@ -190,8 +197,13 @@ rts_status rts_solve_host_async(rts_handle *h, const void *chi, const void *S, c
 rts_status rts_host_wait(rts_handle *h);
 
 /* Wait for the handle's stream and return the device status of the last
- * solve (RTS_OK, RTS_ETIMEOUT, RTS_ENOCONV). */
+ * solve (RTS_OK, RTS_ETIMEOUT, RTS_ENOCONV, RTS_ENONFINITE). */
 rts_status rts_check(rts_handle *h);
+
+/* The compute capability the library's device code was built for, as
+ * major * 10 + minor (103 for sm_103a), read from the loaded kernel image on
+ * the current device; -1 if it cannot be read (no device). */
+int rts_device_code_version(void);
 
 /* Statistics of the last solve and, with RTS_FLAG_TIMING, mean phase times
  * of the solves since the previous call (synchronises the stream). */
@@ -286,25 +298,32 @@ rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, const rts_q
 /* ---------------------------------------------------------------------------
  * Forward solve without any memory allocation. The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
- * code that runs while an enclosing application is capturing a CUDA graph,
- * or an embedding code that hands the solver a fixed memory budget and does
- * not allow cudaMalloc outside its own pool. It runs the same kernels as
- * rts_solve on the same inputs and outputs (caller-owned device pointers,
- * layouts as above), with the default quadrature, bottom I = S, top I = 0 and
- * default options, and takes all its scratch from one static device array of
- * RTS_NOALLOC_SCRATCH_BYTES that the CUDA runtime sets up when the library is
- * loaded on a GPU (every GPU that loads the library keeps it until exit).
+ * an embedding code (for example an MHD code that owns the GPU's memory and
+ * hands the solver a fixed budget) that does not allow cudaMalloc outside its
+ * own pool, or a process whose allocator is already at its limit. It runs
+ * the same kernels as rts_solve on the same inputs and outputs (caller-owned
+ * device pointers, layouts as above), with the default quadrature, bottom
+ * I = S, top I = 0 and default options, and takes all its scratch from one
+ * static device array of RTS_NOALLOC_SCRATCH_BYTES that the CUDA runtime sets
+ * up when the library is loaded on a GPU (every GPU that loads the library
+ * keeps it until exit).
  *  - It calls no cudaMalloc/cudaFree and allocates no host memory.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture of your own.
- *  - Problems whose scratch would not fit (about 64^3 x 2 bands in FP32) are
- *    rejected with RTS_EINVAL and a message in err.
+ *    (cudaGetSymbolAddress) with that device current and keeps it for the
+ *    process. After a cudaDeviceReset that address is stale: do not call this
+ *    function again in a process that reset its device.
+ *  - The call waits for its stream (it reads back the device status), so it
+ *    cannot run inside a stream capture: on a capturing stream it returns
+ *    RTS_EINVAL without touching the capture.
+ *  - Problems whose scratch would not fit are rejected with RTS_EINVAL and a
+ *    message in err. The scratch of one FP32 band is about 36 bytes per
+ *    grid point (its 6 sweep units' partial sums, the band's J and F and the
+ *    transposed copies), so 64^3 x 1 band fits and 64^3 x 2 bands do not.
  *  - All calls share the one array and it keeps the previous call's contents;
  *    the control words are cleared on every call. Calls that overlap on the
  *    GPU (other streams, other host threads) race: serialise them.
- *  - The call waits for its stream and returns the device status (RTS_OK,
- *    RTS_ETIMEOUT, RTS_ENOCONV). err (may be NULL) receives a text.
+ *  - Returns the device status (RTS_OK, RTS_ETIMEOUT, RTS_ENOCONV,
+ *    RTS_ENONFINITE). err (may be NULL) receives a text.
  *  - nbands <= 16; nx, ny <= 1024. */
 #define RTS_NOALLOC_SCRATCH_BYTES (64u << 20)
 rts_status rts_solve_noalloc(const rts_grid *g, int nbands, rts_precision prec,

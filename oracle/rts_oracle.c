@@ -14,7 +14,11 @@
  *                          paper iterates boundary intensities (Sect. 2, 5.1)
  *   orc_solve              flux(): J and F over directions, then Q_rad
  *   orc_adjoint            reverse-mode derivative of orc_solve
- * Readings of the paper where it is silent are listed in the design doc.
+ * Where the paper gives no formula, the reading taken is stated at the
+ * function that takes it (quadrature values, dominant axis and ties, set
+ * boundary layers, linear chi interpolation, trapezoidal dtau, the periodic
+ * wrap's seed and tolerance, the one-sided divergence at the bottom and top,
+ * the thin/thick blend).
  */
 #include "rts_oracle.h"
 

@@ -10,8 +10,9 @@
  * short characteristics (Kunasz & Auer) on a 3-D Cartesian grid, 3 rays per
  * octant (24 directions, Carlson quadrature), one solve per opacity band,
  * boundary intensities iterated to a tolerance, then mean intensity J, flux F
- * and radiative heating Q_rad. The formal-solution formula, interpolation,
- * boundary handling and the Q_rad blend are the readings listed in the design doc.
+ * and radiative heating Q_rad. The paper gives no formulas: the formal
+ * solution, the interpolation, the boundary handling and the Q_rad blend
+ * below are readings of it, each stated where it is used.
  *
  * Layouts (C order, x fastest): grid arrays [B][Nz][Ny][Nx]; F [3][Nz][Ny][Nx];
  * I_top [B][n_up][Ny][Nx] (up directions in direction-table order);

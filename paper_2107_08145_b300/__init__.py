@@ -20,6 +20,7 @@ FLAG_HOST_IO = 1
 FLAG_TIMING = 2
 FLAG_ADJOINT = 4
 FLAG_HOST_IO_ASYNC = 8
+FLAG_LOG_CHI = 16
 
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED, "fp32_compensated": FP32_COMPENSATED}
 _BC = {"zero": BC_ZERO, "equal_s": BC_EQUAL_S}
@@ -62,7 +63,7 @@ _lib = None
 EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "rts_check",
            "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint",
            "rts_create_batched", "rts_solve_batched", "rts_batched_layout", "rts_graph_create", "rts_graph_launch",
-           "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait")
+           "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait", "rts_device_code_version")
 
 
 def library_path() -> str:
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = True):
     L.rts_last_error.restype = C.c_char_p
     L.rts_num_up.argtypes = [vp]
     L.rts_num_up.restype = C.c_int
+    L.rts_device_code_version.argtypes = []
+    L.rts_device_code_version.restype = C.c_int
     L.rts_destroy.argtypes = [vp]
     L.rts_destroy.restype = None
     L.rts_solve_noalloc.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp,
@@ -148,7 +151,7 @@ class Solver:
     def __init__(self, nx, ny, nz, nbands=1, dx=1.0, dy=1.0, dz=1.0, precision="fp64", n=None, w=None,
                  tau_switch=0.1, wrap_tol=0.0, max_wrap_iters=64, tile_rows=0, timeout_s=2.0,
                  host_io=False, timing=False, stream=None, adjoint=False, adjoint_chunk_bands=0,
-                 host_io_async=False, sweep_kernel="auto"):
+                 host_io_async=False, sweep_kernel="auto", log_chi=False):
         import torch
 
         L = load()
@@ -166,7 +169,8 @@ class Solver:
         o.tile_rows = tile_rows
         o.timeout_s = timeout_s
         o.flags = ((FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0) | (FLAG_ADJOINT if adjoint else 0)
-                   | (FLAG_HOST_IO_ASYNC if host_io_async else 0))
+                   | (FLAG_HOST_IO_ASYNC if host_io_async else 0) | (FLAG_LOG_CHI if log_chi else 0))
+        self.log_chi = log_chi
         o.adjoint_chunk_bands = adjoint_chunk_bands
         o.sweep_kernel = _SWEEP[sweep_kernel]
         if stream is None:
@@ -493,31 +497,48 @@ def autotune(shapes, nbands, chi, S, precision="fp32", spacing=None, repeats=3, 
 def solve_noalloc(chi, S, precision="fp32", dx=1.0, dy=1.0, dz=1.0, out=None, stream=None):
     """Forward solve through rts_solve_noalloc: no device (or host) memory is
     allocated by the library; its scratch is a fixed static device array.
-    For callers that must not allocate (inside someone else's graph capture,
-    or under a fixed memory budget). Defaults only: S4 quadrature, bottom
-    I = S, top I = 0. Outputs must be given or are made here with torch.
-    Returns the outputs dict; raises RTSError (with the library's message)
-    on failure, e.g. when the grid is too large for the fixed array."""
+    For callers that must not allocate (an embedding code that owns the
+    GPU's memory and gives the solver a fixed budget). The call waits for its
+    stream, so it cannot run inside a stream capture. Defaults only: S4
+    quadrature, bottom I = S, top I = 0. Outputs may be given (checked for
+    shape, dtype and device) or are made here with torch. Returns the outputs
+    dict; raises RTSError (with the library's message) on failure, e.g. when
+    the grid is too large for the fixed array."""
     import torch
 
     L = load()
+    if chi.dim() != 4:
+        raise ValueError(f"chi must be [B, nz, ny, nx], got shape {tuple(chi.shape)}")
     B, nz, ny, nx = chi.shape
     prec = _PREC[precision]
     dt = torch.float64 if prec == FP64 else torch.float32
-    assert chi.dtype == dt and S.dtype == dt and chi.is_cuda and S.is_cuda
-    if out is None:
-        dev = chi.device
-        out = dict(I_top=torch.empty((B, 12, ny, nx), dtype=dt, device=dev),
-                   J=torch.empty((nz, ny, nx), dtype=torch.float64, device=dev),
-                   F=torch.empty((3, nz, ny, nx), dtype=torch.float64, device=dev),
-                   Q=torch.empty((nz, ny, nx), dtype=torch.float64, device=dev))
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    err = C.create_string_buffer(512)
-    g = Grid(nx, ny, nz, dx, dy, dz)
-    rc = L.rts_solve_noalloc(C.byref(g), B, prec, _ptr(chi.contiguous()), _ptr(S.contiguous()),
-                             _ptr(out.get("I_top")), _ptr(out.get("J")), _ptr(out.get("F")), _ptr(out.get("Q")),
-                             C.c_void_p(stream.cuda_stream), err, 512)
+    for name, t in (("chi", chi), ("S", S)):
+        if not t.is_cuda or t.dtype != dt:
+            raise ValueError(f"{name} must be a CUDA tensor of {dt}, got {t.dtype} on {t.device}")
+    if S.shape != chi.shape or S.device != chi.device:
+        raise ValueError(f"S {tuple(S.shape)} on {S.device} must match chi {tuple(chi.shape)} on {chi.device}")
+    shapes = dict(I_top=((B, 12, ny, nx), dt), J=((nz, ny, nx), torch.float64), F=((3, nz, ny, nx), torch.float64),
+                  Q=((nz, ny, nx), torch.float64))
+    with torch.cuda.device(chi.device):  # the library uses the current device's scratch array and stream
+        if out is None:
+            out = {k: torch.empty(shp, dtype=d, device=chi.device) for k, (shp, d) in shapes.items()}
+        for k, v in out.items():
+            shp, d = shapes[k]
+            if v is not None and (tuple(v.shape) != shp or v.dtype != d or v.device != chi.device
+                                  or not v.is_contiguous()):
+                raise ValueError(f"out[{k!r}] must be a contiguous {d} tensor {shp} on {chi.device}")
+        if stream is None:
+            stream = torch.cuda.current_stream(chi.device)
+        err = C.create_string_buffer(512)
+        g = Grid(nx, ny, nz, dx, dy, dz)
+        rc = L.rts_solve_noalloc(C.byref(g), B, prec, _ptr(chi.contiguous()), _ptr(S.contiguous()),
+                                 _ptr(out.get("I_top")), _ptr(out.get("J")), _ptr(out.get("F")), _ptr(out.get("Q")),
+                                 C.c_void_p(stream.cuda_stream), err, 512)
     if rc != RTS_OK:
         raise RTSError(rc, err.value.decode())
     return out
+
+
+def device_code_version() -> int:
+    """Compute capability the loaded kernels were built for (103 = sm_103a)."""
+    return load().rts_device_code_version()

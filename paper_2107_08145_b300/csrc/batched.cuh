@@ -47,7 +47,8 @@ __host__ __device__ inline long long sub_blocks(int which, int nx, int ny, int n
 template <typename T>
 __global__ void __launch_bounds__(256) transpose_x2_batched(const SubDesc *__restrict__ d, int nsub, int B,
                                                               const T *__restrict__ in0, const T *__restrict__ in1,
-                                                              T *__restrict__ out0, T *__restrict__ out1)
+                                                              T *__restrict__ out0, T *__restrict__ out1,
+                                                              int *status)
 {
     const int s = find_sub(d, nsub, 0, blockIdx.x);
     const SubDesc &sd = d[s];
@@ -56,7 +57,7 @@ __global__ void __launch_bounds__(256) transpose_x2_batched(const SubDesc *__res
     const int bx = r % tx, by = (r / tx) % ty;
     const long long bk = r / (tx * ty);
     transpose_tile2(in0 + sd.in_off, in1 + sd.in_off, out0 + sd.in_off, out1 + sd.in_off, sd.nx, sd.ny, sd.nz, bx * 32,
-                    by * 32, bk / sd.nz, bk % sd.nz);
+                    by * 32, bk / sd.nz, bk % sd.nz, status);
 }
 
 template <typename T, typename Acc>

@@ -9,7 +9,7 @@
 namespace rts {
 
 // Device status bits (mapped to rts_status on the host).
-enum : int { ST_TIMEOUT = 1, ST_NOCONV = 2, ST_BADARG = 4 };
+enum : int { ST_TIMEOUT = 1, ST_NOCONV = 2, ST_BADARG = 4, ST_NONFINITE = 8 };
 
 __device__ __forceinline__ void red_release_add(unsigned *p, unsigned v)
 {

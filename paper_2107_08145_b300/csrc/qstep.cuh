@@ -14,6 +14,7 @@
 #pragma once
 #include <type_traits>
 
+#include "common.cuh"
 #include "df32.cuh"
 
 namespace rts {
@@ -39,23 +40,29 @@ __device__ __forceinline__ void transpose_tile(const T *__restrict__ in, T *__re
 }
 
 // the same tile of two arrays at once (chi and S: all 8 loads of a thread
-// in flight together, one launch for both)
+// in flight together, one launch for both). Every input value passes here
+// once per solve, so this is also where non-finite chi or S is detected:
+// ST_NONFINITE in *status (the solve still runs; rts_check reports it).
 template <typename T>
 __device__ __forceinline__ void transpose_tile2(const T *__restrict__ in0, const T *__restrict__ in1,
                                                 T *__restrict__ out0, T *__restrict__ out1, int nx, int ny, int nz,
-                                                int i0, int j0, long long b, long long k)
+                                                int i0, int j0, long long b, long long k, int *status)
 {
     __shared__ T tile[2][32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const long long so = (b * nz + k) * (long long)ny * nx;
+    bool bad = false;
 #pragma unroll
     for (int jj = ty; jj < 32; jj += 8) {
         const int i = i0 + tx, j = j0 + jj;
         if (i < nx && j < ny) {
-            tile[0][jj][tx] = in0[so + (long long)j * nx + i];
-            tile[1][jj][tx] = in1[so + (long long)j * nx + i];
+            const T c = in0[so + (long long)j * nx + i], s = in1[so + (long long)j * nx + i];
+            tile[0][jj][tx] = c;
+            tile[1][jj][tx] = s;
+            bad = bad || !isfinite(c) || !isfinite(s);
         }
     }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
     __syncthreads();
 #pragma unroll
     for (int ii = ty; ii < 32; ii += 8) {
@@ -71,10 +78,22 @@ __device__ __forceinline__ void transpose_tile2(const T *__restrict__ in0, const
 template <typename T>
 __global__ void __launch_bounds__(256) transpose_x2_kernel(const T *__restrict__ in0, const T *__restrict__ in1,
                                                              T *__restrict__ out0, T *__restrict__ out1, int nx,
-                                                             int ny, int nz)
+                                                             int ny, int nz, int *status)
 {
     const long long bk = blockIdx.z;
-    transpose_tile2(in0, in1, out0, out1, nx, ny, nz, blockIdx.x * 32, blockIdx.y * 32, bk / nz, bk % nz);
+    transpose_tile2(in0, in1, out0, out1, nx, ny, nz, blockIdx.x * 32, blockIdx.y * 32, bk / nz, bk % nz, status);
+}
+
+// The non-finite check alone, for grids whose solve needs no transposed
+// copy: every value of chi and S once, a grid-stride loop.
+template <typename T>
+__global__ void __launch_bounds__(256) check_finite_kernel(const T *__restrict__ a, const T *__restrict__ b,
+                                                             long long n, int *status)
+{
+    bool bad = false;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        bad = bad || !isfinite(a[i]) || !isfinite(b[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NONFINITE);
 }
 
 // four values moved as one element (the adjoint's lam0 of a point)

@@ -31,6 +31,14 @@
 
 namespace {
 
+// chi = exp(log chi) for RTS_FLAG_LOG_CHI (accurate exp of the precision)
+template <typename T>
+__global__ void __launch_bounds__(256) exp_kernel(const T *__restrict__ in, T *__restrict__ out, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = exp(in[i]);
+}
+
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kLag = 8;  // planes between posting the seed-error bound and using it
 
@@ -232,6 +240,7 @@ struct rts_handle {
 
     // device memory (one allocation, carved)
     void *dmem = nullptr;
+    void *d_chi_exp = nullptr;    // RTS_FLAG_LOG_CHI: exp(log chi) of the current call
     rts::SweepUnit *d_units = nullptr;
     int *d_unit_of_tile = nullptr;
     void *d_partial = nullptr, *d_chiT = nullptr, *d_ST = nullptr, *d_JF = nullptr, *d_halo = nullptr;
@@ -722,6 +731,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
 
     const long long nx = g->nx, ny = g->ny, nz = g->nz;
     h->N = nx * ny * nz;
+    if (nz * nbands > 65535)  // the transposes and reductions launch one CTA layer per (band, level)
+        return bail(fail(h, RTS_EINVAL, "nz * nbands = %lld exceeds 65535", nz * (long long)nbands));
 
     // ---- sweep units and tiling ----
     int npmax = 0;
@@ -855,6 +866,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_tacc = take(sizeof(int) * h->units.size());
     const size_t o_ru = take(sizeof(rts::RedUnit) * h->units.size());
     const size_t o_rub = take(sizeof(int) * (nbands + 1));
+    const bool log_chi = (o.flags & RTS_FLAG_LOG_CHI) != 0;
+    const size_t o_cexp = log_chi ? take((size_t)nbands * h->N * es) : 0;
     const size_t o_regu = h->use_reg ? take(sizeof(rts::SweepUnit) * h->reg_units.size()) : 0;
     const size_t o_reguot = h->use_reg ? take(sizeof(int) * h->reg_unit_of_tile.size()) : 0;
     size_t o_adj[9] = {0};
@@ -911,6 +924,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->d_unit_tacc = (int *)(base + o_tacc);
     h->d_ru = (rts::RedUnit *)(base + o_ru);
     h->d_ru_begin = (int *)(base + o_rub);
+    if (log_chi) h->d_chi_exp = base + o_cexp;
     if (h->use_reg) {
         h->d_reg_units = (rts::SweepUnit *)(base + o_regu);
         h->d_reg_uot = (int *)(base + o_reguot);
@@ -1025,6 +1039,21 @@ static rts_status reset_sweep_state(rts_handle *h, cudaStream_t st)
     return RTS_OK;
 }
 
+// RTS_FLAG_LOG_CHI: the caller passed log chi; chi = exp(log chi) goes to the
+// handle's scratch array, which the solve then reads
+template <typename T>
+static rts_status form_chi(rts_handle *h, const void *&chi, int &kernels)
+{
+    if (!h->d_chi_exp) return RTS_OK;
+    const long long n = (long long)h->B * h->N;
+    const int cb = (int)std::min<long long>((n + 255) / 256, 148LL * 8);
+    exp_kernel<T><<<cb, 256, 0, h->stream>>>((const T *)chi, (T *)h->d_chi_exp, n);
+    CUDA_TRY(h, cudaGetLastError());
+    chi = h->d_chi_exp;
+    kernels += 1;
+    return RTS_OK;
+}
+
 template <typename T, typename Acc>
 static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top,
                              double *J, double *F, double *Q)
@@ -1050,10 +1079,17 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
         CUDA_TRY(h, cudaEventRecord(ev[0], st));
     }
     int kernels = 0;
+    if (rts_status fs = form_chi<T>(h, chi, kernels)) return fs;
     if (h->has_x) {
         dim3 tb(32, 8), tg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * B));
         rts::transpose_x2_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (const T *)S, (T *)h->d_chiT, (T *)h->d_ST,
-                                                      g.nx, g.ny, g.nz);
+                                                      g.nx, g.ny, g.nz, h->d_status);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 1;
+    } else {  // no transposed copy to make: the non-finite check alone
+        const long long n = (long long)B * h->N;
+        const int cb = (int)std::min<long long>((n + 255) / 256, 148LL * 8);
+        rts::check_finite_kernel<T><<<cb, 256, 0, st>>>((const T *)chi, (const T *)S, n, h->d_status);
         CUDA_TRY(h, cudaGetLastError());
         kernels += 1;
     }
@@ -1135,9 +1171,16 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
         if (rts_status ms = mark(-1)) return ms;
         ++h->adj_calls;
     }
+    if (rts_status fs = form_chi<T>(h, chi, kernels)) return fs;
     if (h->has_x) {
         rts::transpose_x2_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (const T *)S, (T *)h->d_chiT, (T *)h->d_ST,
-                                                      g.nx, g.ny, g.nz);
+                                                      g.nx, g.ny, g.nz, h->d_status);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 1;
+    } else {
+        const long long n = (long long)B * N;
+        const int cb = (int)std::min<long long>((n + 255) / 256, 148LL * 8);
+        rts::check_finite_kernel<T><<<cb, 256, 0, st>>>((const T *)chi, (const T *)S, n, h->d_status);
         CUDA_TRY(h, cudaGetLastError());
         kernels += 1;
     }
@@ -1368,10 +1411,18 @@ rts_status rts_check(rts_handle *h)
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     int st = 0;
     CUDA_TRY(h, cudaMemcpy(&st, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & rts::ST_NONFINITE) return fail(h, RTS_ENONFINITE, "non-finite value in chi or S (a NaN or an infinity)");
     if (st & rts::ST_TIMEOUT) return fail(h, RTS_ETIMEOUT, "a device-side wait exceeded %.3g s", h->opt.timeout_s);
     if (st & rts::ST_NOCONV)
         return fail(h, RTS_ENOCONV, "periodic wrap not converged within %d periods", h->opt.max_wrap_iters);
     return RTS_OK;
+}
+
+int rts_device_code_version(void)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, rts::check_finite_kernel<float>) != cudaSuccess) return -1;
+    return fa.binaryVersion;
 }
 
 rts_status rts_get_stats(rts_handle *h, rts_stats *out)
@@ -1613,7 +1664,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     if (has_x) {
         dim3 tb(32, 8), tg((g->nx + 31) / 32, (g->ny + 31) / 32, (unsigned)(g->nz * B));
         rts::transpose_x2_kernel<T><<<tg, tb, 0, st>>>((const T *)chi, (const T *)S, (T *)(base + o_chiT),
-                                                      (T *)(base + o_ST), g->nx, g->ny, g->nz);
+                                                      (T *)(base + o_ST), g->nx, g->ny, g->nz,
+                                                      (int *)(base + o_ctl) + 4);
         NA_TRY(cudaGetLastError());
     }
     rts::SweepArgs<T> a;
@@ -1674,6 +1726,10 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     int status = 0;
     NA_TRY(cudaMemcpy(&status, base + o_ctl + 4 * sizeof(int), sizeof(int), cudaMemcpyDeviceToHost));
 #undef NA_TRY
+    if (status & rts::ST_NONFINITE) {
+        noalloc_msg(err, errlen, "non-finite value in chi or S");
+        return RTS_ENONFINITE;
+    }
     if (status & rts::ST_TIMEOUT) {
         noalloc_msg(err, errlen, "a device-side wait exceeded 2 s");
         return RTS_ETIMEOUT;
@@ -1706,6 +1762,11 @@ extern "C" rts_status rts_solve_noalloc(const rts_grid *g, int nbands, rts_preci
         return RTS_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        noalloc_msg(err, errlen, "rts_solve_noalloc waits for its stream and cannot run inside a stream capture");
+        return RTS_EINVAL;
+    }
     switch (prec) {
     case RTS_FP64: return noalloc_solve<double, double>(g, nbands, chi, S, I_top, J, F, Q_rad, st, err, errlen);
     case RTS_FP32_MIXED: return noalloc_solve<float, double>(g, nbands, chi, S, I_top, J, F, Q_rad, st, err, errlen);
@@ -1754,8 +1815,9 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     if (o.prec != RTS_FP64 && o.prec != RTS_FP32_MIXED && o.prec != RTS_FP32_COMPENSATED)
         return bail(fail(h, RTS_EINVAL, "unknown precision %d", (int)o.prec));
     if (!(o.tau_switch > 0)) return bail(fail(h, RTS_EINVAL, "tau_switch must be > 0"));
-    if (o.flags & (RTS_FLAG_ADJOINT | RTS_FLAG_HOST_IO))
-        return bail(fail(h, RTS_EINVAL, "batched handles take neither RTS_FLAG_ADJOINT nor RTS_FLAG_HOST_IO"));
+    if (o.flags & (RTS_FLAG_ADJOINT | RTS_FLAG_HOST_IO | RTS_FLAG_HOST_IO_ASYNC | RTS_FLAG_LOG_CHI))
+        return bail(fail(h, RTS_EINVAL,
+                         "batched handles take none of RTS_FLAG_ADJOINT, RTS_FLAG_HOST_IO(_ASYNC), RTS_FLAG_LOG_CHI"));
     if (o.max_wrap_iters < 1) o.max_wrap_iters = 64;
     if (!(o.timeout_s > 0)) o.timeout_s = 2.0;
     if (!(o.wrap_tol > 0)) o.wrap_tol = o.prec == RTS_FP64 ? 1e-15 : 0x1p-24;
@@ -2004,7 +2066,7 @@ static rts_status solve_batched_impl(rts_handle *h, const void *chi, const void 
     if (h->has_x) {
         rts::transpose_x2_batched<T><<<(unsigned)h->nblk[0], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->B, (const T *)chi,
                                                                                   (const T *)S, (T *)h->d_chiT,
-                                                                                  (T *)h->d_ST);
+                                                                                  (T *)h->d_ST, h->d_status);
         CUDA_TRY(h, cudaGetLastError());
         kernels += 1;
     }

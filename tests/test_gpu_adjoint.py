@@ -189,7 +189,7 @@ def test_autograd_function_matches_adjoint(rts):
 
     nx, ny, nz, B = 12, 12, 10, 2
     chi, S = random_case(nx, ny, nz, B, seed=41)
-    s = rts.Solver(nx, ny, nz, B, precision="fp64", adjoint=True)
+    s = rts.Solver(nx, ny, nz, B, precision="fp64", adjoint=True, log_chi=True)
     lc = torch.tensor(np.log(chi), device="cuda", requires_grad=True)
     St = torch.tensor(S, device="cuda", requires_grad=True)
     I_top, J, F, Q = rts_apply(s, lc, St)
@@ -210,11 +210,11 @@ def _fd_case(rts, precision):
 
     chi, S = workload_inputs("adj16x4")
     B, nz, ny, nx = chi.shape
-    s = rts.Solver(nx, ny, nz, B, precision=precision, adjoint=True)
+    s = rts.Solver(nx, ny, nz, B, precision=precision, adjoint=True, log_chi=True)
     dt = s.dtype
     S_hot = S * 1.05 ** 4
-    with torch.no_grad():
-        tgt = s.solve(torch.tensor(chi, dtype=dt, device="cuda"), torch.tensor(S_hot, dtype=dt, device="cuda"))
+    with torch.no_grad():  # the solver takes log chi
+        tgt = s.solve(torch.tensor(np.log(chi), dtype=dt, device="cuda"), torch.tensor(S_hot, dtype=dt, device="cuda"))
     I_target = tgt["I_top"].clone()
 
     def loss_of(lc, St):

@@ -205,3 +205,48 @@ def test_nonconvergence_reported(rts):
     # the handle stays usable: an optically thick medium converges at once
     out = s.solve(c + 20.0, S)
     assert torch.isfinite(out["J"]).all()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_nonfinite_input_is_reported(rts, prec):
+    """A NaN or an infinity in chi or S is found on the device and reported
+    as RTS_ENONFINITE (with and without x-dominant rays, whose transposed
+    copy otherwise does the check); the handle stays usable."""
+    import oracle
+
+    nx, ny, nz, B = 12, 10, 9, 2
+    chi, S = random_case(nx, ny, nz, B, seed=9)
+    n, w = oracle.a4_quadrature()
+    zonly = [d for d in range(24) if abs(n[d][2]) > 0.8]  # the z-dominant rays only: no transposed copy
+    for quad in (None, (np.ascontiguousarray(n[zonly]), np.ascontiguousarray(w[zonly] / w[zonly].sum()))):
+        kw = {} if quad is None else dict(n=quad[0], w=quad[1])
+        s = rts.Solver(nx, ny, nz, B, precision=prec, **kw)
+        for arr, bad in ((0, np.nan), (1, np.inf)):
+            c, S2 = chi.copy(), S.copy()
+            (c if arr == 0 else S2)[1, 3, 4, 5] = bad
+            with pytest.raises(rts.RTSError) as e:
+                gpu_solve(s, c, S2)
+            assert e.value.code == rts.RTS_ENONFINITE, e.value
+        got = gpu_solve(s, chi, S)  # a clean solve afterwards
+        assert all(np.isfinite(got[k]).all() for k in OUTPUTS)
+
+
+def test_log_chi_flag_matches_chi(rts):
+    """RTS_FLAG_LOG_CHI: the library forms chi = exp(log chi) itself; the
+    solve equals the one on chi to the rounding of exp."""
+    import torch
+
+    nx, ny, nz, B = 14, 12, 10, 2
+    chi, S = random_case(nx, ny, nz, B, seed=13)
+    for prec, tol in (("fp64", 1e-13), ("fp32", 2e-6)):
+        a = rts.Solver(nx, ny, nz, B, precision=prec)
+        b = rts.Solver(nx, ny, nz, B, precision=prec, log_chi=True)
+        dt = a.dtype
+        ga = a.solve(torch.tensor(chi, dtype=dt, device="cuda"), torch.tensor(S, dtype=dt, device="cuda"))
+        gb = b.solve(torch.log(torch.tensor(chi, dtype=dt, device="cuda")), torch.tensor(S, dtype=dt, device="cuda"))
+        for k in OUTPUTS:
+            assert norm_err(gb[k].double().cpu().numpy(), ga[k].double().cpu().numpy()) <= tol, (prec, k)
+
+
+def test_device_code_version(rts):
+    assert rts.device_code_version() == 103

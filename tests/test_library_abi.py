@@ -31,9 +31,24 @@ def test_library_loads_and_exports_every_symbol():
         assert re.search(r"\bT %s$" % name, out, re.M), name
 
 
-def test_library_is_sm103a():
-    out = subprocess.run(["cuobjdump", "--list-elf", rts.library_path()], capture_output=True, text=True).stdout
-    assert "sm_103a" in out
+def test_library_is_built_for_sm103a():
+    """Every translation unit is compiled for sm_103a only (the build
+    command); the GPU test test_device_code_is_sm103 reads the loaded
+    kernels' version at run time."""
+    from paper_2107_08145_b300 import build
+
+    cmd = build.compile_command("x.cu", "x.o")
+    assert "arch=compute_103a,code=sm_103a" in cmd and cmd.count("-gencode") == 1
+    assert "-gencode" in build.link_command([], "x.so")
+
+
+@pytest.mark.gpu
+def test_device_code_is_sm103():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    assert rts.device_code_version() == 103
 
 
 def test_default_options_and_null_handle():
@@ -65,6 +80,17 @@ def test_create_rejects_bad_grid_without_gpu():
     g = rts.Grid(4, 4, 4, 1.0, 1.0, 1.0)
     rc = L.rts_create(ctypes.byref(h), ctypes.byref(g), 1, ctypes.byref(q), None)
     assert rc == rts.RTS_EINVAL and b"n_z" in L.rts_last_error(h)
+    L.rts_destroy(h)
+
+
+def test_create_rejects_too_many_levels_times_bands_without_gpu():
+    """The per-level launches take one CTA layer per (band, level): nz * B is
+    capped at 65535 and refused at create, before any CUDA call."""
+    L = rts.load()
+    h = ctypes.c_void_p()
+    g = rts.Grid(4, 4, 8192, 1.0, 1.0, 1.0)
+    rc = L.rts_create(ctypes.byref(h), ctypes.byref(g), 9, None, None)
+    assert rc == rts.RTS_EINVAL and b"65535" in L.rts_last_error(h)
     L.rts_destroy(h)
 
 

@@ -474,9 +474,6 @@ def test_invalid_problem_rejected(oracle_mod):
 
 def test_exact_value_from_math(oracle_mod):
     """one cell column, one z ray: hand-derived single-step formula."""
-    mu = 0.6
-    n = np.array([[0.0, math.sqrt(1 - mu * mu), mu]])
-    # y component larger than z?  sqrt(0.64)=0.8 > 0.6 -> y-dominant; use z-dominant instead
     n = np.array([[0.0, 0.0, 1.0]])
     P = oracle.Problem(1, 1, 2, 1, n=n, w=np.array([1.0]), bottom=oracle.BC_EXPLICIT,
                        bottom_I=np.array([[[[3.0]]]]))

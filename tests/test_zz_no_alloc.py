@@ -12,7 +12,7 @@ from tests.gpu_common import OUTPUTS, norm_err, random_case
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "fp32_compensated": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -27,7 +27,7 @@ def rts():
     return m
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "fp32_compensated"])
 def test_noalloc_matches_regular_solve_twice(rts, prec):
     import torch
 
@@ -53,3 +53,45 @@ def test_noalloc_rejects_too_large(rts):
         rts.solve_noalloc(c, c, precision="fp32")
     assert ei.value.code == rts.RTS_EINVAL
     assert "scratch" in str(ei.value)
+
+
+def test_noalloc_smaller_grid_after_larger(rts):
+    """The shared array keeps a larger earlier call's contents (partials,
+    reductions, transposes at other offsets): a smaller, differently shaped
+    call afterwards still matches rts_solve."""
+    import torch
+
+    for (nx, ny, nz, B) in ((40, 36, 30, 2), (18, 22, 11, 1), (26, 14, 17, 3)):
+        chi, S = random_case(nx, ny, nz, B, seed=nx)
+        c = torch.as_tensor(chi, dtype=torch.float32, device="cuda")
+        s = torch.as_tensor(S, dtype=torch.float32, device="cuda")
+        ref = rts.Solver(nx, ny, nz, B, precision="fp32").solve(c, s)
+        got = rts.solve_noalloc(c, s, precision="fp32")
+        for k in OUTPUTS:
+            e = norm_err(got[k].double().cpu().numpy(), ref[k].double().cpu().numpy())
+            assert e <= TOL["fp32"], ((nx, ny, nz, B), k, e)
+
+
+def test_noalloc_refuses_stream_capture(rts):
+    """The call waits for its stream, so inside a capture it must refuse
+    (RTS_EINVAL) and leave the capture intact."""
+    import torch
+
+    nx, ny, nz, B = 16, 16, 8, 1
+    chi, S = random_case(nx, ny, nz, B, seed=2)
+    c = torch.as_tensor(chi, dtype=torch.float32, device="cuda")
+    s = torch.as_tensor(S, dtype=torch.float32, device="cuda")
+    out = rts.solve_noalloc(c, s, precision="fp32")  # outputs made outside the capture
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    refused = None
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            try:
+                rts.solve_noalloc(c, s, precision="fp32", out=out, stream=side)
+            except rts.RTSError as e:
+                refused = e
+            c.add_(0.0)  # the capture is still usable
+    assert refused is not None and refused.code == rts.RTS_EINVAL and "capture" in str(refused)
+    g.replay()
+    torch.cuda.synchronize()
