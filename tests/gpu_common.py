@@ -60,3 +60,44 @@ def oracle_solve(chi, S, dx=1.0, dy=1.0, dz=1.0, bottom="equal_s", top="zero", n
 
 def workload_inputs(name, **kw):
     return workload(name, **kw)
+
+
+FOUR_PI = 4.0 * np.pi
+
+
+def elementwise_floors(ref, chi, S, h_min=1.0):
+    """Per-point scales of the terms each output is formed from, for an
+    element-wise bar |got - ref| <= rel * (|ref| + floor):
+      I_top, J   0 (sums of non-negative terms: relative to the value)
+      F          4 pi J        (every |F_c| <= 4 pi sum_d w_d |n_d| I_d <= 4 pi J)
+      Q_rad      4 pi sum_b (chi_b S_b + J_b / h_min), bounded with J for J_b:
+                 the sizes of 4 pi chi (J - S) and of div F, which cancel"""
+    chi = np.asarray(chi, dtype=np.float64)
+    S = np.asarray(S, dtype=np.float64)
+    J = np.abs(np.asarray(ref["J"], dtype=np.float64))
+    fl = {"I_top": 0.0, "J": 0.0, "F": FOUR_PI * J[None]}
+    fl["Q"] = FOUR_PI * ((chi * S).sum(axis=0) + J / h_min)
+    return fl
+
+
+def elementwise_err(got, ref, floor):
+    """max over points of |got - ref| / (|ref| + floor) (0/0 counts as 0)."""
+    g = np.asarray(got, dtype=np.float64)
+    r = np.asarray(ref, dtype=np.float64)
+    den = np.abs(r) + floor
+    d = np.abs(g - r)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        q = np.where(den > 0, d / den, np.where(d > 0, np.inf, 0.0))
+    return float(q.max())
+
+
+def error_report(got, ref, chi, S, h_min=1.0):
+    """Normwise and element-wise errors per output, and the flux components
+    and I_top relative to their own maximum."""
+    fl = elementwise_floors(ref, chi, S, h_min)
+    rep = {}
+    for k in OUTPUTS:
+        rep[k] = {"normwise": norm_err(got[k], ref[k]), "elementwise": elementwise_err(got[k], ref[k], fl[k])}
+    for c, name in enumerate(("F_x", "F_y", "F_z")):
+        rep[name] = {"normwise": norm_err(got["F"][c], ref["F"][c])}
+    return rep
