@@ -331,6 +331,39 @@ rts_status rts_solve_noalloc(const rts_grid *g, int nbands, rts_precision prec,
                              void *I_top, double *J, double *F, double *Q_rad,
                              void *stream, char *err, size_t errlen);
 
+/* ---------------------------------------------------------------------------
+ * The solver's input step (paper Sect. 2, RTS "Interpolate": trilinear
+ * interpolation of the MHD variables from the MHD grid to the staggered RTS
+ * grid, then the source function and the opacities used by the integration).
+ * The MHD fields T and rho are given at the MHD cell centres of a grid of
+ * the same extents as the RTS grid; RTS point (i, j, k) lies at MHD cell
+ * coordinates (i, j, k) + shift (shift = -0.5 each: the RTS points on the
+ * cell corners). Per point: ln T and ln rho interpolated trilinearly from the
+ * 8 surrounding cells (periodic in x and y, clamped to the first and last
+ * layer in z); then for every band b
+ *   ln kappa_b = bilinear in the table ln_kappa[b][ir][it] at
+ *                (ln T - lnT0)/dlnT, (ln rho - lnR0)/dlnR (clamped to the table),
+ *   chi_b      = exp(ln kappa_b) rho,
+ *   S_b        = exp(ln B_b), ln B_b linear in ln_B[b][it] along ln T.
+ * The table is a band-integrated opacity (opacity binning, paper Sect. 1)
+ * and a band source function; the paper's tables are not available, so the
+ * library only defines the lookup. Arrays are device pointers: T_mhd, rho_mhd
+ * [Nz][Ny][Nx] and the tables in the precision's type (FP64 for RTS_FP64,
+ * FP32 otherwise), chi and S out, [B][Nz][Ny][Nx], the layout rts_solve
+ * reads. Enqueued on `stream`; no synchronisation, no allocation. err (may
+ * be NULL) receives a text. */
+typedef struct {
+    int nbands, nT, nR;
+    double lnT0, dlnT;     /* ln T of table column 0, step (> 0) */
+    double lnR0, dlnR;     /* ln rho of table row 0, step (> 0) */
+    const void *ln_kappa;  /* [nbands][nR][nT] ln of the opacity per unit density */
+    const void *ln_B;      /* [nbands][nT] ln of the band source function */
+    double shift[3];       /* RTS point (0,0,0) on the MHD grid, in cells */
+} rts_front_table;
+rts_status rts_front_end(const rts_grid *g, const rts_front_table *tab, rts_precision prec,
+                         const void *T_mhd, const void *rho_mhd, void *chi, void *S, void *stream,
+                         char *err, size_t errlen);
+
 #ifdef __cplusplus
 }
 #endif

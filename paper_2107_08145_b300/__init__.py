@@ -53,6 +53,12 @@ class Stats(C.Structure):
                 ("sweep_kernel", C.c_int)]
 
 
+class FrontTable(C.Structure):
+    _fields_ = [("nbands", C.c_int), ("nT", C.c_int), ("nR", C.c_int), ("lnT0", C.c_double), ("dlnT", C.c_double),
+                ("lnR0", C.c_double), ("dlnR", C.c_double), ("ln_kappa", C.c_void_p), ("ln_B", C.c_void_p),
+                ("shift", C.c_double * 3)]
+
+
 class Boundary(C.Structure):
     _fields_ = [("bottom", C.c_int), ("top", C.c_int), ("bottom_I", C.c_void_p), ("top_I", C.c_void_p)]
 
@@ -63,7 +69,8 @@ _lib = None
 EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "rts_check",
            "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint",
            "rts_create_batched", "rts_solve_batched", "rts_batched_layout", "rts_graph_create", "rts_graph_launch",
-           "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait", "rts_device_code_version")
+           "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait", "rts_device_code_version",
+           "rts_front_end")
 
 
 def library_path() -> str:
@@ -121,6 +128,9 @@ def load(build_if_missing: bool = True):
     L.rts_num_up.restype = C.c_int
     L.rts_device_code_version.argtypes = []
     L.rts_device_code_version.restype = C.c_int
+    L.rts_front_end.argtypes = [C.POINTER(Grid), C.POINTER(FrontTable), C.c_int, vp, vp, vp, vp, vp, C.c_char_p,
+                                C.c_size_t]
+    L.rts_front_end.restype = C.c_int
     L.rts_destroy.argtypes = [vp]
     L.rts_destroy.restype = None
     L.rts_solve_noalloc.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp,
@@ -542,3 +552,42 @@ def solve_noalloc(chi, S, precision="fp32", dx=1.0, dy=1.0, dz=1.0, out=None, st
 def device_code_version() -> int:
     """Compute capability the loaded kernels were built for (103 = sm_103a)."""
     return load().rts_device_code_version()
+
+
+def front_end(T, rho, table, precision="fp32", shift=(-0.5, -0.5, -0.5), out=None, stream=None):
+    """rts_front_end: chi_b and S_b [B, nz, ny, nx] on the RTS grid from the
+    MHD fields T and rho [nz, ny, nx] (CUDA tensors of the precision's dtype)
+    and a band table (dict with ln_kappa [B][nR][nT], ln_B [B][nT], lnT0,
+    dlnT, lnR0, dlnR). Enqueued on the current stream; returns (chi, S)."""
+    import torch
+
+    L = load()
+    prec = _PREC[precision]
+    dt = torch.float64 if prec == FP64 else torch.float32
+    if T.dim() != 3 or rho.shape != T.shape:
+        raise ValueError("T and rho must be [nz, ny, nx] of the same shape")
+    for name, t in (("T", T), ("rho", rho)):
+        if not t.is_cuda or t.dtype != dt:
+            raise ValueError(f"{name} must be a CUDA tensor of {dt}")
+    nz, ny, nx = T.shape
+    dev = T.device
+    lnk = torch.as_tensor(table["ln_kappa"], dtype=dt, device=dev).contiguous()
+    lnB = torch.as_tensor(table["ln_B"], dtype=dt, device=dev).contiguous()
+    nb, nR, nT = lnk.shape
+    if tuple(lnB.shape) != (nb, nT):
+        raise ValueError("ln_B must be [nbands, nT]")
+    tab = FrontTable(nb, nT, nR, table["lnT0"], table["dlnT"], table["lnR0"], table["dlnR"], lnk.data_ptr(),
+                     lnB.data_ptr(), (C.c_double * 3)(*shift))
+    if out is None:
+        out = (torch.empty((nb, nz, ny, nx), dtype=dt, device=dev), torch.empty((nb, nz, ny, nx), dtype=dt, device=dev))
+    if stream is None:
+        stream = torch.cuda.current_stream(dev)
+    err = C.create_string_buffer(256)
+    g = Grid(nx, ny, nz, 1.0, 1.0, 1.0)
+    with torch.cuda.device(dev):
+        rc = L.rts_front_end(C.byref(g), C.byref(tab), prec, _ptr(T.contiguous()), _ptr(rho.contiguous()),
+                             _ptr(out[0]), _ptr(out[1]), C.c_void_p(stream.cuda_stream), err, 256)
+    if rc != RTS_OK:
+        raise RTSError(rc, err.value.decode())
+    out[0]._rts_keep = (lnk, lnB)  # the tables stay alive until the enqueued kernel has read them
+    return out
