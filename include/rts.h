@@ -90,6 +90,7 @@ enum {
     RTS_FLAG_ADJOINT = 4, /* allocate the scratch of rts_adjoint */
     RTS_FLAG_HOST_IO_ASYNC = 8, /* two staging sets and two copy streams for
                              rts_solve_host_async */
+    RTS_FLAG_SCATTER = 32, /* the scratch of rts_scatter_solve */
     RTS_FLAG_LOG_CHI = 16 /* the chi argument of rts_solve, rts_adjoint and
                              rts_graph_create is log chi: the library forms
                              chi = exp(log chi) in a scratch array of B x N
@@ -191,6 +192,35 @@ rts_status rts_solve_host(rts_handle *h, const void *chi, const void *S, const r
  * RTS_FLAG_HOST_IO_ASYNC; bc kinds ZERO / EQUAL_S only. */
 rts_status rts_solve_host_async(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc,
                                 void *I_top, double *J, double *F, double *Q_rad);
+
+/* Scattering solve (paper Sect. 5.3.2: in strongly scattering media the
+ * source function depends on the intensity, S_b = (1 - eps_b) J_b + eps_b B_b,
+ * J_b the band's mean intensity): iterates
+ *   S <- S + [(1 - eps) J[S] + eps B - S] / [1 - (1 - eps) L*]
+ * until the largest relative change of S over all bands and points is
+ * <= tol, each iteration a forward solve of all bands with the current S
+ * (sweep and band reduction; J[S] is the formal solution) followed by the
+ * update. L* is a local approximation of the operator's diagonal,
+ * sum_d w_d (1 - (1 - e^-x_d)/x_d) with x_d = ds_d chi / 2 at the point (a
+ * lower bound of each segment's optical depth, so L* stays below the true
+ * diagonal and the iteration stable): it only preconditions the iteration
+ * (an accelerated Lambda iteration); the converged S solves the equation
+ * above. The paper's alternative, a
+ * Gauss-Seidel update along each ray, is not used: see the design notes.
+ * Arguments: chi, B_src (the thermal source) and eps (photon destruction
+ * probability, 0 < eps <= 1) are [B][Nz][Ny][Nx] device arrays of the sweep
+ * precision; S (same layout) is the initial guess on entry and the converged
+ * source function on return (bottom boundary kind EQUAL_S uses it). After
+ * convergence a last solve with that S writes I_top, J, F, Q_rad (any may be
+ * NULL). *iters (may be NULL) receives the number of iterations. Returns
+ * RTS_ENOCONV after max_iter iterations without convergence. Needs
+ * RTS_FLAG_SCATTER at create time. Synchronises once per iteration (it reads
+ * the change back), so not for stream capture. The problem's conditioning
+ * grows like 1/eps: in the FP32 modes the attainable tol and accuracy are
+ * about 3e-7 / min(eps); use RTS_FP64 for small eps. */
+rts_status rts_scatter_solve(rts_handle *h, const void *chi, const void *B_src, const void *eps, void *S,
+                             const rts_boundary *bc, int max_iter, double tol, int *iters,
+                             void *I_top, double *J, double *F, double *Q_rad);
 
 /* Wait for every rts_solve_host_async call of the handle and return the
  * device status (as rts_check). */

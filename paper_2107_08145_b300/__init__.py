@@ -21,6 +21,7 @@ FLAG_TIMING = 2
 FLAG_ADJOINT = 4
 FLAG_HOST_IO_ASYNC = 8
 FLAG_LOG_CHI = 16
+FLAG_SCATTER = 32
 
 _PREC = {"fp64": FP64, "fp32": FP32_MIXED, "fp32_mixed": FP32_MIXED, "fp32_compensated": FP32_COMPENSATED}
 _BC = {"zero": BC_ZERO, "equal_s": BC_EQUAL_S}
@@ -70,7 +71,7 @@ EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "
            "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint",
            "rts_create_batched", "rts_solve_batched", "rts_batched_layout", "rts_graph_create", "rts_graph_launch",
            "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait", "rts_device_code_version",
-           "rts_front_end")
+           "rts_front_end", "rts_scatter_solve")
 
 
 def library_path() -> str:
@@ -131,6 +132,9 @@ def load(build_if_missing: bool = True):
     L.rts_front_end.argtypes = [C.POINTER(Grid), C.POINTER(FrontTable), C.c_int, vp, vp, vp, vp, vp, C.c_char_p,
                                 C.c_size_t]
     L.rts_front_end.restype = C.c_int
+    L.rts_scatter_solve.argtypes = [vp, vp, vp, vp, vp, C.POINTER(Boundary), C.c_int, C.c_double,
+                                    C.POINTER(C.c_int), vp, vp, vp, vp]
+    L.rts_scatter_solve.restype = C.c_int
     L.rts_destroy.argtypes = [vp]
     L.rts_destroy.restype = None
     L.rts_solve_noalloc.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp,
@@ -161,7 +165,7 @@ class Solver:
     def __init__(self, nx, ny, nz, nbands=1, dx=1.0, dy=1.0, dz=1.0, precision="fp64", n=None, w=None,
                  tau_switch=0.1, wrap_tol=0.0, max_wrap_iters=64, tile_rows=0, timeout_s=2.0,
                  host_io=False, timing=False, stream=None, adjoint=False, adjoint_chunk_bands=0,
-                 host_io_async=False, sweep_kernel="auto", log_chi=False):
+                 host_io_async=False, sweep_kernel="auto", log_chi=False, scatter=False):
         import torch
 
         L = load()
@@ -179,7 +183,8 @@ class Solver:
         o.tile_rows = tile_rows
         o.timeout_s = timeout_s
         o.flags = ((FLAG_HOST_IO if host_io else 0) | (FLAG_TIMING if timing else 0) | (FLAG_ADJOINT if adjoint else 0)
-                   | (FLAG_HOST_IO_ASYNC if host_io_async else 0) | (FLAG_LOG_CHI if log_chi else 0))
+                   | (FLAG_HOST_IO_ASYNC if host_io_async else 0) | (FLAG_LOG_CHI if log_chi else 0)
+                   | (FLAG_SCATTER if scatter else 0))
         self.log_chi = log_chi
         o.adjoint_chunk_bands = adjoint_chunk_bands
         o.sweep_kernel = _SWEEP[sweep_kernel]
@@ -257,6 +262,35 @@ class Solver:
             self.check()
         del keep
         return out
+
+    def scatter_solve(self, chi, B, eps, S=None, max_iter=200, tol=None, bottom="equal_s", top="zero", out=None):
+        """rts_scatter_solve: the band source functions S = (1 - eps) J + eps B
+        (iterated on the GPU from S, default B). chi, B, eps: CUDA tensors
+        [B, nz, ny, nx] in the solver dtype. Returns (S, outputs, iterations).
+        Needs Solver(..., scatter=True)."""
+        torch = self.torch
+        shape = (self.nbands, self.nz, self.ny, self.nx)
+        for name, t in (("chi", chi), ("B", B), ("eps", eps)):
+            if tuple(t.shape) != shape or t.dtype != self.dtype or not t.is_cuda:
+                raise ValueError(f"{name} must be a CUDA {self.dtype} tensor {shape}")
+        S = (B.clone() if S is None else S.clone()).contiguous()
+        if tol is None:
+            tol = 1e-12 if self.prec == FP64 else 2e-6
+        if out is None:
+            dev = chi.device
+            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=self.dtype, device=dev),
+                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        b, keep = self._bc(bottom, top)
+        it = C.c_int(0)
+        rc = self._L.rts_scatter_solve(self._h, _ptr(chi.contiguous()), _ptr(B.contiguous()), _ptr(eps.contiguous()),
+                                       _ptr(S), C.byref(b), max_iter, tol, C.byref(it), _ptr(out.get("I_top")),
+                                       _ptr(out.get("J")), _ptr(out.get("F")), _ptr(out.get("Q")))
+        self._err(rc)
+        self.check()
+        del keep
+        return S, out, it.value
 
     def adjoint(self, chi, S, gI_top=None, gJ=None, gF=None, gQ=None, bottom="equal_s", top="zero", check=True,
                 out=None):

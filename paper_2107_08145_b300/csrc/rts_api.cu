@@ -39,6 +39,61 @@ __global__ void __launch_bounds__(256) exp_kernel(const T *__restrict__ in, T *_
         out[i] = exp(in[i]);
 }
 
+// Local operator of the scattering iteration: the weight of S at a point in
+// its own mean intensity is sum_d w_d (1 - q(dtau_d)), q(x) = (1 - e^-x)/x,
+// with dtau_d = ds_d (chi_up + chi_p)/2 the segment's optical depth. It is
+// taken here with dtau_d = ds_d chi_p / 2, a lower bound (chi_up >= 0), so
+// that L* never exceeds the true diagonal (1 - q grows with dtau): a larger
+// L* over-corrects and the iteration can diverge. Only the preconditioner:
+// the fixed point does not depend on it.
+template <typename T>
+__global__ void __launch_bounds__(256) lambda_star_kernel(const T *__restrict__ chi, const double *__restrict__ dirw,
+                                                           int ndir, long long n, T *__restrict__ lstar)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double c = (double)chi[i];
+        double l = 0.0;
+        for (int d = 0; d < ndir; ++d) {
+            const double x = 0.5 * dirw[2 * d] * c;
+            const double q = x < 1e-4 ? 1.0 - 0.5 * x + x * x / 6.0 : -expm1(-x) / x;
+            l += dirw[2 * d + 1] * (1.0 - q);
+        }
+        lstar[i] = (T)l;
+    }
+}
+
+template <typename A>
+__device__ __forceinline__ double acc_val(const A &v)
+{
+    return rts::acc_to_double(v);
+}
+
+// One step of the scattering iteration per band and point:
+//   S <- S + [(1 - eps) J_b + eps B - S] / [1 - (1 - eps) L*]
+// (J_b of the solve with the current S, from the handle's JF array), and the
+// largest |change| / |S| over all points into *dsmax (float bits, atomic max).
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(256) scatter_update_kernel(const Acc *__restrict__ JF, const T *__restrict__ eps,
+                                                              const T *__restrict__ Bp, const T *__restrict__ lstar,
+                                                              T *__restrict__ S, long long N, int nb,
+                                                              unsigned *dsmax)
+{
+    float m = 0.f;
+    const long long n = N * nb;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / N, p = i - b * N;
+        const double J = acc_val(JF[b * 4 * N + p]);
+        const double e = (double)eps[i], s = (double)S[i];
+        const double ds = ((1.0 - e) * J + e * (double)Bp[i] - s) / (1.0 - (1.0 - e) * (double)lstar[i]);
+        const T sn = (T)(s + ds);
+        S[i] = sn;
+        const double den = fabs((double)sn);
+        m = fmaxf(m, (float)(den > 0.0 ? fabs(ds) / den : (ds != 0.0 ? 1.0 : 0.0)));
+    }
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(dsmax, __float_as_uint(m));
+}
+
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kLag = 8;  // planes between posting the seed-error bound and using it
 
@@ -241,6 +296,12 @@ struct rts_handle {
     // device memory (one allocation, carved)
     void *dmem = nullptr;
     void *d_chi_exp = nullptr;    // RTS_FLAG_LOG_CHI: exp(log chi) of the current call
+    // RTS_FLAG_SCATTER: the local operator of every band and point, the
+    // per-direction path lengths and weights it is formed from, the iteration's
+    // largest relative change of S
+    void *d_lstar = nullptr;
+    double *d_dirw = nullptr;     // [ndir][2]: ds_d, w_d
+    unsigned *d_dsmax = nullptr;
     rts::SweepUnit *d_units = nullptr;
     int *d_unit_of_tile = nullptr;
     void *d_partial = nullptr, *d_chiT = nullptr, *d_ST = nullptr, *d_JF = nullptr, *d_halo = nullptr;
@@ -868,6 +929,10 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_rub = take(sizeof(int) * (nbands + 1));
     const bool log_chi = (o.flags & RTS_FLAG_LOG_CHI) != 0;
     const size_t o_cexp = log_chi ? take((size_t)nbands * h->N * es) : 0;
+    const bool scatter = (o.flags & RTS_FLAG_SCATTER) != 0;
+    const size_t o_lstar = scatter ? take((size_t)nbands * h->N * es) : 0;
+    const size_t o_dirw = scatter ? take(sizeof(double) * 2 * h->ndir) : 0;
+    const size_t o_dsmax = scatter ? take(sizeof(unsigned) * 4) : 0;
     const size_t o_regu = h->use_reg ? take(sizeof(rts::SweepUnit) * h->reg_units.size()) : 0;
     const size_t o_reguot = h->use_reg ? take(sizeof(int) * h->reg_unit_of_tile.size()) : 0;
     size_t o_adj[9] = {0};
@@ -925,6 +990,17 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->d_ru = (rts::RedUnit *)(base + o_ru);
     h->d_ru_begin = (int *)(base + o_rub);
     if (log_chi) h->d_chi_exp = base + o_cexp;
+    if (scatter) {
+        h->d_lstar = base + o_lstar;
+        h->d_dirw = (double *)(base + o_dirw);
+        h->d_dsmax = (unsigned *)(base + o_dsmax);
+        std::vector<double> dw(2 * h->ndir);
+        for (int d = 0; d < h->ndir; ++d) {
+            dw[2 * d] = geo[d].ds;
+            dw[2 * d + 1] = h->w[d];
+        }
+        CUDA_TRY(h, cudaMemcpy(h->d_dirw, dw.data(), sizeof(double) * dw.size(), cudaMemcpyHostToDevice));
+    }
     if (h->use_reg) {
         h->d_reg_units = (rts::SweepUnit *)(base + o_regu);
         h->d_reg_uot = (int *)(base + o_reguot);
@@ -1056,7 +1132,7 @@ static rts_status form_chi(rts_handle *h, const void *&chi, int &kernels)
 
 template <typename T, typename Acc>
 static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, const rts_boundary *bc, void *I_top,
-                             double *J, double *F, double *Q)
+                             double *J, double *F, double *Q, bool reduce_only = false)
 {
     const rts_grid &g = h->g;
     const int B = h->B;
@@ -1101,7 +1177,7 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     kernels += 1;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
-    if (J || F || Q) {
+    if (J || F || Q || reduce_only) {
         dim3 rb(32, 8);
         rts::QParams P;
         P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
@@ -1111,10 +1187,14 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
         rts::reduce_units_kernel<T, Acc><<<rg, rb, 0, st>>>(h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, g.nx, g.ny, g.nz,
                                                            reg ? 1 : 0);
         if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
-        dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
-        rts::qstep_kernel<T, Acc><<<qg, rb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, P, J, F, Q);
+        kernels += 1;
+        if (!reduce_only) {  // the per-band J_b, F_b stay in the handle's JF array
+            dim3 qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
+            rts::qstep_kernel<T, Acc><<<qg, rb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S, P, J, F,
+                                                        Q);
+            kernels += 1;
+        }
         CUDA_TRY(h, cudaGetLastError());
-        kernels += 2;
     } else if (ev) {
         CUDA_TRY(h, cudaEventRecord(ev[3], st));
     }
@@ -1403,6 +1483,70 @@ rts_status rts_host_wait(rts_handle *h)
     if (h->s_h2d) CUDA_TRY(h, cudaStreamSynchronize(h->s_h2d));
     if (h->s_d2h) CUDA_TRY(h, cudaStreamSynchronize(h->s_d2h));
     return rts_check(h);
+}
+
+}  // extern "C"
+
+// The scattering solve (declared in rts.h): the iteration of the band source
+// functions S = (1 - eps) J + eps B, each iteration a forward solve (sweep and
+// band reduction) and the preconditioned update; the outputs of the last
+// solve with the converged S.
+template <typename T, typename Acc>
+static rts_status scatter_impl(rts_handle *h, const void *chi, const void *Bp, const void *eps, void *S,
+                               const rts_boundary *bc, int max_iter, double tol, int *iters, void *I_top, double *J,
+                               double *F, double *Q)
+{
+    cudaStream_t st = h->stream;
+    const long long n = (long long)h->B * h->N;
+    const int cb = (int)std::min<long long>((n + 255) / 256, 148LL * 8);
+    int dummy = 0;
+    const void *c = chi;
+    if (rts_status fs = form_chi<T>(h, c, dummy)) return fs;
+    lambda_star_kernel<T><<<cb, 256, 0, st>>>((const T *)c, h->d_dirw, h->ndir, n, (T *)h->d_lstar);
+    CUDA_TRY(h, cudaGetLastError());
+    int it = 0;
+    bool conv = false;
+    for (; it < max_iter && !conv; ++it) {
+        rts_status rs = solve_impl<T, Acc>(h, chi, S, bc, nullptr, nullptr, nullptr, nullptr, true);
+        if (rs) return rs;
+        CUDA_TRY(h, cudaMemsetAsync(h->d_dsmax, 0, sizeof(unsigned), st));
+        scatter_update_kernel<T, Acc><<<cb, 256, 0, st>>>((const Acc *)h->d_JF, (const T *)eps, (const T *)Bp,
+                                                          (const T *)h->d_lstar, (T *)S, h->N, h->B, h->d_dsmax);
+        CUDA_TRY(h, cudaGetLastError());
+        unsigned bits = 0;
+        CUDA_TRY(h, cudaMemcpyAsync(&bits, h->d_dsmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        rs = rts_check(h);  // waits for the stream; device errors end the iteration
+        if (rs) return rs;
+        float m;
+        std::memcpy(&m, &bits, sizeof(m));
+        conv = m <= tol;
+    }
+    if (iters) *iters = it;
+    if (!conv) return fail(h, RTS_ENOCONV, "scattering iteration not converged in %d iterations", max_iter);
+    return solve_impl<T, Acc>(h, chi, S, bc, I_top, J, F, Q);
+}
+
+extern "C" {
+
+rts_status rts_scatter_solve(rts_handle *h, const void *chi, const void *B_src, const void *eps, void *S,
+                             const rts_boundary *bc, int max_iter, double tol, int *iters, void *I_top, double *J,
+                             double *F, double *Q_rad)
+{
+    if (!h || !h->dmem) return h ? fail(h, RTS_EINVAL, "handle was not created successfully") : RTS_EINVAL;
+    if (!h->d_lstar) return fail(h, RTS_EINVAL, "rts_scatter_solve needs RTS_FLAG_SCATTER at create time");
+    if (!chi || !B_src || !eps || !S) return fail(h, RTS_EINVAL, "chi, B, eps and S must not be NULL");
+    if (S == chi || S == B_src || S == eps) return fail(h, RTS_EINVAL, "S must not alias the other inputs");
+    if (max_iter < 1 || !(tol > 0)) return fail(h, RTS_EINVAL, "max_iter >= 1 and tol > 0 are needed");
+    if (h->capturing) return fail(h, RTS_EINVAL, "the scattering iteration synchronises: not inside a capture");
+    rts_status s = check_bc(h, bc);
+    if (s) return s;
+    switch (h->opt.prec) {
+    case RTS_FP64: return scatter_impl<double, double>(h, chi, B_src, eps, S, bc, max_iter, tol, iters, I_top, J, F, Q_rad);
+    case RTS_FP32_MIXED:
+        return scatter_impl<float, double>(h, chi, B_src, eps, S, bc, max_iter, tol, iters, I_top, J, F, Q_rad);
+    default:
+        return scatter_impl<float, rts::df32>(h, chi, B_src, eps, S, bc, max_iter, tol, iters, I_top, J, F, Q_rad);
+    }
 }
 
 rts_status rts_check(rts_handle *h)
