@@ -151,11 +151,30 @@ typedef struct {
     int sweep_kernel;     /* forward sweep rts_solve runs: RTS_SWEEP_SHARED or RTS_SWEEP_REGISTER */
 } rts_stats;
 
+/* Boundary conditions of a solve, and the optional warm start of the
+ * horizontally periodic wrap (paper Sect. 2: the solver starts from the
+ * intensities of a previous time step or iteration and iterates the boundary
+ * intensities until they converge).
+ * wrap_seed (device, float, rts_wrap_seed_elems(h) elements; FP32 register
+ * sweep only, else RTS_EINVAL): for every x- and y-dominant direction group
+ * the intensities of its wrap plane (the plane upwind of the first swept
+ * one, [Nq][Np][4 sign slots] per group). Written with the converged values
+ * by every solve that is given it. With seed_in != 0 it is also read as the
+ * starting values: the sweep then accumulates from the first period and goes
+ * around the period again until the wrap plane changes by at most seed_tol
+ * times its largest intensity over one period (per tile; default 1e-6) --
+ * the paper's convergence test, which assumes the seed is close (the
+ * previous solve of a slowly changing atmosphere). Without seed_in the wrap
+ * converges from I = S with the rigorous seed-error bound. */
 typedef struct {
     rts_bc_kind bottom, top;
     const void *bottom_I;  /* [B][n_up][Ny][Nx] when bottom == RTS_BC_EXPLICIT */
     const void *top_I;     /* [B][n_down][Ny][Nx] when top == RTS_BC_EXPLICIT */
+    void *wrap_seed;       /* optional warm start, in/out (see above); NULL = none */
+    int seed_in;           /* read wrap_seed as the starting values */
+    double seed_tol;       /* relative change that ends a warm-started wrap (0 = 1e-6) */
 } rts_boundary;
+
 
 typedef struct rts_handle rts_handle;
 
@@ -244,6 +263,10 @@ const char *rts_last_error(rts_handle *h);
 
 /* Number of upward directions of the handle's quadrature. */
 int rts_num_up(rts_handle *h);
+
+/* Elements (floats) of the warm-start buffer of rts_boundary.wrap_seed for
+ * this handle (0 when the handle has no register sweep). */
+long long rts_wrap_seed_elems(rts_handle *h);
 
 void rts_destroy(rts_handle *h);
 

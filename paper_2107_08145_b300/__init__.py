@@ -61,7 +61,8 @@ class FrontTable(C.Structure):
 
 
 class Boundary(C.Structure):
-    _fields_ = [("bottom", C.c_int), ("top", C.c_int), ("bottom_I", C.c_void_p), ("top_I", C.c_void_p)]
+    _fields_ = [("bottom", C.c_int), ("top", C.c_int), ("bottom_I", C.c_void_p), ("top_I", C.c_void_p),
+                ("wrap_seed", C.c_void_p), ("seed_in", C.c_int), ("seed_tol", C.c_double)]
 
 
 _lib = None
@@ -71,7 +72,7 @@ EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "
            "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint",
            "rts_create_batched", "rts_solve_batched", "rts_batched_layout", "rts_graph_create", "rts_graph_launch",
            "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait", "rts_device_code_version",
-           "rts_front_end", "rts_scatter_solve")
+           "rts_front_end", "rts_scatter_solve", "rts_wrap_seed_elems")
 
 
 def library_path() -> str:
@@ -135,6 +136,8 @@ def load(build_if_missing: bool = True):
     L.rts_scatter_solve.argtypes = [vp, vp, vp, vp, vp, C.POINTER(Boundary), C.c_int, C.c_double,
                                     C.POINTER(C.c_int), vp, vp, vp, vp]
     L.rts_scatter_solve.restype = C.c_int
+    L.rts_wrap_seed_elems.argtypes = [vp]
+    L.rts_wrap_seed_elems.restype = C.c_longlong
     L.rts_destroy.argtypes = [vp]
     L.rts_destroy.restype = None
     L.rts_solve_noalloc.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp,
@@ -238,9 +241,17 @@ class Solver:
                 setattr(b, side + "_I", t.data_ptr())
         return b, keep
 
-    def solve(self, chi, S, bottom="equal_s", top="zero", check=True, out=None):
+    def wrap_seed_elems(self):
+        """Floats of the warm-start buffer (rts_wrap_seed_elems)."""
+        return int(self._L.rts_wrap_seed_elems(self._h))
+
+    def solve(self, chi, S, bottom="equal_s", top="zero", check=True, out=None, wrap_seed=None, seed_in=False,
+              seed_tol=0.0):
         """chi, S: CUDA tensors [B, nz, ny, nx] in the solver's dtype.
 
+        wrap_seed: optional float32 CUDA tensor of wrap_seed_elems() elements,
+        written with the converged wrap planes; with seed_in=True also read
+        as the warm start (rts_boundary.wrap_seed).
         Returns dict(I_top [B,n_up,ny,nx], J [nz,ny,nx], F [3,nz,ny,nx], Q [nz,ny,nx])."""
         torch = self.torch
         shape = (self.nbands, self.nz, self.ny, self.nx)
@@ -255,6 +266,13 @@ class Solver:
                        F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
                        Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
         b, keep = self._bc(bottom, top)
+        if wrap_seed is not None:
+            if (not wrap_seed.is_cuda or wrap_seed.dtype != torch.float32 or not wrap_seed.is_contiguous()
+                    or wrap_seed.numel() != self.wrap_seed_elems()):
+                raise ValueError(f"wrap_seed must be a contiguous CUDA float32 tensor of {self.wrap_seed_elems()}")
+            b.wrap_seed = wrap_seed.data_ptr()
+            b.seed_in = 1 if seed_in else 0
+            b.seed_tol = seed_tol
         rc = self._L.rts_solve(self._h, _ptr(chi), _ptr(S), C.byref(b), _ptr(out.get("I_top")), _ptr(out.get("J")),
                                _ptr(out.get("F")), _ptr(out.get("Q")))
         self._err(rc)

@@ -172,7 +172,7 @@ void unit_extents(int axis, long long nx, long long ny, long long nz, int &NP, i
 
 struct PlanOut {
     int nunits = 0, ntiles = 0, max_ntiles = 0;
-    long long halo_elems = 0;
+    long long halo_elems = 0, seed_elems = 0;
     bool has_x = false;
 };
 
@@ -235,6 +235,11 @@ bool plan_units(const DirGeo *geo, const int *udx, const double *n, const double
                     U.up[sl] = geo[d].up;
                     U.udx[sl] = udx[d];
                 }
+                U.seed_off = -1;
+                if (U.wrap) {  // the unit's wrap plane in the warm-start buffer
+                    U.seed_off = po.seed_elems;
+                    po.seed_elems += (long long)U.NP * U.NQ * rts::MAXD;
+                }
                 if (po.ntiles + U.ntiles > max_tiles) return false;
                 for (int t = 0; t < U.ntiles; ++t) unit_of_tile[po.ntiles + t] = po.nunits;
                 po.ntiles += U.ntiles;
@@ -281,6 +286,7 @@ struct rts_handle {
     int adj_tq = 0, adj_maxr = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
     // register-resident FP32 forward sweep (sweep_reg.cuh): its own tiling of the same units
     bool use_reg = false;
+    long long seed_elems = 0;     // warm-start buffer of the register sweep
     std::vector<rts::SweepUnit> reg_units;
     std::vector<int> reg_unit_of_tile;
     rts::SweepUnit *d_reg_units = nullptr;
@@ -892,6 +898,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
             h->reg_smem = tr.smem;
             h->reg_carveout = carveout_percent(tr.blocks, tr.smem);
             h->reg_grid = std::min(pr.ntiles, tr.blocks * nsm);
+            h->seed_elems = pr.seed_elems;
             halo_elems = std::max(halo_elems, pr.halo_elems);
             flag_tiles = std::max(flag_tiles, 2 * pr.ntiles);
             max_nt = std::max(max_nt, pr.max_ntiles);
@@ -1101,6 +1108,11 @@ static rts::SweepArgs<T> sweep_args(rts_handle *h, const void *chi, const void *
     a.unit_tacc = h->d_unit_tacc;
     a.tol = (float)h->opt.wrap_tol;
     a.max_periods = h->opt.max_wrap_iters;
+    if (bc && bc->wrap_seed) {
+        a.seed = (T *)bc->wrap_seed;
+        a.seed_in = bc->seed_in;
+        a.seed_tol = bc->seed_tol > 0 ? (float)bc->seed_tol : 1e-6f;
+    }
     a.timeout_ns = (unsigned long long)(h->opt.timeout_s * 1e9);
     return a;
 }
@@ -1206,6 +1218,9 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
 static rts_status check_bc(rts_handle *h, const rts_boundary *bc)
 {
     if (!bc) return RTS_OK;
+    if (bc->wrap_seed && (!h->use_reg || h->batched))
+        return fail(h, RTS_EINVAL, "the warm start (wrap_seed) needs the FP32 register sweep of a single-grid handle");
+    if (bc->wrap_seed && !(bc->seed_tol >= 0)) return fail(h, RTS_EINVAL, "seed_tol must be >= 0");
     if (bc->bottom < RTS_BC_ZERO || bc->bottom > RTS_BC_EXPLICIT || bc->top < RTS_BC_ZERO || bc->top > RTS_BC_EXPLICIT)
         return fail(h, RTS_EINVAL, "unknown boundary kind");
     if (bc->bottom == RTS_BC_EXPLICIT && !bc->bottom_I) return fail(h, RTS_EINVAL, "bottom_I is NULL");
@@ -1402,6 +1417,7 @@ rts_status rts_adjoint(rts_handle *h, const void *chi, const void *S, const rts_
     if (!chi || !S || !g_logchi || !g_S) return fail(h, RTS_EINVAL, "chi, S, g_logchi and g_S must not be NULL");
     if (g_logchi == g_S || g_logchi == chi || g_logchi == S || g_S == chi || g_S == S)
         return fail(h, RTS_EINVAL, "gradient outputs must not alias the inputs or each other");
+    if (bc && bc->wrap_seed) return fail(h, RTS_EINVAL, "rts_adjoint takes no warm start");
     rts_status s = check_bc(h, bc);
     if (s) return s;
     switch (h->opt.prec) {
@@ -1561,6 +1577,8 @@ rts_status rts_check(rts_handle *h)
         return fail(h, RTS_ENOCONV, "periodic wrap not converged within %d periods", h->opt.max_wrap_iters);
     return RTS_OK;
 }
+
+long long rts_wrap_seed_elems(rts_handle *h) { return h && h->use_reg ? h->seed_elems : 0; }
 
 int rts_device_code_version(void)
 {

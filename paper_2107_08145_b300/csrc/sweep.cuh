@@ -79,6 +79,8 @@ struct SweepUnit {
     double ds[MAXD];            // path length to the upwind plane
     double cJ[MAXD];            // w_d
     double cF[3][MAXD];         // 4 pi w_d n_d
+    long long seed_off;         // x/y groups: element offset of the unit's wrap plane [NQ][NP][4] in the
+                                // warm-start buffer (SweepArgs::seed)
 };
 
 template <typename T>
@@ -117,6 +119,14 @@ struct SweepArgs {
     int *unit_tacc;             // per unit: first accumulated step
     float tol;
     int max_periods;
+    // warm start of the periodic wrap (register sweep, x/y groups): per unit the
+    // intensities of its wrap plane (the plane upwind of the first swept one),
+    // written with the converged values; with seed_in they are also the
+    // starting values, and periods are swept until that plane changes by at
+    // most seed_tol (relative) over a period
+    T *seed;
+    int seed_in;
+    float seed_tol;
     unsigned long long timeout_ns;
 };
 

@@ -171,7 +171,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         return EDG + ((((slot * NW + w) * 2 + side) * TQ) + (k - 1)) * 3;
     };
 
-    __shared__ float s_wmax[32];
+    __shared__ float s_wmax[32], s_imax[32];
     __shared__ int s_ctl[4];                     // 0 abort, 1 wrap decision for the next plane
     __shared__ int s_q[RWS];                     // grid row of shared row k, -1 outside
 
@@ -208,6 +208,10 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     const bool has_upper = qper || r < ntl - 1;
     // the last grid row (q = NQ - 1) of an x/y group: shared row kb of this tile, else 0
     const int kb = (wrap && q0 + nrows == NQ) ? nrows : 0;
+    // warm start (x/y groups): the unit's wrap plane in the caller's buffer
+    float *const sbuf = (wrap && a.seed) ? a.seed + Ug->seed_off : nullptr;
+    const bool seeded = sbuf != nullptr && a.seed_in != 0;
+    const int m_seed = plane_of(-1, NM, sa);
 
     // chi and S of plane t into shared slot `slot`: record c + 1 of row k holds
     // {chi(c), chi(c+H), S(c), S(c+H)}; record 0 is pair H-1 swapped and record
@@ -380,6 +384,8 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                             natural_ij(axis, c + hh * H, q, m, i, j);
                             val = reg_bc(up ? kind_up : kind_dn, up ? a.bc_up + Ug->top_off : a.bc_dn + Ug->dn_off,
                                          Ug->udx[d], unx, uny, i, j, sv[hh]);
+                        } else if (seeded) {  // the caller's warm start (no bound is kept)
+                            val = sbuf[((long long)q * NP + c + hh * H) * 4 + d];
                         } else {  // seed of the periodic wrap: I = S, unit bound
                             val = sv[hh];
                             g[d >> 1][hh] = 1.f;
@@ -399,7 +405,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     __syncthreads();
 
     // z groups: the boundary plane tp is the first accumulated plane
-    int t_acc = wrap ? -1 : 0;
+    int t_acc = (wrap && !seeded) ? -1 : 0;
     const int warm_cap = a.max_periods * NM + a.L;
     const int dec_thread = NT > 32 ? 32 : 0;
 
@@ -424,7 +430,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     auto plane_step = [&](auto ACCF, int t, int m) __attribute__((always_inline)) -> int {
         constexpr bool ACC = decltype(ACCF)::value;
         constexpr bool BND = !ACC;  // bounds only during the warm-up (x/y groups)
-        const bool last = ACC && (t - t_acc == NM - 1);
+        const bool last = ACC && !seeded && (t - t_acc == NM - 1);
         const int es = (t - 1) & 1;  // shared edge records of the previous plane
 
         const float4 *XP = XS + s_prev * RWS * RR + c + 1;   // previous plane, own record
@@ -653,6 +659,60 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         } else if (lane == 0) {
             s_ctl[0] = 1;
         }
+        // the wrap plane of an accumulated period: kept for the next solve and,
+        // when seeded, compared with the previous period's (the paper's
+        // iteration of boundary intensities to a tolerance)
+        if constexpr (ACC) {
+            if (sbuf && m == m_seed) {
+                float dmax = 0.f, imax = 0.f;
+                if (act && ok) {
+#pragma unroll
+                    for (int k = 1; k <= TQ; ++k) {
+                        if (k > nrows) break;
+                        const long long o = ((long long)(q0 + k - 1) * NP + c) * 4;
+#pragma unroll
+                        for (int d = 0; d < MAXD; ++d) {
+                            if (!((actm >> d) & 1)) continue;
+                            const float v0 = Ip[k][d].x, v1 = Ip[k][d].y;
+                            if (seeded) {
+                                dmax = fmaxf(dmax, fmaxf(fabsf(v0 - sbuf[o + d]), fabsf(v1 - sbuf[o + 4 * H + d])));
+                                imax = fmaxf(imax, fmaxf(fabsf(v0), fabsf(v1)));
+                            }
+                            sbuf[o + d] = v0;
+                            sbuf[o + 4 * H + d] = v1;
+                        }
+                    }
+                }
+                if (seeded) {
+                    for (int o = 16; o; o >>= 1) {
+                        dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                        imax = fmaxf(imax, __shfl_xor_sync(0xffffffffu, imax, o));
+                    }
+                    if (lane == 0) {
+                        s_wmax[warp] = dmax;
+                        s_imax[warp] = imax;
+                    }
+                }
+            }
+            // seeded: the decision on period p, L planes after its wrap plane
+            const int tp_end = t - a.L - (NM - 1);
+            if (seeded && tid == dec_thread && tp_end >= 0 && tp_end % NM == 0) {
+                const int p = tp_end / NM;
+                const int slot = p % a.R;
+                const unsigned want = (unsigned)ntl * (unsigned)(p / a.R + 1);
+                bool okd = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
+                if (okd) {
+                    const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
+                    if ((unsigned)(v >> 32) != (unsigned)(p + 1)) {
+                        atomicOr(a.status, ST_BADARG);  // ring overrun: never expected
+                        okd = false;
+                    } else {
+                        s_ctl[1] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.seed_tol ? 1 : 0;
+                    }
+                }
+                if (!okd) s_ctl[0] = 1;
+            }
+        }
         if constexpr (BND) {
             float gmax = 0.f;
             if (act) {
@@ -692,16 +752,34 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 atomicMax(a.gmax + (long long)uidx * a.R + slot, pv);
                 red_release_add(a.gcnt + (long long)uidx * a.R + slot, 1u);
             }
+        } else {
+            if (seeded && m == m_seed && tid == 0) {  // this tile's relative change over period p
+                float dm = 0.f, im = 0.f;
+                for (int w = 0; w < NW; ++w) {
+                    dm = fmaxf(dm, s_wmax[w]);
+                    im = fmaxf(im, s_imax[w]);
+                }
+                const float rel = im > 0.f ? dm / im : (dm > 0.f ? 1.f : 0.f);
+                const int p = (t - (NM - 1)) / NM;
+                const int slot = p % a.R;
+                const unsigned long long pv = ((unsigned long long)(unsigned)(p + 1) << 32) | __float_as_uint(rel);
+                atomicMax(a.gmax + (long long)uidx * a.R + slot, pv);
+                red_release_add(a.gcnt + (long long)uidx * a.R + slot, 1u);
+            }
         }
         const int sp_old = s_prev;
         s_prev = s_cur;
         s_cur = s_next;
         s_next = sp_old;
+        if (seeded && ACC && s_ctl[1]) {  // converged (decided before the barrier): stop after this plane
+            if (r == 0 && tid == 0) a.unit_tacc[uidx] = t + 1 - NM;
+            return 1;
+        }
         return last ? 1 : 0;
     };
 
     int t = t_first;
-    if (wrap) {
+    if (wrap && !seeded) {
         for (;; ++t) {
             if (s_ctl[1]) {  // decision taken during the previous plane
                 t_acc = t;
@@ -720,6 +798,10 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         }
     }
     for (;; ++t) {
+        if (seeded && t >= warm_cap) {  // the warm start did not converge within max_periods
+            if (tid == 0) atomicOr(a.status, ST_NOCONV);
+            break;
+        }
         const int rc = plane_step(Flag<true>{}, t, plane_of(t, NM, sa));
         if (rc == 2) {
             cp_async_wait_all();
