@@ -167,12 +167,21 @@ def _dist():
     return ws, rank, local
 
 
-def _traffic_from_profile(prec, grid, tile_rows):
-    """DRAM bytes per sweep launch from the committed ncu summary
-    (profiles/sweep_rts288x4_dram.md, "- key: value" lines), or None if the
-    sweep source changed since the counters were taken or the run is not the
+SWEEP_PROFILES = {  # sweep kernel -> (committed DRAM summary, the source its counters were taken from)
+    2: ("sweep_reg_rts288x4_dram.md", "sweep_reg.cuh"),
+    1: ("sweep_rts288x4_dram.md", "sweep.cuh"),
+}
+
+
+def _traffic_from_profile(prec, grid, tile_rows, kernel):
+    """DRAM bytes per sweep launch from the committed ncu summary of the
+    sweep kernel that ran ("- key: value" lines), or None if that kernel's
+    source changed since the counters were taken or the run is not the
     summary's workload (grid, precision, tile height)."""
-    path = os.path.join(ROOT, "profiles", "sweep_rts288x4_dram.md")
+    if kernel not in SWEEP_PROFILES:
+        return None
+    name, src_name = SWEEP_PROFILES[kernel]
+    path = os.path.join(ROOT, "profiles", name)
     rec = {}
     try:
         for line in open(path):
@@ -181,7 +190,7 @@ def _traffic_from_profile(prec, grid, tile_rows):
                 rec[k.strip()] = v.strip()
     except OSError:
         return None
-    src = os.path.join(ROOT, "paper_2107_08145_b300", "csrc", "sweep.cuh")
+    src = os.path.join(ROOT, "paper_2107_08145_b300", "csrc", src_name)
     digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     if rec.get("sweep_source_sha256_16") != digest or rec.get("precision") != prec:
         return None
@@ -476,11 +485,15 @@ def run_ours(args):
     sweep_ms = st["ms_sweep"]
     alg = sweep_algorithmic_bytes(prec)
     achieved = alg / (sweep_ms * 1e-3) / 1e9
-    roofline = {"kernel": "sweep_kernel (persistent tile-DAG sweep, all bands and groups)",
+    kname = {2: "sweep_reg_kernel (register-resident persistent tile-DAG sweep, all bands and groups)",
+             1: "sweep_kernel (shared-memory persistent tile-DAG sweep, all bands and groups)"}.get(
+                 st["sweep_kernel"], "sweep")
+    roofline = {"kernel": kname,
                 "bound": "hbm", "achieved": round(achieved, 2), "peak": hbm if hbm else 6400.0,
                 "unit": "GB/s", "frac": round(achieved / (hbm if hbm else 6400.0), 5),
                 "peak_source": "of measured" if hbm else "of fallback",
-                "traffic": _traffic_from_profile(prec, (NX, NY, NZ), TILE_ROWS), "algorithmic_bytes_per_launch": alg,
+                "traffic": _traffic_from_profile(prec, (NX, NY, NZ), TILE_ROWS, st["sweep_kernel"]),
+                "algorithmic_bytes_per_launch": alg,
                 "sweep_ms_mean": round(sweep_ms, 4), "launches_timed": st["timed_solves"]}
     phases = {k: round(st[k], 4) for k in ("ms_transpose", "ms_sweep", "ms_reduce", "ms_qstep")}
 

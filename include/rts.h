@@ -417,6 +417,34 @@ rts_status rts_front_end(const rts_grid *g, const rts_front_table *tab, rts_prec
                          const void *T_mhd, const void *rho_mhd, void *chi, void *S, void *stream,
                          char *err, size_t errlen);
 
+/* ---------------------------------------------------------------------------
+ * Spatial decomposition (paper Sect. 2 and 5.1: the domain is split into
+ * sub-domains; each integrates its rays from the boundary intensities of the
+ * previous iteration, and the boundary intensities are iterated until a
+ * global error is below a tolerance -- 3 to 4 iterations in the paper). A
+ * one-GPU form of that scheme: the grid is cut into nblocks slabs of levels
+ * (the periodic x, y wrap stays inside every slab's solve). Slab k owns
+ * levels [a_k, b_k) (a_k = k nz / nblocks) and is solved on [a_k - 1, b_k + 1)
+ * (a ghost level towards each neighbour) with explicit boundary intensities:
+ * its bottom layer takes the upward intensities slab k-1 computed at level
+ * a_k - 1 in the previous iteration, its top layer the downward intensities
+ * slab k+1 computed at level b_k (the first iteration starts from I = S).
+ * Iterations end when the largest change of J over the grid is <= tol times
+ * max J (the global J criterion). The slabs then hold the undecomposed
+ * solution: J, F and Q_rad of every owned level are those of rts_solve, and
+ * I_top is the top slab's. FP32 modes only (the interface intensities are
+ * read from the register sweep's slot partials); options as rts_create
+ * (only RTS_FLAG_TIMING among the flags). rts_solve_decomposed synchronises
+ * once per iteration (the convergence test); J must be given. */
+typedef struct rts_decomp rts_decomp;
+rts_status rts_create_decomposed(rts_decomp **d, const rts_grid *g, int nbands, int nblocks,
+                                 const rts_quadrature *q, const rts_options *opt);
+rts_status rts_solve_decomposed(rts_decomp *d, const void *chi, const void *S, const rts_boundary *bc,
+                                double tol, int max_iter, int *iters,
+                                void *I_top, double *J, double *F, double *Q_rad);
+const char *rts_decomposed_last_error(rts_decomp *d);
+void rts_destroy_decomposed(rts_decomp *d);
+
 #ifdef __cplusplus
 }
 #endif

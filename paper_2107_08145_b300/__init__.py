@@ -72,7 +72,8 @@ EXPORTS = ("rts_default_options", "rts_create", "rts_solve", "rts_solve_host", "
            "rts_get_stats", "rts_last_error", "rts_num_up", "rts_destroy", "rts_solve_noalloc", "rts_adjoint",
            "rts_create_batched", "rts_solve_batched", "rts_batched_layout", "rts_graph_create", "rts_graph_launch",
            "rts_graph_destroy", "rts_autotune", "rts_solve_host_async", "rts_host_wait", "rts_device_code_version",
-           "rts_front_end", "rts_scatter_solve", "rts_wrap_seed_elems")
+           "rts_front_end", "rts_scatter_solve", "rts_wrap_seed_elems", "rts_create_decomposed",
+           "rts_solve_decomposed", "rts_decomposed_last_error", "rts_destroy_decomposed")
 
 
 def library_path() -> str:
@@ -143,6 +144,16 @@ def load(build_if_missing: bool = True):
     L.rts_solve_noalloc.argtypes = [C.POINTER(Grid), C.c_int, C.c_int, vp, vp, vp, vp, vp, vp, vp,
                                     C.c_char_p, C.c_size_t]
     L.rts_solve_noalloc.restype = C.c_int
+    L.rts_create_decomposed.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Grid), C.c_int, C.c_int,
+                                        C.POINTER(Quadrature), C.POINTER(Options)]
+    L.rts_create_decomposed.restype = C.c_int
+    L.rts_solve_decomposed.argtypes = [vp, vp, vp, C.POINTER(Boundary), C.c_double, C.c_int, C.POINTER(C.c_int),
+                                       vp, vp, vp, vp]
+    L.rts_solve_decomposed.restype = C.c_int
+    L.rts_decomposed_last_error.argtypes = [vp]
+    L.rts_decomposed_last_error.restype = C.c_char_p
+    L.rts_destroy_decomposed.argtypes = [vp]
+    L.rts_destroy_decomposed.restype = None
     _ = dp
     _lib = L
     return L
@@ -643,3 +654,73 @@ def front_end(T, rho, table, precision="fp32", shift=(-0.5, -0.5, -0.5), out=Non
         raise RTSError(rc, err.value.decode())
     out[0]._rts_keep = (lnk, lnB)  # the tables stay alive until the enqueued kernel has read them
     return out
+
+
+class DecomposedSolver:
+    """The grid cut into nblocks slabs of levels, iterated on their boundary
+    intensities until the global J criterion holds (rts_create_decomposed /
+    rts_solve_decomposed). FP32 modes only."""
+
+    def __init__(self, nx, ny, nz, nbands=1, nblocks=2, dx=1.0, dy=1.0, dz=1.0, precision="fp32", tau_switch=0.1,
+                 wrap_tol=0.0, max_wrap_iters=64, timeout_s=2.0, stream=None):
+        import torch
+
+        L = load()
+        self.torch = torch
+        self._L = L
+        self._h = C.c_void_p()
+        self.nx, self.ny, self.nz, self.nbands, self.nblocks = nx, ny, nz, nbands, nblocks
+        self.prec = _PREC[precision]
+        self.dtype = torch.float32
+        o = Options()
+        L.rts_default_options(C.byref(o))
+        o.prec = self.prec
+        o.tau_switch = tau_switch
+        o.wrap_tol = wrap_tol
+        o.max_wrap_iters = max_wrap_iters
+        o.timeout_s = timeout_s
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o.stream = C.c_void_p(stream.cuda_stream)
+        h = C.c_void_p()
+        rc = L.rts_create_decomposed(C.byref(h), C.byref(Grid(nx, ny, nz, dx, dy, dz)), nbands, nblocks, None,
+                                     C.byref(o))
+        if rc != RTS_OK:
+            msg = L.rts_decomposed_last_error(h).decode() if h.value else "rts_create_decomposed failed"
+            L.rts_destroy_decomposed(h)
+            raise RTSError(rc, msg)
+        self._h = h
+        self.n_up = 12
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value:
+                self._L.rts_destroy_decomposed(self._h)
+                self._h = C.c_void_p()
+        except Exception:
+            pass
+
+    def solve(self, chi, S, tol=1e-6, max_iter=32, out=None):
+        """chi, S: float32 CUDA tensors [B, nz, ny, nx]. Returns (outputs,
+        iterations), outputs as Solver.solve."""
+        torch = self.torch
+        shape = (self.nbands, self.nz, self.ny, self.nx)
+        for name, t in (("chi", chi), ("S", S)):
+            if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_cuda:
+                raise ValueError(f"{name} must be a CUDA float32 tensor {shape}")
+        chi = chi.contiguous()
+        S = S.contiguous()
+        if out is None:
+            dev = chi.device
+            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=torch.float32, device=dev),
+                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
+                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        it = C.c_int(0)
+        rc = self._L.rts_solve_decomposed(self._h, _ptr(chi), _ptr(S), None, tol, max_iter, C.byref(it),
+                                          _ptr(out.get("I_top")), _ptr(out.get("J")), _ptr(out.get("F")),
+                                          _ptr(out.get("Q")))
+        if rc != RTS_OK:
+            raise RTSError(rc, self._L.rts_decomposed_last_error(self._h).decode())
+        return out, it.value

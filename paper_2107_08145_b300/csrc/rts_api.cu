@@ -28,6 +28,7 @@
 #include "sweep.cuh"
 #include "kernels.h"
 #include "sweep_reg.cuh"
+#include "qfused.cuh"
 
 namespace {
 
@@ -316,6 +317,11 @@ struct rts_handle {
     unsigned long long *d_gmax = nullptr;
     rts::RedUnit *d_ru = nullptr;
     int *d_ru_begin = nullptr;
+    bool qf_ok = false;  // the register sweep's reduction (qfused.cuh) is used
+    size_t qr_smem = 0;
+    int qr_grid = 0, qr_max_nat = 0, qr_max_x = 0;
+    rts::RedUnit *d_qfu = nullptr;  // its units: per band the x groups first
+    int *d_qfb = nullptr;           // band begins [B+1], then the ends of each band's x groups [B]
     // adjoint scratch (RTS_FLAG_ADJOINT): lam0 [B][N][4] natural and
     // x-transposed, direct Q-step terms [B][2][N], and per checkpoint chunk of
     // at most chunk_units units: the checkpoint [u][N][STORE_CH*4] and the
@@ -934,6 +940,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_tacc = take(sizeof(int) * h->units.size());
     const size_t o_ru = take(sizeof(rts::RedUnit) * h->units.size());
     const size_t o_rub = take(sizeof(int) * (nbands + 1));
+    const size_t o_qfu = take(sizeof(rts::RedUnit) * h->units.size());
+    const size_t o_qfb = take(sizeof(int) * (2 * nbands + 1));
     const bool log_chi = (o.flags & RTS_FLAG_LOG_CHI) != 0;
     const size_t o_cexp = log_chi ? take((size_t)nbands * h->N * es) : 0;
     const bool scatter = (o.flags & RTS_FLAG_SCATTER) != 0;
@@ -996,6 +1004,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->d_unit_tacc = (int *)(base + o_tacc);
     h->d_ru = (rts::RedUnit *)(base + o_ru);
     h->d_ru_begin = (int *)(base + o_rub);
+    h->d_qfu = (rts::RedUnit *)(base + o_qfu);
+    h->d_qfb = (int *)(base + o_qfb);
     if (log_chi) h->d_chi_exp = base + o_cexp;
     if (scatter) {
         h->d_lstar = base + o_lstar;
@@ -1055,6 +1065,41 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * ru.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, rub.data(), sizeof(int) * rub.size(), cudaMemcpyHostToDevice));
     if (h->use_reg) {
+        // the streaming reduction of the register sweep's raw partials: per band the x groups first
+        {
+            std::vector<rts::RedUnit> qfu;
+            std::vector<int> qfb(2 * nbands + 1, 0);
+            for (int b = 0; b < nbands; ++b) {
+                qfb[b] = (int)qfu.size();
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int u = rub[b]; u < rub[b + 1]; ++u)
+                        if ((ru[u].axis == 0) == (pass == 0)) qfu.push_back(ru[u]);
+                int nxu = 0;
+                for (int u = rub[b]; u < rub[b + 1]; ++u) nxu += ru[u].axis == 0;
+                qfb[nbands + 1 + b] = qfb[b] + nxu;
+            }
+            qfb[nbands] = (int)qfu.size();
+            CUDA_TRY(h, cudaMemcpy(h->d_qfu, qfu.data(), sizeof(rts::RedUnit) * qfu.size(), cudaMemcpyHostToDevice));
+            CUDA_TRY(h, cudaMemcpy(h->d_qfb, qfb.data(), sizeof(int) * qfb.size(), cudaMemcpyHostToDevice));
+            for (int b = 0; b < nbands; ++b) {
+                h->qr_max_x = std::max(h->qr_max_x, qfb[nbands + 1 + b] - qfb[b]);
+                h->qr_max_nat = std::max(h->qr_max_nat, qfb[b + 1] - qfb[nbands + 1 + b]);
+            }
+            h->qr_smem = rts::qr_smem_bytes(h->qr_max_nat, h->qr_max_x);
+            int per_sm = 0;
+            const long long qr_tiles = (long long)((nx + rts::QR_TI - 1) / rts::QR_TI) *
+                                       ((ny + rts::QR_TJ - 1) / rts::QR_TJ) * nz * nbands;
+            if (h->qr_smem <= 113 * 1024 && qr_tiles < (1LL << 31) - (1LL << 20) &&
+                cudaFuncSetAttribute(rts::qf_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)h->qr_smem) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rts::qf_reduce_kernel, rts::QR_NT,
+                                                              h->qr_smem) == cudaSuccess &&
+                per_sm > 0) {
+                h->qr_grid = per_sm * nsm;
+                h->qf_ok = true;
+            }
+            cudaGetLastError();
+        }
         for (size_t u = 0; u < h->reg_units.size(); ++u) h->reg_units[u].partial = h->units[u].partial;
         CUDA_TRY(h, cudaMemcpy(h->d_reg_units, h->reg_units.data(), sizeof(rts::SweepUnit) * h->reg_units.size(),
                                cudaMemcpyHostToDevice));
@@ -1189,7 +1234,23 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     kernels += 1;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
-    if (J || F || Q || reduce_only) {
+    if (reg && h->qf_ok && !reduce_only && (J || F || Q)) {
+        // the register sweep's raw partials: the streaming reduction into
+        // double-float J_b, F_b, then the double-float Q step (both FP32 modes)
+        rts::QParams P;
+        P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
+        P.inv2dx = 0.5 / g.dx; P.inv2dy = 0.5 / g.dy; P.inv2dz = 0.5 / g.dz; P.invdz = 1.0 / g.dz;
+        P.thin = std::min(g.dx, std::min(g.dy, g.dz)) / h->opt.tau_switch;
+        rts::df32 *jf = (rts::df32 *)h->d_JF;
+        rts::qf_reduce_kernel<<<h->qr_grid, dim3(rts::QR_TI, rts::QR_RY), h->qr_smem, st>>>(
+            h->d_qfu, h->d_qfb, g.nx, g.ny, g.nz, B, h->qr_max_nat, h->qr_max_x, jf);
+        CUDA_TRY(h, cudaGetLastError());
+        if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
+        dim3 rb(32, 8), qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
+        rts::qstep_kernel<float, rts::df32><<<qg, rb, 0, st>>>(jf, (const float *)chi, (const float *)S, P, J, F, Q);
+        CUDA_TRY(h, cudaGetLastError());
+        kernels += 2;
+    } else if (J || F || Q || reduce_only) {
         dim3 rb(32, 8);
         rts::QParams P;
         P.nx = g.nx; P.ny = g.ny; P.nz = g.nz; P.nbands = B;
@@ -2393,3 +2454,304 @@ extern "C" rts_status rts_autotune(int nsub, const rts_grid *grids, int nbands, 
     if (ncand) *ncand = std::min(n, 8);
     return *best_tile_rows ? RTS_OK : RTS_ECUDA;
 }
+
+// ===========================================================================
+// Spatial decomposition (the paper's scheme, Sect. 2 and 5.1: the domain is
+// split into sub-domains, each integrates its rays from the boundary
+// intensities of the previous iteration, and the boundary intensities are
+// iterated until a global error is below a tolerance). Here the sub-domains
+// are slabs of levels on one GPU (the horizontal periodic wrap stays inside
+// every slab's solve). Slab k owns levels [a_k, b_k) and is solved on
+// [a_k - 1, b_k + 1) (one ghost level each side where it has a neighbour):
+// its bottom layer takes the upward intensities that slab k-1 computed at
+// level a_k - 1, its top layer the downward intensities that slab k+1
+// computed at level b_k, both from the previous iteration (block Jacobi).
+// Those intensities are gathered from the neighbours' raw slot partials (the
+// register sweep stores every ray's intensity at every point), and with a
+// ghost level on each side every owned level sees the same neighbours as in
+// the undecomposed solve, so J, F and Q_rad of the owned levels converge to
+// the undecomposed values. Convergence: the largest change of J between two
+// iterations, relative to max J (the paper's global J criterion).
+// ===========================================================================
+
+namespace {
+
+struct GatherEnt {
+    const float *part;   // the unit's raw partials [N][4] in its layout
+    long long sQ, sM;
+    int axis, slot, band, dir;
+};
+
+// intensity of every gathered (unit, slot) at grid level `level` of a slab,
+// into out[band][dir][j][i] (the layout of the explicit boundary arrays)
+__global__ void __launch_bounds__(256) gather_level_kernel(const GatherEnt *__restrict__ ents, int nx, int ny,
+                                                            int level, int ndir_sel, float *__restrict__ out)
+{
+    const GatherEnt e = ents[blockIdx.y];
+    const long long ij = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (ij >= (long long)nx * ny) return;
+    const int i = (int)(ij % nx), j = (int)(ij / nx);
+    int p, q, m;
+    if (e.axis == 2) { p = i; q = j; m = level; }
+    else if (e.axis == 1) { p = i; q = level; m = j; }
+    else { p = j; q = level; m = i; }
+    const float v = e.part[((long long)m * e.sM + (long long)q * e.sQ + p) * 4 + e.slot];
+    out[(((long long)e.band * ndir_sel + e.dir) * ny + j) * nx + i] = v;
+}
+
+// largest |a - b| and |a| over n values (atomic maxima of their float bits)
+__global__ void __launch_bounds__(256) change_kernel(const double *__restrict__ a, const double *__restrict__ b,
+                                                      long long n, unsigned *out)
+{
+    float d = 0.f, m = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        d = fmaxf(d, (float)fabs(a[i] - b[i]));
+        m = fmaxf(m, (float)fabs(a[i]));
+    }
+    for (int o = 16; o; o >>= 1) {
+        d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, __float_as_uint(d));
+        atomicMax(out + 1, __float_as_uint(m));
+    }
+}
+
+}  // namespace
+
+struct rts_decomp {
+    rts_grid g{};
+    int B = 0, n_up = 0, n_dn = 0, nblk = 0;
+    std::vector<rts_handle *> blk;
+    std::vector<int> lo, hi, a, b;   // slab grid [lo, hi) and owned levels [a, b)
+    void *mem = nullptr;
+    std::vector<float *> chi, S;       // per slab inputs [B][hi-lo][N2]
+    std::vector<double *> J, F, Q;     // per slab outputs
+    std::vector<float *> up[2], dn[2]; // per interface k (between slab k and k+1), double-buffered
+    std::vector<GatherEnt *> ents_up, ents_dn;  // per slab: its rising / descending (unit, slot) entries
+    std::vector<int> nent_up, nent_dn;
+    double *Jprev = nullptr;
+    unsigned *dmax = nullptr;
+    cudaStream_t stream = nullptr;
+    char err[512] = {0};
+};
+
+extern "C" {
+
+rts_status rts_create_decomposed(rts_decomp **out, const rts_grid *g, int nbands, int nblocks,
+                                 const rts_quadrature *q, const rts_options *opt)
+{
+    if (!out) return RTS_EINVAL;
+    *out = nullptr;
+    rts_decomp *d = new (std::nothrow) rts_decomp();
+    if (!d) return RTS_ENOMEM;
+    *out = d;
+    auto bad = [&](rts_status s, const char *m) {
+        snprintf(d->err, sizeof(d->err), "%s", m);
+        return s;
+    };
+    rts_options o;
+    if (opt) o = *opt;
+    else rts_default_options(&o);
+    if (!g || nbands < 1 || nblocks < 1) return bad(RTS_EINVAL, "grid, nbands >= 1 and nblocks >= 1 are needed");
+    if (o.prec == RTS_FP64) return bad(RTS_EINVAL, "the decomposed solve needs an FP32 mode (raw slot partials)");
+    if (g->nz < 2 * nblocks) return bad(RTS_EINVAL, "every slab needs at least 2 levels of its own");
+    if (o.flags & ~RTS_FLAG_TIMING) return bad(RTS_EINVAL, "the decomposed solve takes only RTS_FLAG_TIMING");
+    o.sweep_kernel = RTS_SWEEP_REGISTER;
+    d->g = *g;
+    d->B = nbands;
+    d->nblk = nblocks;
+    d->stream = (cudaStream_t)o.stream;
+    const long long N2 = (long long)g->nx * g->ny;
+    for (int k = 0; k < nblocks; ++k) {
+        d->a.push_back((int)((long long)g->nz * k / nblocks));
+        d->b.push_back((int)((long long)g->nz * (k + 1) / nblocks));
+        d->lo.push_back(std::max(d->a[k] - 1, 0));
+        d->hi.push_back(std::min(d->b[k] + 1, g->nz));
+        rts_grid gk = *g;
+        gk.nz = d->hi[k] - d->lo[k];
+        rts_handle *h = nullptr;
+        rts_status s = rts_create(&h, &gk, nbands, q, &o);
+        d->blk.push_back(h);
+        if (s) return bad(s, h ? h->err : "slab handle");
+    }
+    d->n_up = d->blk[0]->n_up;
+    d->n_dn = d->blk[0]->n_dn;
+    // device memory: slab inputs and outputs, interface arrays, the change check
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t at = off; off = round_up(off + bytes, 256); return at; };
+    std::vector<size_t> oc, os, oj, of, oq, oeu, oed;
+    for (int k = 0; k < nblocks; ++k) {
+        const long long nk = (long long)(d->hi[k] - d->lo[k]) * N2;
+        oc.push_back(take(sizeof(float) * nbands * nk));
+        os.push_back(take(sizeof(float) * nbands * nk));
+        oj.push_back(take(sizeof(double) * nk));
+        of.push_back(take(sizeof(double) * 3 * nk));
+        oq.push_back(take(sizeof(double) * nk));
+        oeu.push_back(take(sizeof(GatherEnt) * nbands * d->n_up));
+        oed.push_back(take(sizeof(GatherEnt) * nbands * d->n_dn));
+    }
+    std::vector<size_t> ou[2], odn[2];
+    for (int k = 0; k + 1 < nblocks; ++k)
+        for (int t = 0; t < 2; ++t) {
+            ou[t].push_back(take(sizeof(float) * nbands * d->n_up * N2));
+            odn[t].push_back(take(sizeof(float) * nbands * d->n_dn * N2));
+        }
+    const size_t oJp = take(sizeof(double) * N2 * g->nz);
+    const size_t omax = take(sizeof(unsigned) * 4);
+    if (cudaMalloc(&d->mem, off) != cudaSuccess) {
+        d->mem = nullptr;
+        return bad(RTS_ENOMEM, "cudaMalloc of the decomposition's buffers failed");
+    }
+    char *base = (char *)d->mem;
+    for (int k = 0; k < nblocks; ++k) {
+        d->chi.push_back((float *)(base + oc[k]));
+        d->S.push_back((float *)(base + os[k]));
+        d->J.push_back((double *)(base + oj[k]));
+        d->F.push_back((double *)(base + of[k]));
+        d->Q.push_back((double *)(base + oq[k]));
+        // the slab's (unit, slot) entries, rising and descending
+        rts_handle *h = d->blk[k];
+        std::vector<GatherEnt> eu, ed;
+        for (const rts::SweepUnit &U : h->units)
+            for (int sl = 0; sl < rts::MAXD; ++sl) {
+                if (!U.active[sl]) continue;
+                GatherEnt e;
+                e.part = (const float *)U.partial;
+                e.sQ = U.sQ;
+                e.sM = U.sM;
+                e.axis = U.axis;
+                e.slot = sl;
+                e.band = U.band;
+                e.dir = U.udx[sl];
+                (U.up[sl] ? eu : ed).push_back(e);
+            }
+        d->ents_up.push_back((GatherEnt *)(base + oeu[k]));
+        d->ents_dn.push_back((GatherEnt *)(base + oed[k]));
+        d->nent_up.push_back((int)eu.size());
+        d->nent_dn.push_back((int)ed.size());
+        if (eu.size() > (size_t)nbands * d->n_up || ed.size() > (size_t)nbands * d->n_dn)
+            return bad(RTS_EINVAL, "gather table overflow");
+        if (cudaMemcpy(d->ents_up[k], eu.data(), sizeof(GatherEnt) * eu.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(d->ents_dn[k], ed.data(), sizeof(GatherEnt) * ed.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bad(RTS_ECUDA, "copy of the gather tables failed");
+    }
+    for (int t = 0; t < 2; ++t)
+        for (int k = 0; k + 1 < nblocks; ++k) {
+            d->up[t].push_back((float *)(base + ou[t][k]));
+            d->dn[t].push_back((float *)(base + odn[t][k]));
+        }
+    d->Jprev = (double *)(base + oJp);
+    d->dmax = (unsigned *)(base + omax);
+    return RTS_OK;
+}
+
+const char *rts_decomposed_last_error(rts_decomp *d) { return d ? d->err : "null handle"; }
+
+void rts_destroy_decomposed(rts_decomp *d)
+{
+    if (!d) return;
+    for (rts_handle *h : d->blk) rts_destroy(h);
+    if (d->mem) cudaFree(d->mem);
+    delete d;
+}
+
+rts_status rts_solve_decomposed(rts_decomp *d, const void *chi, const void *S, const rts_boundary *bc, double tol,
+                                int max_iter, int *iters, void *I_top, double *J, double *F, double *Q_rad)
+{
+    if (!d || !d->mem) return RTS_EINVAL;
+    auto bad = [&](rts_status s, const char *m) {
+        snprintf(d->err, sizeof(d->err), "%s", m);
+        return s;
+    };
+    if (!chi || !S || !J) return bad(RTS_EINVAL, "chi, S and J must not be NULL (J carries the convergence test)");
+    if (max_iter < 1 || !(tol > 0)) return bad(RTS_EINVAL, "max_iter >= 1 and tol > 0 are needed");
+    if (bc && bc->wrap_seed) return bad(RTS_EINVAL, "the decomposed solve takes no warm start");
+    const rts_grid &g = d->g;
+    const long long N2 = (long long)g.nx * g.ny, N = N2 * g.nz;
+    cudaStream_t st = d->stream;
+#define DC_TRY(call)                                                                                         \
+    do {                                                                                                     \
+        cudaError_t e_ = (call);                                                                             \
+        if (e_ != cudaSuccess) return bad(RTS_ECUDA, cudaGetErrorString(e_));                                \
+    } while (0)
+    // the slabs' inputs: levels [lo, hi) of every band
+    for (int k = 0; k < d->nblk; ++k) {
+        const size_t w = sizeof(float) * (size_t)(d->hi[k] - d->lo[k]) * N2;
+        const size_t sp = sizeof(float) * (size_t)N;
+        DC_TRY(cudaMemcpy2DAsync(d->chi[k], w, (const float *)chi + d->lo[k] * N2, sp, w, d->B, cudaMemcpyDeviceToDevice, st));
+        DC_TRY(cudaMemcpy2DAsync(d->S[k], w, (const float *)S + d->lo[k] * N2, sp, w, d->B, cudaMemcpyDeviceToDevice, st));
+    }
+    int it = 0, cur = 0;
+    bool conv = false;
+    for (; it < max_iter && !conv; ++it) {
+        const int nxt = cur ^ 1;
+        for (int k = 0; k < d->nblk; ++k) {
+            rts_boundary b;
+            std::memset(&b, 0, sizeof(b));
+            b.bottom = bc ? bc->bottom : RTS_BC_EQUAL_S;
+            b.top = bc ? bc->top : RTS_BC_ZERO;
+            b.bottom_I = bc ? bc->bottom_I : nullptr;
+            b.top_I = bc ? bc->top_I : nullptr;
+            if (k > 0) {  // from slab k-1; the first iteration starts from I = S
+                b.bottom = it == 0 ? RTS_BC_EQUAL_S : RTS_BC_EXPLICIT;
+                b.bottom_I = d->up[cur][k - 1];
+            }
+            if (k + 1 < d->nblk) {
+                b.top = it == 0 ? RTS_BC_EQUAL_S : RTS_BC_EXPLICIT;
+                b.top_I = d->dn[cur][k];
+            }
+            rts_status s = rts_solve(d->blk[k], d->chi[k], d->S[k], &b, k + 1 == d->nblk ? I_top : nullptr, d->J[k],
+                                     d->F[k], d->Q[k]);
+            if (s) return bad(s, d->blk[k]->err);
+            // the intensities the neighbours take next iteration
+            const unsigned gx = (unsigned)((N2 + 255) / 256);
+            if (k + 1 < d->nblk && d->nent_up[k] > 0)  // rising, at level b_k - 1 (slab k+1's bottom layer)
+                gather_level_kernel<<<dim3(gx, (unsigned)d->nent_up[k]), 256, 0, st>>>(
+                    d->ents_up[k], g.nx, g.ny, d->b[k] - 1 - d->lo[k], d->n_up, d->up[nxt][k]);
+            if (k > 0 && d->nent_dn[k] > 0)  // descending, at level a_k (slab k-1's top layer)
+                gather_level_kernel<<<dim3(gx, (unsigned)d->nent_dn[k]), 256, 0, st>>>(
+                    d->ents_dn[k], g.nx, g.ny, d->a[k] - d->lo[k], d->n_dn, d->dn[nxt][k - 1]);
+            DC_TRY(cudaGetLastError());
+            // the owned levels of J
+            DC_TRY(cudaMemcpyAsync(J + d->a[k] * N2, d->J[k] + (d->a[k] - d->lo[k]) * N2,
+                                   sizeof(double) * (size_t)(d->b[k] - d->a[k]) * N2, cudaMemcpyDeviceToDevice, st));
+        }
+        // the global J criterion: max |J - J_prev| <= tol max |J|
+        DC_TRY(cudaMemsetAsync(d->dmax, 0, sizeof(unsigned) * 2, st));
+        change_kernel<<<(unsigned)std::min<long long>((N + 255) / 256, 148LL * 8), 256, 0, st>>>(J, d->Jprev, N,
+                                                                                                 d->dmax);
+        DC_TRY(cudaGetLastError());
+        unsigned mx[2] = {0, 0};
+        DC_TRY(cudaMemcpyAsync(mx, d->dmax, sizeof(mx), cudaMemcpyDeviceToHost, st));
+        DC_TRY(cudaMemcpyAsync(d->Jprev, J, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, st));
+        DC_TRY(cudaStreamSynchronize(st));
+        for (rts_handle *h : d->blk) {
+            rts_status s = rts_check(h);
+            if (s) return bad(s, h->err);
+        }
+        float dj, jm;
+        std::memcpy(&dj, &mx[0], sizeof(float));
+        std::memcpy(&jm, &mx[1], sizeof(float));
+        conv = it > 0 && dj <= tol * jm;
+        cur = nxt;
+    }
+    if (iters) *iters = it;
+    if (!conv) return bad(RTS_ENOCONV, "the slab iteration did not converge");
+    // the owned levels of F and Q_rad from the last iteration
+    for (int k = 0; k < d->nblk; ++k) {
+        const size_t nb = sizeof(double) * (size_t)(d->b[k] - d->a[k]) * N2;
+        const long long nk = (long long)(d->hi[k] - d->lo[k]) * N2;
+        if (Q_rad) DC_TRY(cudaMemcpyAsync(Q_rad + d->a[k] * N2, d->Q[k] + (d->a[k] - d->lo[k]) * N2, nb,
+                                          cudaMemcpyDeviceToDevice, st));
+        if (F)
+            for (int c = 0; c < 3; ++c)
+                DC_TRY(cudaMemcpyAsync(F + c * N + d->a[k] * N2, d->F[k] + c * nk + (d->a[k] - d->lo[k]) * N2, nb,
+                                       cudaMemcpyDeviceToDevice, st));
+    }
+#undef DC_TRY
+    return RTS_OK;
+}
+
+}  // extern "C"
