@@ -202,6 +202,49 @@ def _traffic_from_profile(prec, grid, tile_rows, kernel):
         return None
 
 
+FP64_PEAK_GFLOPS = 1250.0  # nominal B300 FP64 rate; no measured FP64 peak is on record
+
+
+def _performed_updates(st, nx, ny, nz, nb):
+    """Ray-point updates the sweep executed: every unit's planes, the x/y
+    groups' warm-up planes included (mean over units from the stats), 4 rays
+    per unit (24-ray set: 2 z, 2 y, 2 x groups per band)."""
+    warm = st.get("mean_warmup_steps", 0.0)
+    z = 2 * nz * nx * ny
+    xy = 2 * (nx + warm) * ny * nz + 2 * (ny + warm) * nx * nz
+    return 4 * nb * (z + xy)
+
+
+def _fp64_roofline(st):
+    """The FP64 sweep against the FP64 rate: FP64 flops executed per launch
+    (the per-update count of profiles/sweep_fp64_ops.md, measured by ncu on a
+    smaller grid, times the updates this launch performed) over its time.
+    None when that record is missing or the sweep source changed since."""
+    path = os.path.join(ROOT, "profiles", "sweep_fp64_ops.md")
+    rec = {}
+    try:
+        for line in open(path):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                rec[k.strip()] = v.strip()
+    except OSError:
+        return None
+    src = os.path.join(ROOT, "paper_2107_08145_b300", "csrc", "sweep.cuh")
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if rec.get("sweep_source_sha256_16") != digest:
+        return None
+    try:
+        per_upd = float(rec["fp64_flops_per_update"])
+    except (KeyError, ValueError):
+        return None
+    flops = per_upd * _performed_updates(st, NX, NY, NZ, NB)
+    ach = flops / (st["ms_sweep"] * 1e-3) / 1e9
+    return {"kernel": "sweep_kernel<double> (FP64 persistent tile-DAG sweep)", "bound": "fp64",
+            "achieved": round(ach, 2), "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": round(ach / FP64_PEAK_GFLOPS, 4), "peak_source": "nominal (1.25 TFLOP/s FP64), not measured",
+            "fp64_flops_per_update": per_upd, "tile_rows": st["tile_rows"]}
+
+
 def sweep_algorithmic_bytes(prec, nb=NB, ndir=NDIR):
     """Per launch: every sweep unit (band x group of 4 rays) reads its band's
     chi and S once and writes its 4 partial sums (J, Fx, Fy, Fz) once; plus
@@ -213,9 +256,9 @@ def sweep_algorithmic_bytes(prec, nb=NB, ndir=NDIR):
 
 
 def _adjoint_timing(rts, torch, workload, name, grid, prec, stream, steps, chunk=0):
-    """Mean ms of rts_solve and of rts_adjoint (loss on I_top and Q_rad; one
-    band per checkpoint, or `chunk` bands) on one workload, CUDA events on the
-    solver's stream."""
+    """Mean ms of rts_solve and of rts_adjoint (loss on I_top and Q_rad;
+    `chunk` bands per checkpoint, 0 = the library's automatic choice) on one
+    workload, CUDA events on the solver's stream."""
     import numpy as np
 
     nx, ny, nz = grid
@@ -246,6 +289,7 @@ def _adjoint_timing(rts, torch, workload, name, grid, prec, stream, steps, chunk
     fwd = timed(lambda: s.solve(chi, S, out=out, check=False))
     bwd = timed(lambda: s.adjoint(chi, S, gI_top=gI, gQ=gQ, out=grads, check=False))
     s.check()
+    chunk = s.stats()["adjoint_chunk_bands"]
     upd = nx * ny * nz * NDIR * nb
     r = {"forward_ms": round(fwd, 3), "adjoint_ms": round(bwd, 3), "adjoint_over_forward": round(bwd / fwd, 3),
          "adjoint_gupd_s": round(upd / (bwd * 1e-3) / 1e9, 3),
@@ -374,7 +418,8 @@ def _large_timing(rts, torch):
          "forward_ms": round(fwd, 2), "gupd_s": round(upd / (fwd * 1e-3) / 1e9, 3),
          "phases_ms": {k: round(st[k], 2) for k in ("ms_transpose", "ms_sweep", "ms_reduce", "ms_qstep")},
          "adjoint_ms": round(adj, 2), "adjoint_over_forward": round(adj / fwd, 3),
-         "adjoint_phases_ms": [round(x, 2) for x in sa["ms_adjoint"]], "checkpoint": "1 band",
+         "adjoint_phases_ms": [round(x, 2) for x in sa["ms_adjoint"]],
+         "checkpoint": f"{sa['adjoint_chunk_bands']} bands (automatic)",
          "wrap": {"mean_warmup_planes": st["mean_warmup_steps"], "max_warmup_planes": st["max_warmup_steps"]}}
     del s, c, Sd, out, g, gI, gQ
     torch.cuda.empty_cache()
@@ -516,7 +561,8 @@ def run_ours(args):
         ms64 = max_over_ranks(f0.elapsed_time(f1) / n64)
         st64 = s64.stats()
         extra["fp64"] = {"value": round(ws * upd / (ms64 * 1e-3) / 1e9, 4), "unit": "Gupd/s",
-                         "ms_per_step": round(ms64, 3), "sweep_ms": round(st64["ms_sweep"], 3)}
+                         "ms_per_step": round(ms64, 3), "sweep_ms": round(st64["ms_sweep"], 3),
+                         "roofline": _fp64_roofline(st64)}
         extra["fp32_over_fp64"] = round(ms64 / ms, 2)
         del s64, c64, S64d, o64
 
@@ -569,10 +615,10 @@ def run_ours(args):
     if not args.skip_adjoint:
         adj = {}
         for name, grid in (("adj96x4", (96, 96, 96)), (WORKLOAD, (NX, NY, NZ))):
+            # the default (automatic checkpoint chunk), and one band per checkpoint
             adj[name] = _adjoint_timing(rts, torch, workload, name, grid, prec, stream, max(3, min(args.steps, 10)))
-            # all four bands in one checkpoint: more sweep units at once, 4x the scratch
-            adj[name + "_all_bands_checkpoint"] = _adjoint_timing(rts, torch, workload, name, grid, prec, stream,
-                                                                 max(3, min(args.steps, 10)), chunk=4)
+            adj[name + "_one_band_checkpoint"] = _adjoint_timing(rts, torch, workload, name, grid, prec, stream,
+                                                                max(3, min(args.steps, 10)), chunk=1)
         ratio = adj[WORKLOAD]["adjoint_over_forward"]
     else:
         ratio = None

@@ -112,9 +112,11 @@ typedef struct {
     double timeout_s;     /* device-side wait limit in seconds (default 2) */
     void *stream;         /* cudaStream_t to run on (NULL = legacy default stream) */
     int adjoint_chunk_bands; /* bands whose intensities rts_adjoint recomputes
-                             and keeps at a time (the checkpoint unit;
-                             0 = 1 band); larger chunks run more sweep units
-                             at once and need proportionally more scratch */
+                             and keeps at a time (the checkpoint unit);
+                             larger chunks run more sweep units at once and
+                             need proportionally more scratch. 0 = automatic:
+                             equal chunks, as large as 40 % of the device
+                             memory free at rts_create holds */
     int sweep_kernel;     /* forward sweep of the FP32 modes: RTS_SWEEP_AUTO (0),
                              RTS_SWEEP_SHARED (1) or RTS_SWEEP_REGISTER (2) */
 } rts_options;
@@ -149,6 +151,7 @@ typedef struct {
     int timed_adjoints;
     float ms_adjoint[4];
     int sweep_kernel;     /* forward sweep rts_solve runs: RTS_SWEEP_SHARED or RTS_SWEEP_REGISTER */
+    int adjoint_chunk_bands; /* bands per checkpoint of rts_adjoint (0 without RTS_FLAG_ADJOINT) */
 } rts_stats;
 
 /* Boundary conditions of a solve, and the optional warm start of the

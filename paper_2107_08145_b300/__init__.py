@@ -51,7 +51,7 @@ class Stats(C.Structure):
                 ("tile_rows", C.c_int), ("kernels_per_solve", C.c_int), ("timed_solves", C.c_int),
                 ("ms_transpose", C.c_float), ("ms_sweep", C.c_float), ("ms_reduce", C.c_float),
                 ("ms_qstep", C.c_float), ("timed_adjoints", C.c_int), ("ms_adjoint", C.c_float * 4),
-                ("sweep_kernel", C.c_int)]
+                ("sweep_kernel", C.c_int), ("adjoint_chunk_bands", C.c_int)]
 
 
 class FrontTable(C.Structure):

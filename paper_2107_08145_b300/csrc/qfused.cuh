@@ -28,10 +28,10 @@ constexpr int QR_NAT = QR_TJ * QR_TI;         // float4 of a natural unit's tile
 constexpr int QR_XR = QR_TJ + 1;              // padded row of an x group's tile
 constexpr int QR_XU = QR_TI * QR_XR;          // float4 of an x group's tile
 
-// shared memory: two buffers of the largest band's units
-__host__ __device__ constexpr size_t qr_smem_bytes(int max_nat, int max_x)
+// shared memory: two buffers of the largest band's units, then the units
+__host__ __device__ constexpr size_t qr_smem_bytes(int max_nat, int max_x, int nunits)
 {
-    return (size_t)2 * (max_nat * QR_NAT + max_x * QR_XU) * sizeof(float4);
+    return (size_t)2 * (max_nat * QR_NAT + max_x * QR_XU) * sizeof(float4) + sizeof(RedUnit) * (size_t)nunits;
 }
 
 // 16-byte copy global -> shared; src_bytes 0 fills zeros (the source is not read)
@@ -48,12 +48,20 @@ __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wa
 // groups (each band's units are ordered x groups first)
 __global__ void __launch_bounds__(QR_NT, 2) qf_reduce_kernel(const RedUnit *__restrict__ ru,
                                                                const int *__restrict__ qb, int nx, int ny, int nz,
-                                                               int nbands, int max_nat, int max_x,
+                                                               int nbands, int nunits, int max_nat, int max_x,
                                                                df32 *__restrict__ JF)
 {
     constexpr int RP = QR_TJ / QR_RY;
     extern __shared__ __align__(16) float4 qr_sm[];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * QR_TI + tx;
+    // the units' coefficients, read by every thread of the CTA (broadcast loads)
+    RedUnit *su = reinterpret_cast<RedUnit *>(qr_sm + 2 * (max_nat * QR_NAT + max_x * QR_XU));
+    {
+        const int words = (int)(sizeof(RedUnit) / 4) * nunits;
+        const int *src = reinterpret_cast<const int *>(ru);
+        int *dst = reinterpret_cast<int *>(su);
+        for (int w = tid; w < words; w += QR_NT) dst[w] = src[w];
+    }
     const long long N = (long long)nx * ny * nz;
     const int nti = (nx + QR_TI - 1) / QR_TI, ntj = (ny + QR_TJ - 1) / QR_TJ;
     const int ntiles = nti * ntj * nz * nbands;  // < 2^31: checked on the host
@@ -122,7 +130,7 @@ __global__ void __launch_bounds__(QR_NT, 2) qf_reduce_kernel(const RedUnit *__re
 #pragma unroll
             for (int c = 0; c < 4; ++c) sm[r][c] = se[r][c] = 0.f;
         for (int u = ub; u < ue; ++u) {
-            const RedUnit &U = ru[u];
+            const RedUnit &U = su[u];
             const bool xg = u < ux;
             const float4 *src = xg ? sb + max_nat * QR_NAT + (u - ub) * QR_XU : sb + (u - ux) * QR_NAT;
 #pragma unroll

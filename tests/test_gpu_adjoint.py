@@ -83,6 +83,8 @@ def test_adjoint_fp64_vs_oracle(rts, shape, B, spacing, chunk):
     nx, ny, nz = shape
     chi, S = random_case(nx, ny, nz, B, seed=nx * 7 + ny)
     s = rts.Solver(nx, ny, nz, B, *spacing, precision="fp64", adjoint=True, adjoint_chunk_bands=chunk)
+    # automatic (0): a small problem fits in one checkpoint of all bands
+    assert s.stats()["adjoint_chunk_bands"] == (chunk if chunk else B)
     cot = _cotangents(B, s.n_up, nx, ny, nz, seed=5)
     got = _gpu_adjoint(s, chi, S, cot)
     ref = _oracle_adjoint(chi, S, cot, *spacing)
