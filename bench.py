@@ -344,6 +344,48 @@ def _batched_timing(rts, torch, steps):
     offs = bs.offsets
     del g, bs, out
     torch.cuda.empty_cache()
+    # the sweep alone (phase timer of uncaptured solves) against HBM: every
+    # unit reads chi, S and writes its 4 slot intensities once per point
+    bt = rts.BatchedSolver(shapes, nb, precision="fp32", tile_rows=best, stream=side, timing=True)
+    ot = bt.solve(chi, S)
+    bt.stats()
+    for _ in range(3):
+        bt.solve(chi, S, out=ot, check=False)
+    torch.cuda.synchronize()
+    bt.check()
+    stt = bt.stats()
+    kernel = stt["sweep_kernel"]
+    del bt, ot
+    torch.cuda.empty_cache()
+    npts = sum(nx * ny * nz for nx, ny, nz in shapes)
+    alg = nb * (NDIR // 4) * npts * 24 + nb * (NDIR // 2) * sum(nx * ny for nx, ny, _ in shapes) * 4
+    hbm = _peaks().get("hbm_gbs") or 6400.0
+    ach = alg / (stt["ms_sweep"] * 1e-3) / 1e9
+    roof = {"kernel": "sweep_reg_kernel, one launch for all subdomains" if kernel == 2 else
+            "sweep_kernel, one launch per CTA-width class", "bound": "hbm", "achieved": round(ach, 2), "peak": hbm,
+            "unit": "GB/s", "frac": round(ach / hbm, 5), "algorithmic_bytes_per_launch": alg,
+            "sweep_ms_mean": round(stt["ms_sweep"], 3), "phases_ms": {k: round(stt[k], 3) for k in
+                                                                     ("ms_transpose", "ms_sweep", "ms_reduce",
+                                                                      "ms_qstep")}}
+    # plain FP64 solves, one per subdomain and band: a sample of one band per
+    # subdomain (64 solves, band 0's data), scaled to the 768 solves
+    ms64 = 0.0
+    for (nx, ny, nz), (go, _, _) in zip(shapes, offs):
+        n = nx * ny * nz
+        so = rts.Solver(nx, ny, nz, 1, precision="fp64", stream=side)
+        c64 = chi[go:go + n].double().view(1, nz, ny, nx)
+        s64 = S[go:go + n].double().view(1, nz, ny, nx)
+        o64 = so.solve(c64, s64)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(side)
+        so.solve(c64, s64, out=o64, check=False)
+        b.record(side)
+        torch.cuda.synchronize()
+        so.check()
+        ms64 += a.elapsed_time(b)
+        del so, c64, s64, o64
+    torch.cuda.empty_cache()
+    ms64 *= nb
     # separate solves: one handle per subdomain (one band), 12 calls each
     singles = []
     for (nx, ny, nz) in shapes:
@@ -367,11 +409,15 @@ def _batched_timing(rts, torch, steps):
     torch.cuda.empty_cache()
     upd = sum(nx * ny * nz for nx, ny, nz in shapes) * NDIR * nb
     return {"workload": "64 subdomains, Nx=Ny in {48,64,96,128}, Nz in {96,128,192}, x 12 bands, FP32 sweep + FP64 Q",
+            "sweep_kernel": "register (one persistent launch)" if kernel == 2 else "shared (per CTA-width class)",
             "batched_ms": round(ms_b, 3), "separate_ms": round(ms_s, 3), "speedup": round(ms_s / ms_b, 3),
             "batched_gupd_s": round(upd / (ms_b * 1e-3) / 1e9, 3), "separate_gupd_s": round(upd / (ms_s * 1e-3) / 1e9, 3),
             "separate": "768 rts_solve calls (one per subdomain and band), same precision",
-            "tile_rows": best, "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
-            "units": st["n_units"], "tiles": st["n_tiles"], "grid": st["grid"], "launch": "cuda graph"}
+            "separate_fp64_ms": round(ms64, 3), "speedup_over_fp64_separate": round(ms64 / ms_b, 3),
+            "separate_fp64": "768 plain FP64 rts_solve calls: 64 timed (one band per subdomain) x 12",
+            "roofline": roof, "tile_rows": best, "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
+            "units": st["n_units"], "tiles": st["n_tiles"], "grid": st["grid"], "launch": "cuda graph",
+            "sweep_launches_per_solve": 1 if kernel == 2 else None}
 
 
 def _large_timing(rts, torch):

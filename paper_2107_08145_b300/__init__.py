@@ -455,7 +455,7 @@ class BatchedSolver(Solver):
     Inputs and outputs are packed 1-D tensors (see pack / unpack)."""
 
     def __init__(self, shapes, nbands=1, spacing=None, precision="fp32", tau_switch=0.1, wrap_tol=0.0,
-                 max_wrap_iters=64, tile_rows=0, timeout_s=2.0, timing=False, stream=None):
+                 max_wrap_iters=64, tile_rows=0, timeout_s=2.0, timing=False, stream=None, sweep_kernel="auto"):
         import torch
 
         L = load()
@@ -474,6 +474,7 @@ class BatchedSolver(Solver):
         o.tile_rows = tile_rows
         o.timeout_s = timeout_s
         o.flags = FLAG_TIMING if timing else 0
+        o.sweep_kernel = _SWEEP[sweep_kernel]
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

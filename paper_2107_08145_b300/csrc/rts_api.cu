@@ -19,6 +19,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "rts.h"
@@ -2221,18 +2222,80 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
         k = k1;
     }
 
+    // ---- FP32: the register-resident sweep, one persistent launch for every
+    // subdomain (units narrower than the CTA leave their extra threads idle) ----
+    long long reg_halo = 0;
+    if (o.prec != RTS_FP64 && o.sweep_kernel != RTS_SWEEP_SHARED && reg_eligible(h->units)) {
+        int nq_per = 0;  // the tile height must divide every subdomain's periodic z-group rows (ny)
+        for (int s = 0; s < nsub; ++s) nq_per = std::gcd(nq_per, grids[s].ny);
+        const Tiling tr = choose_reg(o.tile_rows, npmax, nqmax, nq_per, nsm);
+        if (tr.tq >= 1) {
+            std::vector<rts::SweepUnit> rplan;
+            std::vector<int> rtmp_uot((size_t)max_units * ((maxext + tr.tq - 1) / tr.tq));
+            bool ok = true;
+            for (int s = 0; s < nsub && ok; ++s) {
+                const rts_grid &g = grids[s];
+                const double hsp[3] = {g.dx, g.dy, g.dz};
+                std::vector<DirGeo> geo(h->ndir);
+                std::vector<int> udx(h->ndir);
+                int nup = 0, ndn = 0;
+                for (int d = 0; d < h->ndir; ++d) {
+                    direction_geometry(hsp, &h->n[3 * d], geo[d]);
+                    udx[d] = geo[d].up ? nup++ : ndn++;
+                }
+                PlanOut pr;
+                ok = plan_units(geo.data(), udx.data(), h->n.data(), h->w.data(), h->ndir, g.nx, g.ny, g.nz, nbands,
+                                tr.tq, tmp.data(), max_units, rtmp_uot.data(), (int)rtmp_uot.size(), pr);
+                for (int u = 0; ok && u < pr.nunits; ++u) {
+                    rts::SweepUnit U = tmp[u];
+                    U.in_off += h->subs[s].in_off;
+                    U.top_off += h->subs[s].top_off;
+                    U.dn_off = 0;
+                    rplan.push_back(U);
+                }
+            }
+            if (ok && (int)rplan.size() == nunits) {
+                h->reg_units.resize(nunits);
+                h->reg_unit_of_tile.clear();
+                for (int k = 0; k < nunits; ++k) {  // the shared-sweep order, so that unit k is the same in both
+                    rts::SweepUnit U = rplan[order[k]];
+                    U.tile0 = (int)h->reg_unit_of_tile.size();
+                    for (int t = 0; t < U.ntiles; ++t) h->reg_unit_of_tile.push_back(k);
+                    U.halo_off = reg_halo;
+                    reg_halo += (long long)U.ntiles * rts::reg_ring_elems(U.NP);
+                    h->reg_units[k] = U;
+                }
+                h->reg_total_tiles = (int)h->reg_unit_of_tile.size();
+                h->reg_tq = tr.tq;
+                h->reg_maxr = tr.maxt;
+                h->reg_nt = tr.nt;
+                h->reg_smem = tr.smem;
+                h->reg_carveout = carveout_percent(tr.blocks, tr.smem);
+                h->reg_grid = std::min(h->reg_total_tiles, tr.blocks * nsm);
+                h->flag_tiles = std::max(h->flag_tiles, 2 * h->reg_total_tiles);
+                h->use_reg = true;
+            } else {
+                h->reg_units.clear();
+                h->reg_unit_of_tile.clear();
+                reg_halo = 0;
+            }
+        }
+    }
+
     // ---- device memory ----
     const size_t es = h->esize;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t at = off; off = round_up(off + bytes, 256); return at; };
     const size_t o_units = take(sizeof(rts::SweepUnit) * nunits);
     const size_t o_uot = take(sizeof(int) * h->unit_of_tile.size());
+    const size_t o_regu = h->use_reg ? take(sizeof(rts::SweepUnit) * nunits) : 0;
+    const size_t o_reguot = h->use_reg ? take(sizeof(int) * h->reg_unit_of_tile.size()) : 0;
     const size_t o_part = take((size_t)part_elems * es);
     const size_t o_chiT = h->has_x ? take((size_t)h->in_total * es) : 0;
     const size_t o_ST = h->has_x ? take((size_t)h->in_total * es) : 0;
     const size_t o_JF = take((size_t)jf_off * 8);
-    const size_t o_halo = take((size_t)halo * es);
-    const size_t o_flags = take(sizeof(int) * 2 * h->total_tiles);
+    const size_t o_halo = take((size_t)std::max(halo, reg_halo) * es);
+    const size_t o_flags = take(sizeof(int) * h->flag_tiles);
     const size_t o_gcnt = take(sizeof(unsigned int) * nunits * R);
     const size_t o_gmax = take(sizeof(unsigned long long) * nunits * R);
     const size_t o_ticket = take(sizeof(int) * 4);
@@ -2274,6 +2337,15 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * nunits, cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, ru_begin.data(), sizeof(int) * ru_begin.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_subs, h->subs.data(), sizeof(rts::SubDesc) * nsub, cudaMemcpyHostToDevice));
+    if (h->use_reg) {
+        h->d_reg_units = (rts::SweepUnit *)(base + o_regu);
+        h->d_reg_uot = (int *)(base + o_reguot);
+        for (int k = 0; k < nunits; ++k) h->reg_units[k].partial = h->units[k].partial;
+        CUDA_TRY(h, cudaMemcpy(h->d_reg_units, h->reg_units.data(), sizeof(rts::SweepUnit) * nunits,
+                               cudaMemcpyHostToDevice));
+        CUDA_TRY(h, cudaMemcpy(h->d_reg_uot, h->reg_unit_of_tile.data(), sizeof(int) * h->reg_unit_of_tile.size(),
+                               cudaMemcpyHostToDevice));
+    }
     h->band_unit.assign(1, 0);
     CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(int) * 4));
     CUDA_TRY(h, cudaMemset(h->d_unit_tacc, 0, sizeof(int) * nunits));
@@ -2314,13 +2386,15 @@ static rts_status solve_batched_impl(rts_handle *h, const void *chi, const void 
     rts::SweepArgs<T> a = sweep_args<T>(h, chi, S, bc);
     a.itop = (T *)I_top;
     int launches = 0;
-    cudaError_t e = launch_sweep_classes<T>(h, a, &launches);
+    const bool reg = h->use_reg && sizeof(T) == 4;
+    cudaError_t e = reg ? launch_reg_sweep(h, *reinterpret_cast<const rts::SweepArgs<float> *>(&a))
+                        : launch_sweep_classes<T>(h, a, &launches);
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
-    kernels += launches;
+    kernels += reg ? 1 : launches;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
     if (J || F || Q) {
-        rts::reduce_units_batched<T, Acc><<<(unsigned)h->nblk[1], dim3(32, 8), 0, st>>>(h->d_subs, ns, h->d_ru,
-                                                                                       h->d_ru_begin, (Acc *)h->d_JF, 0);
+        rts::reduce_units_batched<T, Acc><<<(unsigned)h->nblk[1], dim3(32, 8), 0, st>>>(
+            h->d_subs, ns, h->d_ru, h->d_ru_begin, (Acc *)h->d_JF, reg ? 1 : 0);
         if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
         rts::qstep_batched<T, Acc><<<(unsigned)h->nblk[2], dim3(32, 8), 0, st>>>(
             h->d_subs, ns, (const Acc *)h->d_JF, (const T *)chi, (const T *)S, J, F, Q);

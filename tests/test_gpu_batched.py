@@ -1,7 +1,11 @@
 """Batched solves (rts_create_batched / rts_solve_batched): many grids of
 uneven size x bands in one persistent launch, its CUDA graph, and the tile
-autotuner. A batched solve must give exactly (bit for bit) what rts_solve
-gives on each grid alone, and the FP64 path must match the oracle."""
+autotuner. On the shared-memory tile sweep (FP64, and FP32 batches with an
+odd plane width) a batched solve must give exactly (bit for bit) what
+rts_solve gives on each grid alone; FP32 batches of even widths run the
+register sweep in one launch and must match the register-sweep single solves
+to the rounding of the band reduction and the FP32 oracle bar; the FP64 path
+must match the oracle element-wise."""
 import numpy as np
 import pytest
 
@@ -43,14 +47,13 @@ def _batched(rts, shapes, B, chis, Ss, precision, **kw):
     return bs, chi, S, out
 
 
-def _singles(rts, shapes, B, chis, Ss, precision, tile_rows=0):
-    """rts_solve on each grid with the sweep the batched handle runs (the
-    shared-memory tile sweep), so the results must be bit-identical."""
+def _singles(rts, shapes, B, chis, Ss, precision, tile_rows=0, sweep_kernel="shared"):
+    """rts_solve on each grid with the sweep the batched handle runs."""
     import torch
 
     res = []
     for (nx, ny, nz), c, s in zip(shapes, chis, Ss):
-        so = rts.Solver(nx, ny, nz, B, precision=precision, tile_rows=tile_rows, sweep_kernel="shared")
+        so = rts.Solver(nx, ny, nz, B, precision=precision, tile_rows=tile_rows, sweep_kernel=sweep_kernel)
         o = so.solve(torch.as_tensor(c, dtype=so.dtype, device="cuda"), torch.as_tensor(s, dtype=so.dtype, device="cuda"))
         res.append({k: v.cpu().numpy() for k, v in o.items()})
     return res
@@ -64,6 +67,7 @@ def test_batched_equals_single_solves(rts, precision):
     B = 3
     chis, Ss = _inputs(SHAPES, B)
     bs, _, _, out = _batched(rts, SHAPES, B, chis, Ss, precision)
+    assert bs.stats()["sweep_kernel"] == rts.SWEEP_SHARED  # odd plane widths: the shared-memory sweep
     got = bs.unpack(out)
     ref = _singles(rts, SHAPES, B, chis, Ss, precision)
     for i, (g, r) in enumerate(zip(got, ref)):
@@ -154,8 +158,9 @@ def test_batched_rejects_explicit_boundaries(rts):
 
 
 def test_batched_uneven_subdomains_12_bands(rts):
-    """Eight subdomains of the batched workload's size mix x 12 bands, FP32:
-    bit-identical to solving each grid alone."""
+    """Eight subdomains of the batched workload's size mix x 12 bands, FP32,
+    on the register sweep in one launch: the same as solving each grid alone
+    with the register sweep, to the rounding of the band reduction."""
     shapes = batched_subdomain_shapes(8, seed=0)
     cs, ss = batched_bands()
     chis, Ss = [], []
@@ -165,7 +170,55 @@ def test_batched_uneven_subdomains_12_bands(rts):
         chis.append(c)
         Ss.append(s)
     bs, _, _, out = _batched(rts, shapes, 12, chis, Ss, "fp32")
-    ref = _singles(rts, shapes, 12, chis, Ss, "fp32")
+    assert bs.stats()["sweep_kernel"] == rts.SWEEP_REGISTER
+    ref = _singles(rts, shapes, 12, chis, Ss, "fp32", sweep_kernel="register")
     for g, r in zip(bs.unpack(out), ref):
+        assert np.array_equal(g["I_top"].cpu().numpy(), r["I_top"])  # the same sweep arithmetic per point
+        for k in ("J", "F", "Q"):
+            e = norm_err(g[k].cpu().numpy(), r[k])
+            assert e <= 1e-6, (k, e)
+
+
+EVEN = [(16, 16, 12), (24, 20, 10), (12, 18, 14), (20, 24, 8)]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_compensated"])
+def test_batched_register_sweep_vs_oracle(rts, precision):
+    """Even plane widths: one register-sweep launch for all subdomains,
+    against the FP64 oracle (FP32 bar, 1e-5 of max)."""
+    B = 3
+    chis, Ss = _inputs(EVEN, B, seed0=40)
+    bs, _, _, out = _batched(rts, EVEN, B, chis, Ss, precision)
+    assert bs.stats()["sweep_kernel"] == rts.SWEEP_REGISTER
+    for g, c, s in zip(bs.unpack(out), chis, Ss):
+        ref = oracle_solve(c.astype(np.float32), s.astype(np.float32))
         for k in OUTPUTS:
-            assert np.array_equal(g[k].cpu().numpy(), r[k]), k
+            e = norm_err(g[k].double().cpu().numpy(), ref[k])
+            assert e <= 1e-5, (precision, k, e)
+
+
+def test_batched_register_sweep_graph_and_shared_option(rts):
+    """The register-sweep batch replays in a CUDA graph; sweep_kernel='shared'
+    keeps the per-width launches and agrees to the FP32 bar."""
+    import torch
+
+    B = 2
+    chis, Ss = _inputs(EVEN, B, seed0=50)
+    stream = torch.cuda.Stream()
+    bs, chi, S, out = _batched(rts, EVEN, B, chis, Ss, "fp32", stream=stream)
+    assert bs.stats()["sweep_kernel"] == rts.SWEEP_REGISTER
+    ref = {k: v.clone() for k, v in out.items()}
+    g, gout = bs.graph(chi, S)
+    for _ in range(2):
+        for v in gout.values():
+            v.fill_(-1)
+        g.launch()
+        bs.check()
+        for k in OUTPUTS:
+            assert torch.equal(gout[k], ref[k]), k
+    sh = rts.BatchedSolver(EVEN, B, precision="fp32", sweep_kernel="shared")
+    assert sh.stats()["sweep_kernel"] == rts.SWEEP_SHARED
+    o2 = sh.solve(chi, S)
+    for k in OUTPUTS:
+        e = norm_err(o2[k].double().cpu().numpy(), out[k].double().cpu().numpy())
+        assert e <= 1e-5, (k, e)
