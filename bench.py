@@ -497,7 +497,9 @@ def _sequence_timing(rts, torch, s, chi, S, stream, steps=6):
         res[mode] = {"sweep_ms": round(float(np.mean(sweeps)), 3), "extra_planes_mean": round(float(np.mean(mean_w)), 1),
                      "extra_planes_max": int(max(max_w))}
     res["change_per_step"] = "S = T^4 grows by 4e-5 relative per step"
-    res["warm_criterion"] = "wrap plane's relative change over a period <= 1e-6 (the paper's test on boundary intensities)"
+    res["warm_criterion"] = ("the wrap plane's change over a period r and the bound's one-period contraction gam "
+                             "(tracked in the first period): every plane of the accumulated period carries at most "
+                             "1e-6 relative error (seed error <= r / (1 - gam))")
     return res
 
 

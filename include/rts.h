@@ -115,8 +115,9 @@ typedef struct {
                              and keeps at a time (the checkpoint unit);
                              larger chunks run more sweep units at once and
                              need proportionally more scratch. 0 = automatic:
-                             equal chunks, as large as 40 % of the device
-                             memory free at rts_create holds */
+                             equal chunks, as large as fit in 85 % of the
+                             device memory free at rts_create next to the
+                             handle's other arrays (at least 1 band) */
     int sweep_kernel;     /* forward sweep of the FP32 modes: RTS_SWEEP_AUTO (0),
                              RTS_SWEEP_SHARED (1) or RTS_SWEEP_REGISTER (2) */
 } rts_options;
@@ -163,19 +164,24 @@ typedef struct {
  * the intensities of its wrap plane (the plane upwind of the first swept
  * one, [Nq][Np][4 sign slots] per group). Written with the converged values
  * by every solve that is given it. With seed_in != 0 it is also read as the
- * starting values: the sweep then accumulates from the first period and goes
- * around the period again until the wrap plane changes by at most seed_tol
- * times its largest intensity over one period (per tile; default 1e-6) --
- * the paper's convergence test, which assumes the seed is close (the
- * previous solve of a slowly changing atmosphere). Without seed_in the wrap
- * converges from I = S with the rigorous seed-error bound. */
+ * starting values: the sweep accumulates from the first period, carrying in
+ * that period the seed-error bound from 1 on the wrap plane. With r_p the
+ * wrap plane's change over period p (relative to its largest intensity,
+ * per tile) and gam the bound after one period (its contraction of a wrap
+ * error), the seed error is at most r_0 / (1 - gam): the solve stops when
+ * one whole period of planes is shown to carry at most seed_tol (default
+ * 1e-6) relative error -- planes of the first period once their bound times
+ * r_0 / (1 - gam) is below it, later planes once r_p / (1 - gam) is (the
+ * paper's test on boundary intensities, made rigorous by gam; with gam >= 1
+ * the plain test r_p <= seed_tol). Without seed_in the wrap converges from
+ * I = S with the seed-error bound alone. */
 typedef struct {
     rts_bc_kind bottom, top;
     const void *bottom_I;  /* [B][n_up][Ny][Nx] when bottom == RTS_BC_EXPLICIT */
     const void *top_I;     /* [B][n_down][Ny][Nx] when top == RTS_BC_EXPLICIT */
     void *wrap_seed;       /* optional warm start, in/out (see above); NULL = none */
     int seed_in;           /* read wrap_seed as the starting values */
-    double seed_tol;       /* relative change that ends a warm-started wrap (0 = 1e-6) */
+    double seed_tol;       /* relative error that ends a warm-started wrap (0 = 1e-6) */
 } rts_boundary;
 
 

@@ -855,17 +855,24 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         if (o.adjoint_chunk_bands > 0) {
             h->chunk_bands = std::min(nbands, o.adjoint_chunk_bands);
         } else {
-            // automatic: as many bands per checkpoint as 40 % of the free device
-            // memory holds (more bands at once keep more sweep units resident;
-            // measured on B300, 4-band chunks run the 288^3 x 4 adjoint in 0.88 and
-            // the 96^3 x 4 one in 0.56 of the 1-band time), split into equal chunks
+            // automatic: as many bands per checkpoint as fit in 85 % of the free
+            // device memory next to the handle's other arrays (more bands at once
+            // keep more sweep units resident; measured on B300, 4-band chunks run
+            // the 288^3 x 4 adjoint in 0.88 and the 96^3 x 4 one in 0.56 of the
+            // 1-band time), split into equal chunks
             size_t fr = 0, tot = 0;
             if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) fr = 0;
             cudaGetLastError();
             int upb = 0;
             for (int b = 0; b < nbands; ++b) upb = std::max(upb, h->band_unit[b + 1] - h->band_unit[b]);
-            const double per_band = (double)upb * (rts::STORE_CH * rts::MAXD + rts::GRAD_CH) * (double)h->N * h->esize;
-            const int fit = per_band > 0 ? (int)std::min<double>(nbands, 0.4 * (double)fr / per_band) : nbands;
+            const double es_ = (double)h->esize, Nd = (double)h->N, Bd = (double)nbands;
+            const double per_band = (double)upb * (rts::STORE_CH * rts::MAXD + rts::GRAD_CH) * Nd * es_;
+            // partials, transposed inputs, J_b/F_b, lam0 (and its transpose), direct terms, exp(log chi)
+            const double others = (double)h->units.size() * 4 * Nd * es_ + (h->has_x ? 2 * Bd * Nd * es_ : 0.0) +
+                                  Bd * 4 * Nd * 8 + Bd * 4 * Nd * es_ * (h->has_x ? 2 : 1) + Bd * 2 * Nd * es_ +
+                                  ((o.flags & RTS_FLAG_LOG_CHI) ? Bd * Nd * es_ : 0.0);
+            const double room = 0.85 * (double)fr - others;
+            const int fit = per_band > 0 ? (int)std::max(1.0, std::min<double>(nbands, room / per_band)) : nbands;
             const int nchunks = (nbands + std::max(1, fit) - 1) / std::max(1, fit);
             h->chunk_bands = (nbands + nchunks - 1) / nchunks;
         }
@@ -950,8 +957,9 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_JF = take((size_t)nbands * 4 * h->N * accsz);
     const size_t o_halo = take((size_t)halo_elems * es);
     const size_t o_flags = take(sizeof(int) * flag_tiles);
-    const size_t o_gcnt = take(sizeof(unsigned int) * h->units.size() * R);
-    const size_t o_gmax = take(sizeof(unsigned long long) * h->units.size() * R);
+    // per unit: R plane slots, then 4 period slots (the warm start's residual)
+    const size_t o_gcnt = take(sizeof(unsigned int) * h->units.size() * (R + 4));
+    const size_t o_gmax = take(sizeof(unsigned long long) * h->units.size() * (R + 4));
     const size_t o_ticket = take(sizeof(int) * 4);
     const size_t o_status = take(sizeof(int) * 4);
     const size_t o_tacc = take(sizeof(int) * h->units.size());
@@ -1164,6 +1172,8 @@ static rts::SweepArgs<T> sweep_args(rts_handle *h, const void *chi, const void *
     a.halo = (T *)h->d_halo;
     a.gcnt = h->d_gcnt;
     a.gmax = h->d_gmax;
+    a.pcnt = h->d_gcnt + h->units.size() * h->R;
+    a.pmax = h->d_gmax + h->units.size() * h->R;
     a.R = h->R;
     a.L = kLag;
     a.status = h->d_status;
@@ -1184,8 +1194,8 @@ static rts_status reset_sweep_state(rts_handle *h, cudaStream_t st)
 {
     CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * std::max(h->flag_tiles, 2 * h->total_tiles), st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * (h->R + 4), st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * (h->R + 4), st));
     return RTS_OK;
 }
 
@@ -1215,8 +1225,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     CUDA_TRY(h, cudaMemsetAsync(h->d_ticket, 0, sizeof(int) * 4, st));
     const bool reg = h->use_reg && sizeof(T) == 4;
     CUDA_TRY(h, cudaMemsetAsync(h->d_flags, 0, sizeof(int) * 2 * (reg ? h->reg_total_tiles : h->total_tiles), st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * h->R, st));
-    CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * h->R, st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gcnt, 0, sizeof(unsigned int) * h->units.size() * (h->R + 4), st));
+    CUDA_TRY(h, cudaMemsetAsync(h->d_gmax, 0, sizeof(unsigned long long) * h->units.size() * (h->R + 4), st));
     CUDA_TRY(h, cudaMemsetAsync(h->d_unit_tacc, 0, sizeof(int) * h->units.size(), st));
     cudaEvent_t *ev = nullptr;
     if (h->timing && !h->capturing) {
@@ -1853,8 +1863,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     const size_t o_ru = take(sizeof(rts::RedUnit) * nunits);
     const size_t o_rub = take(sizeof(int) * (B + 1));
     const size_t o_flags = take(sizeof(int) * 2 * ntile);  // a pair per tile
-    const size_t o_gcnt = take(sizeof(unsigned int) * nunits * R);
-    const size_t o_gmax = take(sizeof(unsigned long long) * nunits * R);
+    const size_t o_gcnt = take(sizeof(unsigned int) * nunits * (R + 4));
+    const size_t o_gmax = take(sizeof(unsigned long long) * nunits * (R + 4));
     const size_t o_ctl = take(sizeof(int) * 8);  // ticket, status
     const size_t o_tacc = take(sizeof(int) * nunits);
     const size_t o_halo = take((size_t)halo_elems * es);
@@ -1897,8 +1907,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     NA_TRY(cudaMemcpyAsync(base + o_ru, ru, sizeof(rts::RedUnit) * nunits, cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemcpyAsync(base + o_rub, rub, sizeof(int) * (B + 1), cudaMemcpyHostToDevice, st));
     NA_TRY(cudaMemsetAsync(base + o_flags, 0, sizeof(int) * 2 * ntile, st));
-    NA_TRY(cudaMemsetAsync(base + o_gcnt, 0, sizeof(unsigned int) * nunits * R, st));
-    NA_TRY(cudaMemsetAsync(base + o_gmax, 0, sizeof(unsigned long long) * nunits * R, st));
+    NA_TRY(cudaMemsetAsync(base + o_gcnt, 0, sizeof(unsigned int) * nunits * (R + 4), st));
+    NA_TRY(cudaMemsetAsync(base + o_gmax, 0, sizeof(unsigned long long) * nunits * (R + 4), st));
     NA_TRY(cudaMemsetAsync(base + o_ctl, 0, sizeof(int) * 8, st));
     NA_TRY(cudaMemsetAsync(base + o_tacc, 0, sizeof(int) * nunits, st));
 
@@ -1929,6 +1939,8 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     a.halo = (T *)(base + o_halo);
     a.gcnt = (unsigned int *)(base + o_gcnt);
     a.gmax = (unsigned long long *)(base + o_gmax);
+    a.pcnt = a.gcnt + (long long)nunits * R;
+    a.pmax = a.gmax + (long long)nunits * R;
     a.R = R;
     a.L = kLag;
     a.unit_tacc = (int *)(base + o_tacc);
@@ -2296,8 +2308,8 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     const size_t o_JF = take((size_t)jf_off * 8);
     const size_t o_halo = take((size_t)std::max(halo, reg_halo) * es);
     const size_t o_flags = take(sizeof(int) * h->flag_tiles);
-    const size_t o_gcnt = take(sizeof(unsigned int) * nunits * R);
-    const size_t o_gmax = take(sizeof(unsigned long long) * nunits * R);
+    const size_t o_gcnt = take(sizeof(unsigned int) * nunits * (R + 4));
+    const size_t o_gmax = take(sizeof(unsigned long long) * nunits * (R + 4));
     const size_t o_ticket = take(sizeof(int) * 4);
     const size_t o_status = take(sizeof(int) * 4);
     const size_t o_tacc = take(sizeof(int) * nunits);

@@ -114,6 +114,8 @@ struct SweepArgs {
     T *halo;                    // per tile: [2 slots][2 sides][HALO_CH][NP]
     unsigned int *gcnt;         // [units][R] tiles that posted a plane (cumulative per slot)
     unsigned long long *gmax;   // [units][R] (plane+1)<<32 | bits(max g), atomic max
+    unsigned int *pcnt;         // [units][4] tiles that posted a period's wrap residual (warm start)
+    unsigned long long *pmax;   // [units][4] (period+1)<<32 | bits(residual), atomic max
     int R, L;
     int *status;
     int *unit_tacc;             // per unit: first accumulated step

@@ -73,6 +73,9 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src)
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(gmem_src) : "memory");
 }
 
+template <int M>
+using Mode = std::integral_constant<int, M>;
+
 // Constants of a unit's stencil, packed for both columns.
 struct RegStencil {
     float2 b0, b1, b2, b3;  // bilinear weights of corners (0,0), (-sP,0), (0,-sQ), (-sP,-sQ)
@@ -171,8 +174,9 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         return EDG + ((((slot * NW + w) * 2 + side) * TQ) + (k - 1)) * 3;
     };
 
-    __shared__ float s_wmax[32], s_imax[32];
-    __shared__ int s_ctl[4];                     // 0 abort, 1 wrap decision for the next plane
+    __shared__ float s_wmax[32], s_imax[32], s_dmax[32];
+    __shared__ float s_glog[1024];               // warm start: the unit's bound of every plane of period 0
+    __shared__ int s_ctl[4];                     // 0 abort, 1 wrap decision for the next plane, 2 warm start: last plane
     __shared__ int s_q[RWS];                     // grid row of shared row k, -1 outside
 
     // unit constants (every active slot has the same stencil)
@@ -197,7 +201,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         else if (q < 0 || q >= NQ) q = -1;
         s_q[tid] = q;
     }
-    if (tid == 0) { s_ctl[0] = 0; s_ctl[1] = 0; }
+    if (tid == 0) { s_ctl[0] = 0; s_ctl[1] = 0; s_ctl[2] = INT_MAX; }
     __syncthreads();
 
     const int t_first = wrap ? 0 : 1;
@@ -384,10 +388,8 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                             natural_ij(axis, c + hh * H, q, m, i, j);
                             val = reg_bc(up ? kind_up : kind_dn, up ? a.bc_up + Ug->top_off : a.bc_dn + Ug->dn_off,
                                          Ug->udx[d], unx, uny, i, j, sv[hh]);
-                        } else if (seeded) {  // the caller's warm start (no bound is kept)
-                            val = sbuf[((long long)q * NP + c + hh * H) * 4 + d];
-                        } else {  // seed of the periodic wrap: I = S, unit bound
-                            val = sv[hh];
+                        } else {  // seed of the periodic wrap: I = S or the caller's warm start; unit bound
+                            val = seeded ? sbuf[((long long)q * NP + c + hh * H) * 4 + d] : sv[hh];
                             g[d >> 1][hh] = 1.f;
                         }
                     }
@@ -428,8 +430,11 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     // (rising TQ, descending 1) come first and are published at once; the rows
     // that need a neighbour (rising 1, descending TQ) come last.
     auto plane_step = [&](auto ACCF, int t, int m) __attribute__((always_inline)) -> int {
-        constexpr bool ACC = decltype(ACCF)::value;
-        constexpr bool BND = !ACC;  // bounds only during the warm-up (x/y groups)
+        // 0: warm-up (bounds), 1: accumulated, 2: accumulated with bounds (the first
+        // period of a warm-started x/y group)
+        constexpr int MD = decltype(ACCF)::value;
+        constexpr bool ACC = MD != 0;
+        constexpr bool BND = MD != 1;
         const bool last = ACC && !seeded && (t - t_acc == NM - 1);
         const int es = (t - 1) & 1;  // shared edge records of the previous plane
 
@@ -689,28 +694,69 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                         imax = fmaxf(imax, __shfl_xor_sync(0xffffffffu, imax, o));
                     }
                     if (lane == 0) {
-                        s_wmax[warp] = dmax;
+                        s_dmax[warp] = dmax;
                         s_imax[warp] = imax;
                     }
                 }
             }
-            // seeded: the decision on period p, L planes after its wrap plane
-            const int tp_end = t - a.L - (NM - 1);
-            if (seeded && tid == dec_thread && tp_end >= 0 && tp_end % NM == 0) {
-                const int p = tp_end / NM;
-                const int slot = p % a.R;
-                const unsigned want = (unsigned)ntl * (unsigned)(p / a.R + 1);
-                bool okd = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
-                if (okd) {
-                    const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
-                    if ((unsigned)(v >> 32) != (unsigned)(p + 1)) {
-                        atomicOr(a.status, ST_BADARG);  // ring overrun: never expected
-                        okd = false;
-                    } else {
-                        s_ctl[1] = __uint_as_float((unsigned)(v & 0xffffffffu)) <= a.seed_tol ? 1 : 0;
+            // warm start: the unit's bound of each plane of period 0 (swept from
+            // the seed with unit bound) and, L planes after each period's wrap
+            // plane, the decision. With gam = the bound after one period (a
+            // contraction of the wrap error per period) and r_p the period's
+            // relative change of the wrap plane, the seed error is at most
+            // r_0 / (1 - gam), a plane u of period 0 carries at most G_u times
+            // that, and every plane after period p-1 at most r_p / (1 - gam).
+            // The stop plane closes a window of one period whose planes all
+            // meet seed_tol.
+            if (seeded && tid == dec_thread) {
+                const int ts = t + 1 - a.L;
+                if (ts >= 0 && ts < NM && ts < 1024) {
+                    const int slot = ts % a.R;
+                    const unsigned want = (unsigned)ntl * (unsigned)(ts / a.R + 1);
+                    bool okd = wait_count_geq(a.gcnt + (long long)uidx * a.R + slot, want, a.status, a.timeout_ns);
+                    if (okd) {
+                        const unsigned long long v = ld_acquire64(a.gmax + (long long)uidx * a.R + slot);
+                        if ((unsigned)(v >> 32) != (unsigned)(ts + 1)) {
+                            atomicOr(a.status, ST_BADARG);  // ring overrun: never expected
+                            okd = false;
+                        } else {
+                            s_glog[ts] = __uint_as_float((unsigned)(v & 0xffffffffu));
+                        }
                     }
+                    if (!okd) s_ctl[0] = 1;
                 }
-                if (!okd) s_ctl[0] = 1;
+                const int tp_end = t - a.L - (NM - 1);
+                if (tp_end >= 0 && tp_end % NM == 0) {
+                    const int p = tp_end / NM, slot = p & 3;
+                    const unsigned want = (unsigned)ntl * (unsigned)(p / 4 + 1);
+                    bool okd = wait_count_geq(a.pcnt + (long long)uidx * 4 + slot, want, a.status, a.timeout_ns);
+                    if (okd) {
+                        const unsigned long long v = ld_acquire64(a.pmax + (long long)uidx * 4 + slot);
+                        if ((unsigned)(v >> 32) != (unsigned)(p + 1)) {
+                            atomicOr(a.status, ST_BADARG);
+                            okd = false;
+                        } else {
+                            const float rp = __uint_as_float((unsigned)(v & 0xffffffffu));
+                            const float gam = NM <= 1024 ? s_glog[NM - 1] : 2.f;
+                            int stop = INT_MAX;
+                            if (!(gam < 1.f)) {
+                                if (rp <= a.seed_tol) stop = t;  // no contraction shown: the plain residual test
+                            } else if (p == 0) {
+                                const float th = a.seed_tol * (1.f - gam);
+                                for (int u = 0; u < NM; ++u) {
+                                    if (s_glog[u] * rp <= th) {
+                                        stop = max(t, u + NM - 1);
+                                        break;
+                                    }
+                                }
+                            } else if (rp <= a.seed_tol * (1.f - gam)) {
+                                stop = t;
+                            }
+                            if (stop != INT_MAX) s_ctl[2] = stop;
+                        }
+                    }
+                    if (!okd) s_ctl[0] = 1;
+                }
             }
         }
         if constexpr (BND) {
@@ -723,7 +769,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             for (int o = 16; o; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
             if (lane == 0) s_wmax[warp] = gmax;
             // decision for plane t+1 (its bound is L planes old: normally complete)
-            if (tid == dec_thread && t + 1 - a.L >= 0) {
+            if (MD == 0 && tid == dec_thread && t + 1 - a.L >= 0) {
                 const int ts = t + 1 - a.L;
                 const int slot = ts % a.R;
                 const unsigned want = (unsigned)ntl * (unsigned)(ts / a.R + 1);
@@ -752,26 +798,27 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 atomicMax(a.gmax + (long long)uidx * a.R + slot, pv);
                 red_release_add(a.gcnt + (long long)uidx * a.R + slot, 1u);
             }
-        } else {
+        }
+        if constexpr (ACC) {
             if (seeded && m == m_seed && tid == 0) {  // this tile's relative change over period p
                 float dm = 0.f, im = 0.f;
                 for (int w = 0; w < NW; ++w) {
-                    dm = fmaxf(dm, s_wmax[w]);
+                    dm = fmaxf(dm, s_dmax[w]);
                     im = fmaxf(im, s_imax[w]);
                 }
                 const float rel = im > 0.f ? dm / im : (dm > 0.f ? 1.f : 0.f);
                 const int p = (t - (NM - 1)) / NM;
-                const int slot = p % a.R;
+                const int slot = p & 3;
                 const unsigned long long pv = ((unsigned long long)(unsigned)(p + 1) << 32) | __float_as_uint(rel);
-                atomicMax(a.gmax + (long long)uidx * a.R + slot, pv);
-                red_release_add(a.gcnt + (long long)uidx * a.R + slot, 1u);
+                atomicMax(a.pmax + (long long)uidx * 4 + slot, pv);
+                red_release_add(a.pcnt + (long long)uidx * 4 + slot, 1u);
             }
         }
         const int sp_old = s_prev;
         s_prev = s_cur;
         s_cur = s_next;
         s_next = sp_old;
-        if (seeded && ACC && s_ctl[1]) {  // converged (decided before the barrier): stop after this plane
+        if (seeded && ACC && t >= s_ctl[2]) {  // warm start decided (before the barrier): last plane
             if (r == 0 && tid == 0) a.unit_tacc[uidx] = t + 1 - NM;
             return 1;
         }
@@ -791,7 +838,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 cp_async_wait_all();
                 return;  // every tile of the unit stops at the same plane; nothing in flight
             }
-            if (plane_step(Flag<false>{}, t, plane_of(t, NM, sa)) == 2) {
+            if (plane_step(Mode<0>{}, t, plane_of(t, NM, sa)) == 2) {
                 cp_async_wait_all();
                 return;
             }
@@ -802,7 +849,8 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             if (tid == 0) atomicOr(a.status, ST_NOCONV);
             break;
         }
-        const int rc = plane_step(Flag<true>{}, t, plane_of(t, NM, sa));
+        const int rc = (seeded && t < NM) ? plane_step(Mode<2>{}, t, plane_of(t, NM, sa))
+                                          : plane_step(Mode<1>{}, t, plane_of(t, NM, sa));
         if (rc == 2) {
             cp_async_wait_all();
             return;
