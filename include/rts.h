@@ -190,8 +190,15 @@ typedef struct rts_handle rts_handle;
 /* Default options: RTS_FP64, tau_switch 0.1, automatic tiling, 2 s timeout. */
 void rts_default_options(rts_options *opt);
 
-/* Create a solver for one grid and band count. Allocates all device scratch.
- * opt may be NULL (defaults). */
+/* Create a solver for one grid and band count (the paper's RTS setup,
+ * Sect. 5.1: the grid, its spacing, the band count of the multi-band scheme
+ * and the 24-ray quadrature of Sect. 2; q may be NULL for that set, or give
+ * 1..24 directions with n_z != 0 and weights). Plans the direction groups and
+ * tiles, allocates all device scratch (nothing is allocated by solves) and
+ * owns it until rts_destroy. opt may be NULL (defaults). On failure *h may
+ * still be set (read rts_last_error, then rts_destroy). Errors: RTS_EINVAL
+ * (grid, band count, quadrature or options out of range; nz * nbands >
+ * 65535), RTS_ENOMEM, RTS_ECUDA. */
 rts_status rts_create(rts_handle **h, const rts_grid *g, int nbands,
                       const rts_quadrature *q, const rts_options *opt);
 
@@ -264,7 +271,10 @@ rts_status rts_check(rts_handle *h);
 int rts_device_code_version(void);
 
 /* Statistics of the last solve and, with RTS_FLAG_TIMING, mean phase times
- * of the solves since the previous call (synchronises the stream). */
+ * of the solves since the previous call (synchronises the stream): the
+ * tiling, the kernels per solve, the periodic wrap's warm-up planes (the
+ * paper's iterations of boundary intensities, Sect. 5.1) and the transpose /
+ * sweep / reduction / Q-step times (the phases of Sect. 5.3). */
 rts_status rts_get_stats(rts_handle *h, rts_stats *out);
 
 /* Text of the last error on this handle (never NULL). */
@@ -277,6 +287,10 @@ int rts_num_up(rts_handle *h);
  * this handle (0 when the handle has no register sweep). */
 long long rts_wrap_seed_elems(rts_handle *h);
 
+/* Release a handle of rts_create or rts_create_batched: its device scratch
+ * (cudaFree, which waits for the device's outstanding work), its events and
+ * copy streams (graphs of rts_graph_create are released by
+ * rts_graph_destroy). NULL is ignored. */
 void rts_destroy(rts_handle *h);
 
 /* Gradient of the scalar
