@@ -558,6 +558,7 @@ static bool reg_eligible(const std::vector<rts::SweepUnit> &units)
 {
     for (const rts::SweepUnit &U : units) {
         if (U.NP % 2 != 0 || U.NP > 2048 || U.NM < 2) return false;
+        if (U.N >= (1LL << 31)) return false;  // the kernel's in-band offsets are 32-bit
         int f = -1;
         for (int d = 0; d < rts::MAXD; ++d) {
             if (!U.active[d]) continue;

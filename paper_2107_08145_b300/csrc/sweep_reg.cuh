@@ -221,16 +221,21 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     // {chi(c), chi(c+H), S(c), S(c+H)}; record 0 is pair H-1 swapped and record
     // H+1 pair 0 swapped (the periodic neighbours of the first and last pair)
     const bool padR = act && tid == 0, padL = act && tid == H - 1;
-    auto prefetch = [&](int t, int slot) {
+    // the plane after plane mm in sweep order (periodic)
+    auto next_m = [&](int mm) { return sa > 0 ? (mm + 1 == NM ? 0 : mm + 1) : (mm == 0 ? NM - 1 : mm - 1); };
+    // (offsets within a band's array: below 2^31 points, checked on the host)
+    const int sQi = (int)sQ, sMi = (int)sM;
+    auto prefetch = [&](int mpl, int slot) {
         if (act) {
-            const long long mo = (long long)plane_of(t, NM, sa) * sM + c;
+            const int mo = mpl * sMi + c;
             float4 *row0 = XS + slot * RWS * RR;
 #pragma unroll
             for (int k = 0; k < RWS; ++k) {
                 const int q = s_q[k];
                 float *dst = reinterpret_cast<float *>(row0 + k * RR + c + 1);
                 if (q >= 0) {
-                    const float *gx = chi + mo + (long long)q * sQ, *gs = Sg + mo + (long long)q * sQ;
+                    const int off = mo + q * sQi;
+                    const float *gx = chi + off, *gs = Sg + off;
                     cp_async(dst, gx);
                     cp_async(dst + 1, gx + H);
                     cp_async(dst + 2, gs);
@@ -299,12 +304,13 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     // (shared slot t & 1): {I0, I2}, {I1, I3}, {gu, gd} pairs
     auto publish_edges = [&](int t) {
         if (isF || isL) {
+            float4 *const eo = edg(t & 1, warp, 0, 1);  // this warp's records of plane t (side 1 follows side 0)
 #pragma unroll
             for (int k = 1; k <= TQ; ++k) {
 #pragma unroll
                 for (int side = 0; side < 2; ++side) {
                     if (side == 0 ? !isF : !isL) continue;
-                    float4 *e = edg(t & 1, warp, side, k);
+                    float4 *e = eo + (side * TQ + (k - 1)) * 3;
                     e[0] = make_float4(Ip[k][0].x, Ip[k][0].y, Ip[k][2].x, Ip[k][2].y);
                     e[1] = make_float4(Ip[k][1].x, Ip[k][1].y, Ip[k][3].x, Ip[k][3].y);
                     e[2] = make_float4(Gp[k][0].x, Gp[k][0].y, Gp[k][1].x, Gp[k][1].y);
@@ -319,10 +325,9 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
 #pragma unroll
         for (int k = 1; k <= TQ; ++k) {
             if (k > nrows) break;
-            const long long off = ((long long)m * sM + (long long)(q0 + k - 1) * sQ + c) * 4;
-            *reinterpret_cast<float4 *>(part + off) = make_float4(Ip[k][0].x, Ip[k][1].x, Ip[k][2].x, Ip[k][3].x);
-            *reinterpret_cast<float4 *>(part + off + 4 * H) =
-                make_float4(Ip[k][0].y, Ip[k][1].y, Ip[k][2].y, Ip[k][3].y);
+            float4 *pp = reinterpret_cast<float4 *>(part) + (m * sMi + (q0 + k - 1) * sQi + c);
+            pp[0] = make_float4(Ip[k][0].x, Ip[k][1].x, Ip[k][2].x, Ip[k][3].x);
+            pp[H] = make_float4(Ip[k][0].y, Ip[k][1].y, Ip[k][2].y, Ip[k][3].y);
         }
         if (!itop) return;
         if (axis == 2 && sa > 0 && m == NM - 1) {  // top plane of a rising z group
@@ -361,8 +366,8 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
 
     // ---------------- prologue: plane tp = t_first - 1 (seed or boundary plane) ----
     int s_prev = (tp + 3) % 3, s_cur = (t_first + 3) % 3, s_next = (t_first + 4) % 3;
-    prefetch(tp, s_prev);
-    prefetch(t_first, s_cur);
+    prefetch(plane_of(tp, NM, sa), s_prev);
+    prefetch(plane_of(t_first, NM, sa), s_cur);
     cp_async_wait_all();
     __syncthreads();
     {
@@ -437,6 +442,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         constexpr bool BND = MD != 1;
         const bool last = ACC && !seeded && (t - t_acc == NM - 1);
         const int es = (t - 1) & 1;  // shared edge records of the previous plane
+        const float4 *const eprev = edg(es, wprev, 1, 1), *const enext = edg(es, wnext, 0, 1);
 
         const float4 *XP = XS + s_prev * RWS * RR + c + 1;   // previous plane, own record
         const float4 *XC = XS + s_cur * RWS * RR + c + 1;    // current plane
@@ -465,7 +471,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 n.gr = shfl_dn2(Gp[k][h]);
             }
             if (isF) {  // the previous warp's last thread (for c = 0: the last pair, swapped)
-                const float4 *e = edg(es, wprev, 1, k);
+                const float4 *e = eprev + (k - 1) * 3;
                 const float4 iv = e[0];
                 const float2 v = h ? f2(iv.z, iv.w) : f2(iv.x, iv.y);
                 n.il = swapL ? swp(v) : v;
@@ -476,7 +482,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 }
             }
             if (isL) {  // the next warp's first thread (for c = H-1: pair 0, swapped)
-                const float4 *e = edg(es, wnext, 0, k);
+                const float4 *e = enext + (k - 1) * 3;
                 const float4 iv = e[1];
                 const float2 v = h ? f2(iv.z, iv.w) : f2(iv.x, iv.y);
                 n.ir = swapR ? swp(v) : v;
@@ -550,7 +556,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             }
             publish_ring(t, Ip[1][2], Ip[1][3], gd1, Ip[TQ][0], Ip[TQ][1], guq);
         }
-        prefetch(t + 1, s_next);  // after the release, so that its fence does not wait for the copies
+        prefetch(next_m(m), s_next);  // after the release, so that its fence does not wait for the copies
         // ---- the other rows that need no neighbour tile ----
 #pragma unroll
         for (int k = TQ - 1; k >= 2; --k) {  // rising, downwards: row k from rows k and k-1
@@ -826,6 +832,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     };
 
     int t = t_first;
+    int mc = plane_of(t_first, NM, sa);  // plane of step t, advanced without a division
     if (wrap && !seeded) {
         for (;; ++t) {
             if (s_ctl[1]) {  // decision taken during the previous plane
@@ -838,10 +845,11 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 cp_async_wait_all();
                 return;  // every tile of the unit stops at the same plane; nothing in flight
             }
-            if (plane_step(Mode<0>{}, t, plane_of(t, NM, sa)) == 2) {
+            if (plane_step(Mode<0>{}, t, mc) == 2) {
                 cp_async_wait_all();
                 return;
             }
+            mc = next_m(mc);
         }
     }
     for (;; ++t) {
@@ -849,13 +857,13 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             if (tid == 0) atomicOr(a.status, ST_NOCONV);
             break;
         }
-        const int rc = (seeded && t < NM) ? plane_step(Mode<2>{}, t, plane_of(t, NM, sa))
-                                          : plane_step(Mode<1>{}, t, plane_of(t, NM, sa));
+        const int rc = (seeded && t < NM) ? plane_step(Mode<2>{}, t, mc) : plane_step(Mode<1>{}, t, mc);
         if (rc == 2) {
             cp_async_wait_all();
             return;
         }
         if (rc == 1) break;
+        mc = next_m(mc);
     }
     cp_async_wait_all();
 }
