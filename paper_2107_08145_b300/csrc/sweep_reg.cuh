@@ -442,7 +442,8 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         constexpr bool BND = MD != 1;
         const bool last = ACC && !seeded && (t - t_acc == NM - 1);
         const int es = (t - 1) & 1;  // shared edge records of the previous plane
-        const float4 *const eprev = edg(es, wprev, 1, 1), *const enext = edg(es, wnext, 0, 1);
+        // (warps past the last column pair read warp 0's records: in bounds, and discarded)
+        const float4 *const eprev = edg(es, wact ? wprev : 0, 1, 1), *const enext = edg(es, wact ? wnext : 0, 0, 1);
 
         const float4 *XP = XS + s_prev * RWS * RR + c + 1;   // previous plane, own record
         const float4 *XC = XS + s_cur * RWS * RR + c + 1;    // current plane
@@ -470,26 +471,33 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 n.gl = shfl_up2(Gp[k][h]);
                 n.gr = shfl_dn2(Gp[k][h]);
             }
-            if (isF) {  // the previous warp's last thread (for c = 0: the last pair, swapped)
+            // the warp-edge lanes take their outer neighbour from the records of
+            // the adjacent warps: every lane loads them (one broadcast load per
+            // record) and selects, so the warp does not diverge
+            {  // the previous warp's last thread (for c = 0: the last pair, swapped)
                 const float4 *e = eprev + (k - 1) * 3;
                 const float4 iv = e[0];
-                const float2 v = h ? f2(iv.z, iv.w) : f2(iv.x, iv.y);
-                n.il = swapL ? swp(v) : v;
+                float2 v = h ? f2(iv.z, iv.w) : f2(iv.x, iv.y);
+                v = swapL ? swp(v) : v;
+                n.il = f2(isF ? v.x : n.il.x, isF ? v.y : n.il.y);
                 if constexpr (BND) {
                     const float4 gg = e[2];
-                    const float2 g = h ? f2(gg.z, gg.w) : f2(gg.x, gg.y);
-                    n.gl = swapL ? swp(g) : g;
+                    float2 g = h ? f2(gg.z, gg.w) : f2(gg.x, gg.y);
+                    g = swapL ? swp(g) : g;
+                    n.gl = f2(isF ? g.x : n.gl.x, isF ? g.y : n.gl.y);
                 }
             }
-            if (isL) {  // the next warp's first thread (for c = H-1: pair 0, swapped)
+            {  // the next warp's first thread (for c = H-1: pair 0, swapped)
                 const float4 *e = enext + (k - 1) * 3;
                 const float4 iv = e[1];
-                const float2 v = h ? f2(iv.z, iv.w) : f2(iv.x, iv.y);
-                n.ir = swapR ? swp(v) : v;
+                float2 v = h ? f2(iv.z, iv.w) : f2(iv.x, iv.y);
+                v = swapR ? swp(v) : v;
+                n.ir = f2(isL ? v.x : n.ir.x, isL ? v.y : n.ir.y);
                 if constexpr (BND) {
                     const float4 gg = e[2];
-                    const float2 g = h ? f2(gg.z, gg.w) : f2(gg.x, gg.y);
-                    n.gr = swapR ? swp(g) : g;
+                    float2 g = h ? f2(gg.z, gg.w) : f2(gg.x, gg.y);
+                    g = swapR ? swp(g) : g;
+                    n.gr = f2(isL ? g.x : n.gr.x, isL ? g.y : n.gr.y);
                 }
             }
             return n;
