@@ -597,60 +597,35 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         if (ok) {
             const int hs = (t - 1) & 3;
             const int cm = swapL ? H - 1 : c - 1, cpp = swapR ? 0 : c + 1;
+            // every lane loads its own pair and its left and right neighbours' pairs
+            // (the same ring lines, shifted by one; no shuffle, no divergent edge
+            // lanes); c = 0 and c = H-1 take the periodic pair swapped
             if (has_lower) {  // its last row: rising slots and bound (side 1, channels 3..5)
                 const float *tl = halo_base + (long long)lower * tstride;
                 Ip[0][0] = __ldcg(ring_at(tl, hs, 3) + c);
                 Ip[0][1] = __ldcg(ring_at(tl, hs, 4) + c);
-                if constexpr (BND) Gp[0][0] = __ldcg(ring_at(tl, hs, 5) + c);
-                Nlo.il = shfl_up2(Ip[0][0]);
-                Nlo.ir = shfl_dn2(Ip[0][1]);
+                const float2 vl = __ldcg(ring_at(tl, hs, 3) + cm), vr = __ldcg(ring_at(tl, hs, 4) + cpp);
+                Nlo.il = swapL ? swp(vl) : vl;
+                Nlo.ir = swapR ? swp(vr) : vr;
                 if constexpr (BND) {
-                    Nlo.gl = shfl_up2(Gp[0][0]);
-                    Nlo.gr = shfl_dn2(Gp[0][0]);
-                }
-                if (isF) {
-                    const float2 v = __ldcg(ring_at(tl, hs, 3) + cm);
-                    Nlo.il = swapL ? swp(v) : v;
-                    if constexpr (BND) {
-                        const float2 g = __ldcg(ring_at(tl, hs, 5) + cm);
-                        Nlo.gl = swapL ? swp(g) : g;
-                    }
-                }
-                if (isL) {
-                    const float2 v = __ldcg(ring_at(tl, hs, 4) + cpp);
-                    Nlo.ir = swapR ? swp(v) : v;
-                    if constexpr (BND) {
-                        const float2 g = __ldcg(ring_at(tl, hs, 5) + cpp);
-                        Nlo.gr = swapR ? swp(g) : g;
-                    }
+                    Gp[0][0] = __ldcg(ring_at(tl, hs, 5) + c);
+                    const float2 gl = __ldcg(ring_at(tl, hs, 5) + cm), gr = __ldcg(ring_at(tl, hs, 5) + cpp);
+                    Nlo.gl = swapL ? swp(gl) : gl;
+                    Nlo.gr = swapR ? swp(gr) : gr;
                 }
             }
             if (has_upper) {  // its first row: descending slots and bound (side 0, channels 0..2)
                 const float *tu = halo_base + (long long)upper * tstride;
                 Ip[TQ + 1][2] = __ldcg(ring_at(tu, hs, 0) + c);
                 Ip[TQ + 1][3] = __ldcg(ring_at(tu, hs, 1) + c);
-                if constexpr (BND) Gp[TQ + 1][1] = __ldcg(ring_at(tu, hs, 2) + c);
-                Nup.il = shfl_up2(Ip[TQ + 1][2]);
-                Nup.ir = shfl_dn2(Ip[TQ + 1][3]);
+                const float2 vl = __ldcg(ring_at(tu, hs, 0) + cm), vr = __ldcg(ring_at(tu, hs, 1) + cpp);
+                Nup.il = swapL ? swp(vl) : vl;
+                Nup.ir = swapR ? swp(vr) : vr;
                 if constexpr (BND) {
-                    Nup.gl = shfl_up2(Gp[TQ + 1][1]);
-                    Nup.gr = shfl_dn2(Gp[TQ + 1][1]);
-                }
-                if (isF) {
-                    const float2 v = __ldcg(ring_at(tu, hs, 0) + cm);
-                    Nup.il = swapL ? swp(v) : v;
-                    if constexpr (BND) {
-                        const float2 g = __ldcg(ring_at(tu, hs, 2) + cm);
-                        Nup.gl = swapL ? swp(g) : g;
-                    }
-                }
-                if (isL) {
-                    const float2 v = __ldcg(ring_at(tu, hs, 1) + cpp);
-                    Nup.ir = swapR ? swp(v) : v;
-                    if constexpr (BND) {
-                        const float2 g = __ldcg(ring_at(tu, hs, 2) + cpp);
-                        Nup.gr = swapR ? swp(g) : g;
-                    }
+                    Gp[TQ + 1][1] = __ldcg(ring_at(tu, hs, 2) + c);
+                    const float2 gl = __ldcg(ring_at(tu, hs, 2) + cm), gr = __ldcg(ring_at(tu, hs, 2) + cpp);
+                    Nup.gl = swapL ? swp(gl) : gl;
+                    Nup.gr = swapR ? swp(gr) : gr;
                 }
             }
         }
