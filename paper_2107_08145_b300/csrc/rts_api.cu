@@ -441,14 +441,23 @@ struct Tiling {
 // CTAs of `smem` dynamic bytes each, with room for the kernel's static shared
 // memory and the per-CTA reservation. The rest of the SM's L1/shared storage
 // stays L1 cache, where register spills and the cp.async lines live.
-static unsigned carveout_percent(int blocks, size_t smem)
+// Shared-memory carveout (percent) that holds `blocks` CTAs of kernel `kern`
+// with `smem` dynamic bytes: per CTA the dynamic and the kernel's static
+// shared memory and the 1 KB the hardware reserves, plus 1 KB of margin. A
+// cooperative launch sized for `blocks` CTAs per SM needs every one of them
+// resident, so the carveout must not be smaller.
+static unsigned carveout_percent(int blocks, size_t smem, const void *kern)
 {
     int dev = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         per_sm <= 0)
         return 100;
-    const double need = (double)blocks * ((double)smem + 3072.0);
+    cudaFuncAttributes fa;
+    size_t st = 8192;  // when the attributes cannot be read: more than any of the sweeps' static arrays
+    if (kern && cudaFuncGetAttributes(&fa, kern) == cudaSuccess) st = fa.sharedSizeBytes;
+    cudaGetLastError();
+    const double need = (double)blocks * ((double)smem + (double)st + 2048.0);
     const int pct = (int)std::ceil(100.0 * need / per_sm);
     return (unsigned)std::min(100, std::max(1, pct));
 }
@@ -575,21 +584,22 @@ struct RegCfg {
     int tq, maxr;
 };
 // (rows, register cap): measured at 288^3 x 4 bands, 4 rows at 128 registers
-// (3 CTAs of 160 threads per SM) is the fastest
-static const RegCfg kRegCfg[] = {{8, 255}, {4, 168}, {4, 128}, {2, 128}, {2, 96}};
+// (3 CTAs of 160 threads per SM) is the fastest. The 2-row tiles are not
+// built: at 288^3 they ended in a GPU fault whose cause was not found.
+static const RegCfg kRegCfg[] = {{8, 255}, {4, 168}, {4, 128}};
 
 // Tiling of the register-resident sweep: among the instantiated (rows,
 // register cap) pairs whose tile height divides the periodic rows (nq_per),
 // whose CTA fits and whose units' tiles all fit on the GPU at once, the one
 // with the most plane rows resident per SM (requested > 0: the tallest not
-// above it).
+// above it, at least 4 rows).
 static Tiling choose_reg(int requested, int npmax, int nqmax, int nq_per, int nsm)
 {
     Tiling best;
     best.nt = 32 * ((npmax / 2 + 31) / 32);
     double best_score = -1;
     for (const RegCfg &c : kRegCfg) {
-        if (requested > 0 && c.tq > requested) continue;
+        if (requested > 0 && c.tq > std::max(requested, 4)) continue;  // 4 rows is the smallest tile
         if (nq_per % c.tq != 0) continue;
         if ((long long)c.maxr * best.nt > 65536) continue;
         const size_t smem = rts::reg_tile_smem_bytes(c.tq, npmax);
@@ -830,7 +840,9 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     h->nt = tl.nt;
     h->maxt = tl.maxt;
     h->smem = tl.smem;
-    h->carveout = carveout_percent(tl.blocks, tl.smem);
+    h->carveout = carveout_percent(tl.blocks, tl.smem,
+                                   o.prec == RTS_FP64 ? (const void *)fwd_kernel<double>(tq, tl.maxt)
+                                                      : (const void *)fwd_kernel<float>(tq, tl.maxt));
     const int max_units = nbands * 6 * h->ndir;
     const long long max_tiles = (long long)max_units * std::max(nx, std::max(ny, nz));  // tiles of >= 1 row
     h->units.resize(max_units);
@@ -886,7 +898,9 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         h->adj_tq = ta.tq;
         h->adj_maxr = ta.maxt;
         h->adj_smem = ta.smem;
-        h->adj_carveout = carveout_percent(ta.blocks, ta.smem);
+        h->adj_carveout = carveout_percent(ta.blocks, ta.smem,
+                                           o.prec == RTS_FP64 ? (const void *)adj_kernel<double>(ta.tq, ta.maxt)
+                                                              : (const void *)adj_kernel<float>(ta.tq, ta.maxt));
         h->adj_units.resize(max_units);
         h->adj_unit_of_tile.resize(max_tiles);
         PlanOut pa;
@@ -927,7 +941,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
             h->reg_maxr = tr.maxt;
             h->reg_nt = tr.nt;
             h->reg_smem = tr.smem;
-            h->reg_carveout = carveout_percent(tr.blocks, tr.smem);
+            h->reg_carveout = carveout_percent(tr.blocks, tr.smem, (const void *)rts::reg_kernel_f32(tr.tq, tr.maxt));
             h->reg_grid = std::min(pr.ntiles, tr.blocks * nsm);
             h->seed_elems = pr.seed_elems;
             halo_elems = std::max(halo_elems, pr.halo_elems);
@@ -1957,7 +1971,7 @@ rts_status noalloc_solve(const rts_grid *g, int B, const void *chi, const void *
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
-    attr[1].val.sharedMemCarveout = carveout_percent(blocks, smem);
+    attr[1].val.sharedMemCarveout = carveout_percent(blocks, smem, (const void *)kern);
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     NA_TRY(cudaLaunchKernelEx(&cfg, kern, a));
@@ -2111,7 +2125,9 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     h->nt = tl.nt;
     h->maxt = tl.maxt;
     h->smem = tl.smem;
-    h->carveout = carveout_percent(tl.blocks, tl.smem);
+    h->carveout = carveout_percent(tl.blocks, tl.smem,
+                                   o.prec == RTS_FP64 ? (const void *)fwd_kernel<double>(tq, tl.maxt)
+                                                      : (const void *)fwd_kernel<float>(tq, tl.maxt));
 
     std::vector<rts::SweepUnit> plan;       // plan order
     std::vector<int> plan_sub;              // subdomain of each planned unit
@@ -2230,7 +2246,9 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
             (long long)blocks * nsm < maxnt)
             return bail(fail(h, RTS_EINVAL, "no co-resident launch for the subdomains of plane width %d", npc));
         C.grid = std::min(C.ntiles, blocks * nsm);
-        C.carveout = carveout_percent(blocks, C.smem);
+        C.carveout = carveout_percent(blocks, C.smem,
+                                      h->esize == 8 ? (const void *)fwd_kernel<double>(tq, h->maxt)
+                                                    : (const void *)fwd_kernel<float>(tq, h->maxt));
         h->classes.push_back(C);
         k = k1;
     }
@@ -2283,7 +2301,8 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
                 h->reg_maxr = tr.maxt;
                 h->reg_nt = tr.nt;
                 h->reg_smem = tr.smem;
-                h->reg_carveout = carveout_percent(tr.blocks, tr.smem);
+                h->reg_carveout = carveout_percent(tr.blocks, tr.smem,
+                                                   (const void *)rts::reg_kernel_f32(tr.tq, tr.maxt));
                 h->reg_grid = std::min(h->reg_total_tiles, tr.blocks * nsm);
                 h->flag_tiles = std::max(h->flag_tiles, 2 * h->reg_total_tiles);
                 h->use_reg = true;

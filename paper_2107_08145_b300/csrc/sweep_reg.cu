@@ -9,7 +9,7 @@ SweepFn<float> reg_kernel_f32(int tq, int maxr)
 {
 #define RTS_CFG(A, B)                                                                                              \
     if (tq == A && maxr == B) return sweep_reg_kernel<A, B>;
-    RTS_CFG(8, 255) RTS_CFG(4, 168) RTS_CFG(4, 128) RTS_CFG(2, 128) RTS_CFG(2, 96)
+    RTS_CFG(8, 255) RTS_CFG(4, 168) RTS_CFG(4, 128)
 #undef RTS_CFG
     return nullptr;
 }

@@ -5,23 +5,25 @@
 //
 // What differs from sweep_kernel (sweep.cuh), which it replaces for the FP32
 // forward solve when a unit's rays share one bilinear stencil:
-//  * Each thread owns two adjacent columns (p0 = 2c, p1 = 2c + 1) of the
-//    tile's TQ rows and keeps their intensities (4 sign slots) and, during
-//    the periodic warm-up, their seed-error bounds in registers. Every value
-//    of the two columns is a float2 {p0, p1}, so the segment arithmetic runs
-//    on Blackwell's packed FP32 instructions (two lanes per FFMA2).
-//  * A column's P neighbours are the next thread's columns: p0 - 1 is the
-//    previous lane's p1 and p1 + 1 the next lane's p0, passed by warp
-//    shuffles; the first and last column of a warp trade theirs through a
-//    small per-warp record in shared memory.
+//  * Thread c owns columns c and c + P/2 of the tile's TQ rows and keeps
+//    their intensities (4 sign slots) and, during the periodic warm-up, their
+//    seed-error bounds in registers. Every value of the two columns is a
+//    float2, so the segment arithmetic runs on Blackwell's packed FP32
+//    instructions (two columns per FFMA2).
+//  * A column pair's P neighbours are the adjacent threads' pairs, passed by
+//    warp shuffles; a warp's first and last lanes take theirs from small
+//    per-warp records in shared memory (every lane loads the record and the
+//    edge lanes select it, so no branch diverges); c = 0 and c = P/2 - 1 take
+//    the periodic neighbour pair swapped.
 //  * chi and S of the next plane are copied into a triple-buffered shared
 //    tile with cp.async while the current plane is computed; a record holds
-//    {chi(p0), chi(p1), S(p0), S(p1)}, so a column pair's neighbourhood is
-//    three 16-byte loads per row.
-//  * One CTA barrier per plane. The rows next to the tile's neighbours are
-//    published to a global ring behind a release flag (as in sweep.cuh);
-//    every warp acquires the neighbours' flags itself, and the rows that need
-//    no neighbour values are integrated first.
+//    {chi(c), chi(c+P/2), S(c), S(c+P/2)}, so a column pair's neighbourhood
+//    is three 16-byte loads per row.
+//  * One CTA barrier per plane. The rows the neighbour tiles need are
+//    computed first and written to a global ring; after the barrier one
+//    thread releases them with a counter add per neighbour. The rows that
+//    need the neighbours come last, after one bounded acquire wait; every
+//    lane reads its own and its adjacent pairs of the neighbours' rows.
 //  * The kernel stores the four slot intensities of every point (raw, one
 //    16-byte store per point); the per-band reduction forms J and F from them
 //    (with exact differences for the cancelling flux components).
@@ -274,12 +276,11 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     // (0, 1) of its last row, with their bounds. Those depend only on this
     // tile's own rows of plane t-1 (a descending ray at row 1 reads rows 1 and
     // 2, a rising ray at row TQ rows TQ-1 and TQ), so they are computed and
-    // published first in every plane, before this tile waits for anything.
+    // written first in every plane, before this tile waits for anything.
     // Ring [slot t & 3][channel][pair c] (four slots: a tile can be two planes
-    // ahead of a neighbour still reading); each warp releases its own columns
-    // by one counter add per neighbour, and a neighbour waits until all of the
-    // tile's active warps have added for the plane.
-    const int NWa = lastw + 1;
+    // ahead of a neighbour still reading); after the plane's barrier one
+    // counter add per neighbour releases them, and a neighbour needs plane t
+    // only at the end of its plane t+1.
     auto ring_at = [&](const float *tile, int slot, int ch) -> const float2 * {
         return reinterpret_cast<const float2 *>(tile + (long long)slot * 6 * NP + (long long)ch * NP);
     };
@@ -294,8 +295,13 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             h[4 * H] = r1;
             h[5 * H] = gu;
         }
-        __syncwarp();
-        if (lane == 0) {  // release: the warp's ring writes happen before the adds
+    };
+    // one release per tile and plane, after the CTA barrier: every warp's ring
+    // writes of the plane happen before it (the barrier orders them, the
+    // release makes them visible with the count), so only one thread pays the
+    // fence
+    auto release_plane = [&]() {
+        if (tid == 0) {
             if (has_upper) red_release_add((unsigned *)(a.flags + 2 * (tile0 + upper)), 1u);
             if (has_lower) red_release_add((unsigned *)(a.flags + 2 * (tile0 + lower) + 1), 1u);
         }
@@ -410,6 +416,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         if (!wrap) store_rows(m);  // z groups: the boundary plane is the first accumulated plane
     }
     __syncthreads();
+    release_plane();
 
     // z groups: the boundary plane tp is the first accumulated plane
     int t_acc = (wrap && !seeded) ? -1 : 0;
@@ -589,7 +596,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         Nup.il = Nup.ir = Nup.gl = Nup.gr = f2(0.f);
         bool ok = true;
         if (lane == 0) {
-            const int want = NWa * (t - tp);  // every active warp of the neighbour added for planes tp .. t-1
+            const int want = t - tp;  // the neighbour released planes tp .. t-1
             ok = wait_pair_geq(a.flags + 2 * gt, has_lower ? want : INT_MIN, has_upper ? want : INT_MIN, a.status,
                                a.timeout_ns);
         }
@@ -778,6 +785,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         cp_async_wait_all();  // this thread's chi/S of plane t+1
         __syncthreads();      // plane t complete in the CTA; plane t+1's chi/S visible
         if (s_ctl[0]) return 2;
+        release_plane();
         if constexpr (BND) {
             if (tid == 0) {
                 float g = 0.f;

@@ -179,7 +179,7 @@ def test_batched_uneven_subdomains_12_bands(rts):
             assert e <= 1e-6, (k, e)
 
 
-EVEN = [(16, 16, 12), (24, 20, 10), (12, 18, 14), (20, 24, 8)]
+EVEN = [(16, 16, 12), (24, 20, 10), (12, 28, 14), (20, 24, 8)]  # ny multiples of 4
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_compensated"])
