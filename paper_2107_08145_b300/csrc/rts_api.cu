@@ -319,6 +319,8 @@ struct rts_handle {
     rts::RedUnit *d_ru = nullptr;
     int *d_ru_begin = nullptr;
     bool qf_ok = false;  // the register sweep's reduction (qfused.cuh) is used
+    int reg_grid_seed = 0;       // grid and carveout of the warm-start instantiation (0: none fits)
+    unsigned reg_carveout_seed = 100;
     size_t qr_smem = 0;
     int qr_grid = 0, qr_max_nat = 0, qr_max_x = 0;
     rts::RedUnit *d_qfu = nullptr;  // its units: per band the x groups first
@@ -647,8 +649,9 @@ static cudaError_t launch_sweep(rts_handle *h, const rts::SweepArgs<T> &a, bool 
 // the register-resident FP32 forward sweep over all units (its own tiling)
 static cudaError_t launch_reg_sweep(rts_handle *h, rts::SweepArgs<float> a)
 {
-    rts::SweepFn<float> kern = rts::reg_kernel_f32(h->reg_tq, h->reg_maxr);
-    if (!kern) return cudaErrorInvalidValue;
+    const bool sd = a.seed != nullptr && a.seed_in != 0;  // warm start: its own instantiation
+    rts::SweepFn<float> kern = rts::reg_kernel_f32(h->reg_tq, h->reg_maxr, sd);
+    if (!kern || (sd && h->reg_grid_seed < 1)) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->reg_smem);
     if (e != cudaSuccess) return e;
     a.units = h->d_reg_units;
@@ -656,7 +659,7 @@ static cudaError_t launch_reg_sweep(rts_handle *h, rts::SweepArgs<float> a)
     a.tile_base = 0;
     a.total_tiles = h->reg_total_tiles;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(std::min(h->reg_grid, a.total_tiles));
+    cfg.gridDim = dim3(std::min(sd ? h->reg_grid_seed : h->reg_grid, a.total_tiles));
     cfg.blockDim = dim3(h->reg_nt);
     cfg.dynamicSmemBytes = h->reg_smem;
     cfg.stream = h->stream;
@@ -664,7 +667,7 @@ static cudaError_t launch_reg_sweep(rts_handle *h, rts::SweepArgs<float> a)
     attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident
     attr[0].val.cooperative = 1;
     attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
-    attr[1].val.sharedMemCarveout = h->reg_carveout;
+    attr[1].val.sharedMemCarveout = sd ? h->reg_carveout_seed : h->reg_carveout;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, kern, a);
@@ -943,6 +946,16 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
             h->reg_smem = tr.smem;
             h->reg_carveout = carveout_percent(tr.blocks, tr.smem, (const void *)rts::reg_kernel_f32(tr.tq, tr.maxt));
             h->reg_grid = std::min(pr.ntiles, tr.blocks * nsm);
+            {  // the warm-start instantiation (more static shared memory): its own residency
+                rts::SweepFn<float> ks = rts::reg_kernel_f32(tr.tq, tr.maxt, true);
+                int bs = 0;
+                if (ks && kernel_occupancy<float>(ks, tr.nt, tr.smem, &bs) == cudaSuccess && bs > 0 &&
+                    (long long)bs * nsm >= pr.max_ntiles) {
+                    h->reg_grid_seed = std::min(pr.ntiles, bs * nsm);
+                    h->reg_carveout_seed = carveout_percent(bs, tr.smem, (const void *)ks);
+                }
+                cudaGetLastError();
+            }
             h->seed_elems = pr.seed_elems;
             halo_elems = std::max(halo_elems, pr.halo_elems);
             flag_tiles = std::max(flag_tiles, 2 * pr.ntiles);
@@ -1323,6 +1336,8 @@ static rts_status check_bc(rts_handle *h, const rts_boundary *bc)
     if (!bc) return RTS_OK;
     if (bc->wrap_seed && (!h->use_reg || h->batched))
         return fail(h, RTS_EINVAL, "the warm start (wrap_seed) needs the FP32 register sweep of a single-grid handle");
+    if (bc->wrap_seed && bc->seed_in && h->reg_grid_seed < 1)
+        return fail(h, RTS_EINVAL, "the warm-started sweep's tiles do not all fit on the GPU at once");
     if (bc->wrap_seed && !(bc->seed_tol >= 0)) return fail(h, RTS_EINVAL, "seed_tol must be >= 0");
     if (bc->bottom < RTS_BC_ZERO || bc->bottom > RTS_BC_EXPLICIT || bc->top < RTS_BC_ZERO || bc->top > RTS_BC_EXPLICIT)
         return fail(h, RTS_EINVAL, "unknown boundary kind");

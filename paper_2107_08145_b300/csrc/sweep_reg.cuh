@@ -131,7 +131,9 @@ __device__ __forceinline__ float reg_bc(int kind, const float *arr, int udx, int
     return arr[((long long)udx * ny + j) * nx + i];
 }
 
-template <int TQ>
+// SEED: the instantiation for warm-started solves (rts_boundary.wrap_seed
+// with seed_in); the plain one carries none of that code.
+template <int TQ, bool SEED>
 __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restrict__ Ug, int uidx, int r, int gt,
                              unsigned char *smem)
 {
@@ -177,7 +179,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     };
 
     __shared__ float s_wmax[32], s_imax[32], s_dmax[32];
-    __shared__ float s_glog[1024];               // warm start: the unit's bound of every plane of period 0
+    __shared__ float s_glog[SEED ? 1024 : 1];    // warm start: the unit's bound of every plane of period 0
     __shared__ int s_ctl[4];                     // 0 abort, 1 wrap decision for the next plane, 2 warm start: last plane
     __shared__ int s_q[RWS];                     // grid row of shared row k, -1 outside
 
@@ -216,7 +218,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     const int kb = (wrap && q0 + nrows == NQ) ? nrows : 0;
     // warm start (x/y groups): the unit's wrap plane in the caller's buffer
     float *const sbuf = (wrap && a.seed) ? a.seed + Ug->seed_off : nullptr;
-    const bool seeded = sbuf != nullptr && a.seed_in != 0;
+    const bool seeded = SEED && sbuf != nullptr && a.seed_in != 0;
     const int m_seed = plane_of(-1, NM, sa);
 
     // chi and S of plane t into shared slot `slot`: record c + 1 of row k holds
@@ -848,7 +850,11 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             if (tid == 0) atomicOr(a.status, ST_NOCONV);
             break;
         }
-        const int rc = (seeded && t < NM) ? plane_step(Mode<2>{}, t, mc) : plane_step(Mode<1>{}, t, mc);
+        int rc;
+        if constexpr (SEED)
+            rc = (seeded && t < NM) ? plane_step(Mode<2>{}, t, mc) : plane_step(Mode<1>{}, t, mc);
+        else
+            rc = plane_step(Mode<1>{}, t, mc);
         if (rc == 2) {
             cp_async_wait_all();
             return;
@@ -859,7 +865,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     cp_async_wait_all();
 }
 
-template <int TQ, int MAXR>
+template <int TQ, int MAXR, bool SEED>
 __global__ void __maxnreg__(MAXR) sweep_reg_kernel(SweepArgs<float> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -875,7 +881,7 @@ __global__ void __maxnreg__(MAXR) sweep_reg_kernel(SweepArgs<float> a)
         if (s_tile < 0 || s_tile >= a.total_tiles) return;
         const int tile = a.tile_base + s_tile;
         const int u = a.unit_of_tile[tile];
-        run_tile_reg<TQ>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
+        run_tile_reg<TQ, SEED>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
     }
 }
 
