@@ -38,6 +38,24 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
     e = __fmaf_rn(a, b, -p);
 }
 
+// packed FP32 pairs: one instruction for both lanes, each lane rounded as its
+// scalar form (Blackwell's FFMA2 / FMUL2 / FADD2)
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as one packed FMA (b times -1 is exact, so a single rounding of a - b)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
+
+// two_sum on both lanes
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = add2(a, b);
+    const float2 bb = sub2(s, a);
+    e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+
 __device__ __forceinline__ df32 df_make(float a) { return {a, 0.f}; }
 
 __device__ __forceinline__ df32 df_add(df32 a, df32 b)

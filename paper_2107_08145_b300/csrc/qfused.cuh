@@ -15,6 +15,18 @@
 // Rump and Oishi, as accurate as summing in twice the precision), written as
 // double-float J_b, F_b ([b][c][N], the layout qstep_kernel<float, df32>
 // reads). No FP64 arithmetic: B300's FP64 rate would bound this step.
+//
+// The kernel is issue-bound unless its instruction count per point is small,
+// so: each thread owns two points of a tile and runs every operation on the
+// pair as one packed FP32x2 instruction (lane-wise the same roundings as
+// the scalar form, so the result is the scalar kernel's to the bit); the
+// slot pairing of each moment is fixed at compile time per group of units
+// (a unit's own flux component across its sweep axis pairs slots (0,2) and
+// (1,3): F_z for x and y units, F_y for z units; the host checks that
+// every unit's table agrees), so the unit loop has no branch; the
+// coefficients sit in shared memory already duplicated for both lanes and
+// with the negated ones the exact product errors need; a tile's index is
+// decoded once and its copy offsets computed once for all its units.
 #pragma once
 #include "qstep.cuh"
 
@@ -22,16 +34,25 @@ namespace rts {
 
 constexpr int QR_TI = 32;  // tile extent in i (threads in x)
 constexpr int QR_TJ = 16;  // tile extent in j
-constexpr int QR_RY = 8;   // threads in y: each owns QR_TJ / QR_RY points
+constexpr int QR_RY = 8;   // threads in y: each owns QR_TJ / QR_RY = 2 points
 constexpr int QR_NT = QR_TI * QR_RY;
 constexpr int QR_NAT = QR_TJ * QR_TI;         // float4 of a natural unit's tile
 constexpr int QR_XR = QR_TJ + 1;              // padded row of an x group's tile
 constexpr int QR_XU = QR_TI * QR_XR;          // float4 of an x group's tile
+constexpr int QR_KU = 13;                     // float4 of a unit's shared record
+static_assert(QR_TJ == 2 * QR_RY, "each thread owns two points of a tile");
 
-// shared memory: two buffers of the largest band's units, then the units
-__host__ __device__ constexpr size_t qr_smem_bytes(int max_nat, int max_x, int nunits)
+// the moment whose slot pairing is (0,2)+(1,3) for units sweeping along
+// axis a (the component along the unit's second transverse axis)
+__host__ __device__ constexpr int qr_cross_moment(int axis) { return axis == 2 ? 2 : 3; }
+
+// shared memory: two buffers of the largest band's units, the unit records
+// (partial pointer, then per moment three float4 of duplicated
+// coefficients) and the band table (3 B + 1 ints)
+__host__ __device__ constexpr size_t qr_smem_bytes(int max_nat, int max_x, int nunits, int nbands)
 {
-    return (size_t)2 * (max_nat * QR_NAT + max_x * QR_XU) * sizeof(float4) + sizeof(RedUnit) * (size_t)nunits;
+    return (size_t)2 * (max_nat * QR_NAT + max_x * QR_XU) * sizeof(float4) +
+           sizeof(float4) * QR_KU * (size_t)nunits + ((size_t)(3 * nbands + 1) * sizeof(int) + 15) / 16 * 16;
 }
 
 // 16-byte copy global -> shared; src_bytes 0 fills zeros (the source is not read)
@@ -44,129 +65,162 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src,
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// a x + b y on both lanes, as pair_sum: p = b y rounded, the exact error
+// b y - p recovered as -(p - b y) = -fma(-b, y, p), added to fma(a, x, p)
+__device__ __forceinline__ float2 pair_sum2(float2 a, float2 x, float2 b, float2 nb, float2 y)
+{
+    const float2 p = mul2(b, y);
+    return sub2(fma2(a, x, p), fma2(nb, y, p));
+}
+
+// one unit's four moments at the thread's two points, added to (s, e). K:
+// the unit's record; per moment c three float4 (a1 a1 b1 b1), (-b1 -b1 a2
+// a2), (b2 b2 -b2 -b2) for the pairs (a1, b1) + (a2, b2) of its pairing.
+template <int QC>
+__device__ __forceinline__ void qr_unit(const float4 *__restrict__ K, float4 A, float4 B, float2 (&s)[4],
+                                        float2 (&e)[4])
+{
+    const float2 I0 = f2(A.x, B.x), I1 = f2(A.y, B.y), I2 = f2(A.z, B.z), I3 = f2(A.w, B.w);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float4 q0 = K[1 + 3 * c], q1 = K[2 + 3 * c], q2 = K[3 + 3 * c];
+        const float2 m = add2(pair_sum2(f2(q0.x, q0.y), I0, f2(q0.z, q0.w), f2(q1.x, q1.y), c == QC ? I2 : I1),
+                              pair_sum2(f2(q1.z, q1.w), c == QC ? I1 : I2, f2(q2.x, q2.y), f2(q2.z, q2.w), I3));
+        float2 s2, e2;
+        two_sum2(s[c], m, s2, e2);
+        s[c] = s2;
+        e[c] = add2(e[c], e2);
+    }
+}
+
 // qb: [0 .. B] first unit of each band, [B+1 .. 2B] end of the band's x
-// groups (each band's units are ordered x groups first)
+// groups, [2B+1 .. 3B] end of its y units (each band's units are ordered
+// x groups, y units, z units)
 __global__ void __launch_bounds__(QR_NT, 2) qf_reduce_kernel(const RedUnit *__restrict__ ru,
                                                                const int *__restrict__ qb, int nx, int ny, int nz,
                                                                int nbands, int nunits, int max_nat, int max_x,
                                                                df32 *__restrict__ JF)
 {
-    constexpr int RP = QR_TJ / QR_RY;
     extern __shared__ __align__(16) float4 qr_sm[];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * QR_TI + tx;
-    // the units' coefficients, read by every thread of the CTA (broadcast loads)
-    RedUnit *su = reinterpret_cast<RedUnit *>(qr_sm + 2 * (max_nat * QR_NAT + max_x * QR_XU));
-    {
-        const int words = (int)(sizeof(RedUnit) / 4) * nunits;
-        const int *src = reinterpret_cast<const int *>(ru);
-        int *dst = reinterpret_cast<int *>(su);
-        for (int w = tid; w < words; w += QR_NT) dst[w] = src[w];
+    const int buf = max_nat * QR_NAT + max_x * QR_XU;
+    float4 *sk = qr_sm + 2 * buf;  // unit records, read by every thread (broadcast loads)
+    int *sq = reinterpret_cast<int *>(sk + QR_KU * nunits);
+    for (int w = tid; w < QR_KU * nunits; w += QR_NT) {
+        const int u = w / QR_KU, q = w % QR_KU;
+        const RedUnit &U = ru[u];
+        float4 v;
+        if (q == 0) {
+            v = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<const void **>(&v) = U.partial;
+        } else {
+            const int c = (q - 1) / 3, f = (q - 1) % 3;
+            const float *k = U.c[c];
+            const int a1 = 0, b1 = U.qpair[c] ? 2 : 1, a2 = U.qpair[c] ? 1 : 2, b2 = 3;
+            if (f == 0) v = make_float4(k[a1], k[a1], k[b1], k[b1]);
+            else if (f == 1) v = make_float4(-k[b1], -k[b1], k[a2], k[a2]);
+            else v = make_float4(k[b2], k[b2], -k[b2], -k[b2]);
+        }
+        sk[w] = v;
     }
+    for (int w = tid; w < 3 * nbands + 1; w += QR_NT) sq[w] = qb[w];
+    __syncthreads();
+
     const long long N = (long long)nx * ny * nz;
     const int nti = (nx + QR_TI - 1) / QR_TI, ntj = (ny + QR_TJ - 1) / QR_TJ;
     const int ntiles = nti * ntj * nz * nbands;  // < 2^31: checked on the host
-    const int buf = max_nat * QR_NAT + max_x * QR_XU;
     // x groups are copied along j: point (xi + 16 r, xj) of the tile
     const int xj = tid % QR_TJ, xi = tid / QR_TJ;
     constexpr int XR = QR_NT / QR_TJ;
+    // the thread's shared offsets of its two points: natural, x group
+    const int on0 = ty * QR_TI + tx, on1 = on0 + QR_RY * QR_TI;
+    const int ox0 = tx * QR_XR + ty, ox1 = ox0 + QR_RY;
+    const int cn0 = ty * QR_TI + tx, cx0 = xi * QR_XR + xj;  // its copy destinations
 
     // tile t: i tile fastest, then j tile, level, band
-    auto decode = [&](int t, int &ti, int &tj, int &k, int &b) {
-        ti = t % nti;
+    auto decode = [&](int t) {
+        int4 d;
+        d.x = t % nti;
         t /= nti;
-        tj = t % ntj;
+        d.y = t % ntj;
         t /= ntj;
-        k = t % nz;
-        b = t / nz;
+        d.z = t % nz;
+        d.w = t / nz;
+        return d;
     };
-    auto issue = [&](int t, int half) {
-        if (t < ntiles) {
-            int ti, tj, k, b;
-            decode(t, ti, tj, k, b);
-            const int i0 = ti * QR_TI, j0 = tj * QR_TJ;
-            const int ub = qb[b], ux = qb[nbands + 1 + b], ue = qb[b + 1];
-            float4 *sb = qr_sm + (long long)half * buf;
-            for (int u = ux; u < ue; ++u) {  // natural: [j][i]
-                const float4 *part = reinterpret_cast<const float4 *>(ru[u].partial);
-                float4 *dst = sb + (u - ux) * QR_NAT;
+    auto issue = [&](bool live, int4 d, int half) {
+        if (live) {
+            const int i0 = d.x * QR_TI, j0 = d.y * QR_TJ, k = d.z, b = d.w;
+            const int ub = sq[b], ux = sq[nbands + 1 + b], ue = sq[b + 1];
+            float4 *sb = qr_sm + half * buf;
+            // the point offsets (float4) and source sizes of this tile, for all units
+            long long gn[2], gx[2];
+            int zn[2], zx[2];
 #pragma unroll
-                for (int r = 0; r < RP; ++r) {
-                    const int i = i0 + tx, j = j0 + ty + QR_RY * r;
-                    const bool in = i < nx && j < ny;
-                    cp_async16(dst + (ty + QR_RY * r) * QR_TI + tx,
-                               part + (in ? ((long long)k * ny + j) * nx + i : 0), in ? 16 : 0);
-                }
+            for (int r = 0; r < 2; ++r) {
+                const int i = i0 + tx, j = j0 + ty + QR_RY * r;
+                const bool in = i < nx && j < ny;
+                gn[r] = in ? ((long long)k * ny + j) * nx + i : 0;
+                zn[r] = in ? 16 : 0;
+                const int ii = i0 + xi + XR * r, jj = j0 + xj;
+                const bool inx = ii < nx && jj < ny;
+                gx[r] = inx ? ((long long)ii * nz + k) * ny + jj : 0;
+                zx[r] = inx ? 16 : 0;
+            }
+            for (int u = ux; u < ue; ++u) {  // natural: [j][i]
+                const float4 *part = *reinterpret_cast<const float4 *const *>(sk + QR_KU * u);
+                float4 *dst = sb + (u - ux) * QR_NAT + cn0;
+                cp_async16(dst, part + gn[0], zn[0]);
+                cp_async16(dst + QR_RY * QR_TI, part + gn[1], zn[1]);
             }
             for (int u = ub; u < ux; ++u) {  // x groups: [i][j], rows padded
-                const float4 *part = reinterpret_cast<const float4 *>(ru[u].partial);
-                float4 *dst = sb + max_nat * QR_NAT + (u - ub) * QR_XU;
-#pragma unroll
-                for (int r = 0; r < RP; ++r) {
-                    const int i = i0 + xi + XR * r, j = j0 + xj;
-                    const bool in = i < nx && j < ny;
-                    cp_async16(dst + (xi + XR * r) * QR_XR + xj,
-                               part + (in ? ((long long)i * nz + k) * ny + j : 0), in ? 16 : 0);
-                }
+                const float4 *part = *reinterpret_cast<const float4 *const *>(sk + QR_KU * u);
+                float4 *dst = sb + max_nat * QR_NAT + (u - ub) * QR_XU + cx0;
+                cp_async16(dst, part + gx[0], zx[0]);
+                cp_async16(dst + XR * QR_XR, part + gx[1], zx[1]);
             }
         }
         cp_async_commit_group();
     };
 
     int t = blockIdx.x;
-    issue(t, 0);
+    int4 cur = decode(t < ntiles ? t : 0);
+    issue(t < ntiles, cur, 0);
     for (int n = 0; t < ntiles; ++n, t += gridDim.x) {
-        issue(t + (int)gridDim.x, (n + 1) & 1);
+        const int tn = t + (int)gridDim.x;
+        const int4 nxt = decode(tn < ntiles ? tn : 0);
+        issue(tn < ntiles, nxt, (n + 1) & 1);
         cp_async_wait_prev();
         __syncthreads();  // tile t in shared memory
-        int ti, tj, k, b;
-        decode(t, ti, tj, k, b);
-        const int ub = qb[b], ux = qb[nbands + 1 + b], ue = qb[b + 1];
-        const float4 *sb = qr_sm + (long long)(n & 1) * buf;
-        // per point and moment: the running sum s and the sum e of the rounding
-        // errors of its additions (each exact by TwoSum), s + e at the end
-        float sm[RP][4], se[RP][4];
+        const int b = cur.w;
+        const int ub = sq[b], ux = sq[nbands + 1 + b], uy = sq[2 * nbands + 1 + b], ue = sq[b + 1];
+        const float4 *sb = qr_sm + (n & 1) * buf;
+        // per point pair and moment: the running sum s and the sum e of the
+        // rounding errors of its additions (each exact by TwoSum), s + e at the end
+        float2 s[4], e[4];
 #pragma unroll
-        for (int r = 0; r < RP; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) sm[r][c] = se[r][c] = 0.f;
-        for (int u = ub; u < ue; ++u) {
-            const RedUnit &U = su[u];
-            const bool xg = u < ux;
-            const float4 *src = xg ? sb + max_nat * QR_NAT + (u - ub) * QR_XU : sb + (u - ux) * QR_NAT;
-#pragma unroll
-            for (int r = 0; r < RP; ++r) {
-                const int jj = ty + QR_RY * r;
-                const float4 I = xg ? src[tx * QR_XR + jj] : src[jj * QR_TI + tx];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    // the moment with the unit's pairing (a unit-wide branch)
-                    const float *kc = U.c[c];
-                    float m;
-                    if (U.qpair[c])
-                        m = pair_sum(kc[0], I.x, kc[2], I.z) + pair_sum(kc[1], I.y, kc[3], I.w);
-                    else
-                        m = pair_sum(kc[0], I.x, kc[1], I.y) + pair_sum(kc[2], I.z, kc[3], I.w);
-                    float s2, e2;
-                    two_sum(sm[r][c], m, s2, e2);
-                    sm[r][c] = s2;
-                    se[r][c] += e2;
-                }
-            }
+        for (int c = 0; c < 4; ++c) s[c] = e[c] = f2(0.f);
+        {
+            const float4 *src = sb + max_nat * QR_NAT;
+            for (int u = ub; u < ux; ++u, src += QR_XU)
+                qr_unit<qr_cross_moment(0)>(sk + QR_KU * u, src[ox0], src[ox1], s, e);
         }
-        const int i = ti * QR_TI + tx;
-        df32 *jf = JF + (long long)b * 4 * N;
+        const float4 *src = sb;
+        for (int u = ux; u < uy; ++u, src += QR_NAT)
+            qr_unit<qr_cross_moment(1)>(sk + QR_KU * u, src[on0], src[on1], s, e);
+        for (int u = uy; u < ue; ++u, src += QR_NAT)
+            qr_unit<qr_cross_moment(2)>(sk + QR_KU * u, src[on0], src[on1], s, e);
+        const int i = cur.x * QR_TI + tx, j = cur.y * QR_TJ + ty;
+        df32 *jf = JF + (long long)b * 4 * N + ((long long)cur.z * ny + j) * nx + i;
+        const bool in0 = i < nx && j < ny, in1 = i < nx && j + QR_RY < ny;
 #pragma unroll
-        for (int r = 0; r < RP; ++r) {
-            const int j = tj * QR_TJ + ty + QR_RY * r;
-            if (i >= nx || j >= ny) continue;
-            const long long p = ((long long)k * ny + j) * nx + i;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                df32 v;
-                two_sum(sm[r][c], se[r][c], v.hi, v.lo);
-                jf[c * N + p] = v;
-            }
+        for (int c = 0; c < 4; ++c) {
+            float2 hi, lo;
+            two_sum2(s[c], e[c], hi, lo);
+            if (in0) jf[c * N] = df32{hi.x, lo.x};
+            if (in1) jf[c * N + QR_RY * nx] = df32{hi.y, lo.y};
         }
+        cur = nxt;
         __syncthreads();  // buffer n & 1 is refilled by the next iteration's copies
     }
 }

@@ -324,7 +324,7 @@ struct rts_handle {
     size_t qr_smem = 0;
     int qr_grid = 0, qr_max_nat = 0, qr_max_x = 0;
     rts::RedUnit *d_qfu = nullptr;  // its units: per band the x groups first
-    int *d_qfb = nullptr;           // band begins [B+1], then the ends of each band's x groups [B]
+    int *d_qfb = nullptr;           // band begins [B+1], the ends of each band's x groups [B], of its y units [B]
     // adjoint scratch (RTS_FLAG_ADJOINT): lam0 [B][N][4] natural and
     // x-transposed, direct Q-step terms [B][2][N], and per checkpoint chunk of
     // at most chunk_units units: the checkpoint [u][N][STORE_CH*4] and the
@@ -994,7 +994,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_ru = take(sizeof(rts::RedUnit) * h->units.size());
     const size_t o_rub = take(sizeof(int) * (nbands + 1));
     const size_t o_qfu = take(sizeof(rts::RedUnit) * h->units.size());
-    const size_t o_qfb = take(sizeof(int) * (2 * nbands + 1));
+    const size_t o_qfb = take(sizeof(int) * (3 * nbands + 1));
     const bool log_chi = (o.flags & RTS_FLAG_LOG_CHI) != 0;
     const size_t o_cexp = log_chi ? take((size_t)nbands * h->N * es) : 0;
     const bool scatter = (o.flags & RTS_FLAG_SCATTER) != 0;
@@ -1118,18 +1118,24 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     CUDA_TRY(h, cudaMemcpy(h->d_ru, ru.data(), sizeof(rts::RedUnit) * ru.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(h, cudaMemcpy(h->d_ru_begin, rub.data(), sizeof(int) * rub.size(), cudaMemcpyHostToDevice));
     if (h->use_reg) {
-        // the streaming reduction of the register sweep's raw partials: per band the x groups first
+        // the streaming reduction of the register sweep's raw partials: per
+        // band the x groups, then the y units, then the z units
         {
             std::vector<rts::RedUnit> qfu;
-            std::vector<int> qfb(2 * nbands + 1, 0);
+            std::vector<int> qfb(3 * nbands + 1, 0);
+            bool pairing_ok = true;  // each unit pairs slots as its group's code assumes
             for (int b = 0; b < nbands; ++b) {
                 qfb[b] = (int)qfu.size();
-                for (int pass = 0; pass < 2; ++pass)
-                    for (int u = rub[b]; u < rub[b + 1]; ++u)
-                        if ((ru[u].axis == 0) == (pass == 0)) qfu.push_back(ru[u]);
-                int nxu = 0;
-                for (int u = rub[b]; u < rub[b + 1]; ++u) nxu += ru[u].axis == 0;
-                qfb[nbands + 1 + b] = qfb[b] + nxu;
+                for (int axis = 0; axis < 3; ++axis) {
+                    for (int u = rub[b]; u < rub[b + 1]; ++u) {
+                        if (ru[u].axis != axis) continue;
+                        qfu.push_back(ru[u]);
+                        for (int c = 0; c < 4; ++c)
+                            pairing_ok &= (ru[u].qpair[c] != 0) == (c == rts::qr_cross_moment(axis));
+                    }
+                    if (axis == 0) qfb[nbands + 1 + b] = (int)qfu.size();
+                    if (axis == 1) qfb[2 * nbands + 1 + b] = (int)qfu.size();
+                }
             }
             qfb[nbands] = (int)qfu.size();
             CUDA_TRY(h, cudaMemcpy(h->d_qfu, qfu.data(), sizeof(rts::RedUnit) * qfu.size(), cudaMemcpyHostToDevice));
@@ -1138,11 +1144,12 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
                 h->qr_max_x = std::max(h->qr_max_x, qfb[nbands + 1 + b] - qfb[b]);
                 h->qr_max_nat = std::max(h->qr_max_nat, qfb[b + 1] - qfb[nbands + 1 + b]);
             }
-            h->qr_smem = rts::qr_smem_bytes(h->qr_max_nat, h->qr_max_x, (int)qfu.size());
+            h->qr_smem = rts::qr_smem_bytes(h->qr_max_nat, h->qr_max_x, (int)qfu.size(), nbands);
             int per_sm = 0;
             const long long qr_tiles = (long long)((nx + rts::QR_TI - 1) / rts::QR_TI) *
                                        ((ny + rts::QR_TJ - 1) / rts::QR_TJ) * nz * nbands;
-            if (h->qr_smem <= 113 * 1024 && qr_tiles < (1LL << 31) - (1LL << 20) &&
+            if (pairing_ok && qfu.size() == h->units.size() && h->qr_smem <= 113 * 1024 &&
+                qr_tiles < (1LL << 31) - (1LL << 20) &&
                 cudaFuncSetAttribute(rts::qf_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)h->qr_smem) == cudaSuccess &&
                 cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rts::qf_reduce_kernel, rts::QR_NT,

@@ -33,6 +33,7 @@
 // set), the plane extent P is even, and the tile height divides the extent of
 // the periodic z-group rows.
 #pragma once
+#include "df32.cuh"
 #include "sweep.cuh"
 
 namespace rts {
@@ -48,13 +49,6 @@ constexpr float kQPolyY[5] = {(float)kQPolyX[0], (float)(kQPolyX[1] * -kLn2), (f
                               (float)(kQPolyX[4] * kLn2 * kLn2 * kLn2 * kLn2)};
 constexpr float kYSwitch = (float)(-0.25 * kLog2e);  // x < 1/4  <=>  y > kYSwitch
 
-__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-// a - b as one packed FMA
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f), a); }
 __device__ __forceinline__ float2 max2(float2 a, float2 b) { return f2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
 // hardware approximations (PTX ex2.approx / rcp.approx)
 __device__ __forceinline__ float ex2_approx(float x)
