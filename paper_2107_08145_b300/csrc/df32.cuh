@@ -103,6 +103,94 @@ __device__ __forceinline__ df32 df_mul(df32 a, df32 b)
 
 __device__ __forceinline__ double df_to_double(df32 a) { return (double)a.hi + (double)a.lo; }
 
+// Double-float values of two points (lane x: the first, lane y: the second),
+// each operation the df32 one above lane by lane with the same roundings.
+// Negated operands are passed in where an error term needs one, so that the
+// exact product errors come out negated (fma(a, -b, p) = -(a b - p)) and no
+// packed negation is spent; results differ from the scalar forms at most in
+// the sign of a zero.
+struct df2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ float2 neg2(float2 a) { return mul2(a, f2(-1.f)); }
+__device__ __forceinline__ df2 df2_neg(df2 a) { return {neg2(a.hi), neg2(a.lo)}; }
+__device__ __forceinline__ void fast_two_sum2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = add2(a, b);
+    e = sub2(b, sub2(s, a));
+}
+// s + e = a - b exactly (two_sum of a and -b)
+__device__ __forceinline__ void two_diff2(float2 a, float2 b, float2 &s, float2 &e)
+{
+    s = sub2(a, b);
+    const float2 bb = sub2(s, a);
+    e = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+// p + e with e given negated (ne = -e): fast_two_sum(p, e)
+__device__ __forceinline__ df2 fast_two_sum2_ne(float2 p, float2 ne)
+{
+    const float2 s = sub2(p, ne);
+    return {s, fma2(ne, f2(-1.f), sub2(p, s))};
+}
+__device__ __forceinline__ df2 df2_add(df2 a, df2 b)
+{
+    float2 s, e, t, f;
+    two_sum2(a.hi, b.hi, s, e);
+    two_sum2(a.lo, b.lo, t, f);
+    e = add2(e, t);
+    fast_two_sum2(s, e, s, e);
+    e = add2(e, f);
+    fast_two_sum2(s, e, s, e);
+    return {s, e};
+}
+__device__ __forceinline__ df2 df2_sub(df2 a, df2 b)
+{
+    float2 s, e, t, f;
+    two_diff2(a.hi, b.hi, s, e);
+    two_diff2(a.lo, b.lo, t, f);
+    e = add2(e, t);
+    fast_two_sum2(s, e, s, e);
+    e = add2(e, f);
+    fast_two_sum2(s, e, s, e);
+    return {s, e};
+}
+// a - (b, 0): the low-part steps of df_sub with a zero there are identities
+__device__ __forceinline__ df2 df2_sub(df2 a, float2 b)
+{
+    float2 s, e;
+    two_diff2(a.hi, b, s, e);
+    e = add2(e, a.lo);
+    fast_two_sum2(s, e, s, e);
+    return {s, e};
+}
+// a * b, nb = -b
+__device__ __forceinline__ df2 df2_mul(df2 a, df2 b, df2 nb)
+{
+    const float2 p = mul2(a.hi, b.hi);
+    float2 ne = fma2(a.hi, nb.hi, p);
+    ne = fma2(a.hi, nb.lo, ne);
+    ne = fma2(a.lo, nb.hi, ne);
+    return fast_two_sum2_ne(p, ne);
+}
+// (x, 0) * b, nx = -x (the zero low part's product is dropped)
+__device__ __forceinline__ df2 df2_mul(float2 x, float2 nx, df2 b)
+{
+    const float2 p = mul2(x, b.hi);
+    float2 ne = fma2(nx, b.hi, p);
+    ne = fma2(nx, b.lo, ne);
+    return fast_two_sum2_ne(p, ne);
+}
+// a * (y, 0), na = -a (the zero low part's product is dropped)
+__device__ __forceinline__ df2 df2_mul(df2 a, df2 na, float2 y)
+{
+    const float2 p = mul2(a.hi, y);
+    float2 ne = fma2(na.hi, y, p);
+    ne = fma2(na.lo, y, ne);
+    return fast_two_sum2_ne(p, ne);
+}
+__device__ __forceinline__ df2 df2_splat(df32 a) { return {f2(a.hi), f2(a.lo)}; }
+__device__ __forceinline__ df2 df2_pair(df32 a, df32 b) { return {f2(a.hi, b.hi), f2(a.lo, b.lo)}; }
+
 // Arithmetic-type shims so the Q step is written once for double and df32.
 __device__ __forceinline__ double acc_zero(double *) { return 0.0; }
 __device__ __forceinline__ df32 acc_zero(df32 *) { return {0.f, 0.f}; }

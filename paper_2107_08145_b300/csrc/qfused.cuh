@@ -225,4 +225,111 @@ __global__ void __launch_bounds__(QR_NT, 2) qf_reduce_kernel(const RedUnit *__re
     }
 }
 
+// The Q step over double-float J_b, F_b (qstep_kernel<float, df32>'s
+// arithmetic, Sect. 5.1's Q_rad = sum_b [om_b 4 pi chi_b (J_b - S_b) +
+// (1 - om_b)(-div F_b)] with the band sums of J and F), two points per
+// thread -- (i, j) and (i, j + 8) of a 32 x 16 tile of one level -- so that
+// the double-float operations run packed and each thread has both points'
+// loads in flight. Up to the sign of a zero, the results are those of the
+// one-point kernel.
+constexpr int QS_TJ = 16;
+// the double-float stencil and 4 pi constants of qstep_kernel<float, df32>
+// (acc_from of the FP64 values), splatted on both lanes with their negations
+struct Acc2Const {
+    df2 cx, ncx, cy, ncy, cz, ncz, four_pi, nfour_pi;
+    float thin;
+    __device__ __forceinline__ Acc2Const(const QParams &P, int k)
+    {
+        df32 *tag = nullptr;
+        cx = df2_splat(acc_from(tag, P.inv2dx));
+        cy = df2_splat(acc_from(tag, P.inv2dy));
+        cz = df2_splat(z_coef<df32>(P, k));
+        four_pi = df2_splat(acc_from(tag, 12.566370614359172953850573533118));
+        ncx = df2_neg(cx);
+        ncy = df2_neg(cy);
+        ncz = df2_neg(cz);
+        nfour_pi = df2_neg(four_pi);
+        thin = (float)P.thin;
+    }
+};
+__global__ void __launch_bounds__(256, 3) qstep_df2_kernel(const df32 *__restrict__ JF, const float *__restrict__ chi,
+                                                        const float *__restrict__ S, QParams P,
+                                                        double *__restrict__ J, double *__restrict__ F,
+                                                        double *__restrict__ Q)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x, j0 = blockIdx.y * QS_TJ + threadIdx.y, k = blockIdx.z;
+    if (i >= P.nx || j0 >= P.ny) return;
+    const bool two = j0 + QS_TJ / 2 < P.ny;
+    const int j1 = two ? j0 + QS_TJ / 2 : j0;  // outside the grid: the first point again, not stored
+    const int nx = P.nx, ny = P.ny, nz = P.nz;
+    const long long N = (long long)nx * ny * nz;
+    // the two points and their neighbours (periodic in x and y; one-sided
+    // differences at the bottom and top levels); in-band offsets are below
+    // N < 2^31 (the register sweep serves no larger band)
+    int p[2], xp[2], xm[2], yp[2], ym[2];
+    const int jj[2] = {j0, j1};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int j = jj[r];
+        p[r] = (k * ny + j) * nx + i;
+        xp[r] = p[r] - i + (i + 1 == nx ? 0 : i + 1);
+        xm[r] = p[r] - i + (i == 0 ? nx - 1 : i - 1);
+        yp[r] = p[r] + ((j + 1 == ny ? 0 : j + 1) - j) * nx;
+        ym[r] = p[r] + ((j == 0 ? ny - 1 : j - 1) - j) * nx;
+    }
+    int dzp, dzm;  // z neighbours as offsets from the point
+    if (nz == 1) { dzp = dzm = 0; }
+    else if (k == 0) { dzp = nx * ny; dzm = 0; }
+    else if (k == nz - 1) { dzp = 0; dzm = -nx * ny; }
+    else { dzp = nx * ny; dzm = -nx * ny; }
+    Acc2Const K(P, k);
+    auto ld2 = [&](const df32 *a, int o0, int o1) { return df2_pair(a[o0], a[o1]); };
+    const df2 z2 = {f2(0.f), f2(0.f)};
+    df2 Jt = z2, Fx = z2, Fy = z2, Fz = z2, Qt = z2;
+    for (int b = 0; b < P.nbands; ++b) {
+        const df32 *jf = JF + (long long)b * 4 * N;
+        const df2 Jb = ld2(jf, p[0], p[1]);
+        const df2 fx = ld2(jf + N, p[0], p[1]), fy = ld2(jf + 2 * N, p[0], p[1]), fz = ld2(jf + 3 * N, p[0], p[1]);
+        const df2 dvx = df2_mul(df2_sub(ld2(jf + N, xp[0], xp[1]), ld2(jf + N, xm[0], xm[1])), K.cx, K.ncx);
+        const df2 dvy = df2_mul(df2_sub(ld2(jf + 2 * N, yp[0], yp[1]), ld2(jf + 2 * N, ym[0], ym[1])), K.cy, K.ncy);
+        const df2 dvz = df2_mul(df2_sub(ld2(jf + 3 * N, p[0] + dzp, p[1] + dzp), ld2(jf + 3 * N, p[0] + dzm, p[1] + dzm)),
+                                K.cz, K.ncz);
+        const df2 D = df2_add(df2_add(dvx, dvy), dvz);  // div F_b; the Q step uses -D
+        const float *cb = chi + (long long)b * N, *sb = S + (long long)b * N;
+        const float2 c = f2(cb[p[0]], cb[p[1]]), sv = f2(sb[p[0]], sb[p[1]]);
+        const df2 dJ = df2_sub(Jb, sv);
+        const df2 qj = df2_mul(df2_mul(K.four_pi, K.nfour_pi, c), dJ, df2_neg(dJ));
+        // om = e^-x, omc = 1 - om = -expm1(-x), x = chi thin (blend_weights)
+        float2 om, m1;  // m1 = expm1(-x) = -omc
+        {
+            const float x0 = c.x * K.thin, x1 = c.y * K.thin;
+            om = f2(expf(-x0), expf(-x1));
+            m1 = f2(expm1f(-x0), expm1f(-x1));
+        }
+        // om qj + omc (-D), with omc (-D) = (-omc) D = m1 D
+        const df2 qb = df2_add(df2_mul(om, neg2(om), qj), df2_mul(m1, neg2(m1), D));
+        if (b == 0) {
+            Jt = Jb; Fx = fx; Fy = fy; Fz = fz; Qt = qb;  // 0 + v is v for a normalised v
+        } else {
+            Jt = df2_add(Jt, Jb);
+            Fx = df2_add(Fx, fx);
+            Fy = df2_add(Fy, fy);
+            Fz = df2_add(Fz, fz);
+            Qt = df2_add(Qt, qb);
+        }
+    }
+    const int p1 = p[1];
+    auto st = [&](double *o, df2 v) {
+        o[p[0]] = (double)v.hi.x + (double)v.lo.x;
+        if (two) o[p1] = (double)v.hi.y + (double)v.lo.y;
+    };
+    if (J) st(J, Jt);
+    if (F) {
+        st(F, Fx);
+        st(F + N, Fy);
+        st(F + 2 * N, Fz);
+    }
+    if (Q) st(Q, Qt);
+}
+
 }  // namespace rts

@@ -1308,8 +1308,8 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
             h->d_qfu, h->d_qfb, g.nx, g.ny, g.nz, B, (int)h->units.size(), h->qr_max_nat, h->qr_max_x, jf);
         CUDA_TRY(h, cudaGetLastError());
         if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
-        dim3 rb(32, 8), qg((g.nx + 31) / 32, (g.ny + 7) / 8, (unsigned)g.nz);
-        rts::qstep_kernel<float, rts::df32><<<qg, rb, 0, st>>>(jf, (const float *)chi, (const float *)S, P, J, F, Q);
+        dim3 rb(32, 8), qg((g.nx + 31) / 32, (g.ny + rts::QS_TJ - 1) / rts::QS_TJ, (unsigned)g.nz);
+        rts::qstep_df2_kernel<<<qg, rb, 0, st>>>(jf, (const float *)chi, (const float *)S, P, J, F, Q);
         CUDA_TRY(h, cudaGetLastError());
         kernels += 2;
     } else if (J || F || Q || reduce_only) {
