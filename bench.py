@@ -50,7 +50,16 @@ def _peaks():
         return {}
 
 
-def _config(prec, ws=1):
+def _config(prec, ws=1, sweep_kernel=2):
+    """The workload as the JSON line names it. sweep_kernel: 2 for the register
+    sweep (both FP32 modes then reduce and form Q_rad in double-float), 1 for
+    the shared sweep (FP32 mixed: FP64 for the cancelling parts)."""
+    if prec == "fp64":
+        q_step = "FP64"
+    elif sweep_kernel == 2 or prec == "fp32_compensated":
+        q_step = "double-float (2xFP32)"
+    else:
+        q_step = "FP64 for the cancelling parts"
     return {
         "grid": [NX, NY, NZ],
         "parallelism": ("single GPU" if ws == 1 else
@@ -60,7 +69,7 @@ def _config(prec, ws=1):
                     "S = T^4 x {0.4,0.3,0.2,0.1}), 24 rays (S4 Carlson), bottom I=S, top I=0",
         "precision": prec,
         "sweep": "FP32 sweep" if prec != "fp64" else "FP64 sweep",
-        "q_step": {"fp32": "FP64", "fp32_compensated": "double-float (2xFP32)", "fp64": "FP64"}[prec],
+        "q_step": q_step,
         "l2": "inputs (764 MB chi+S FP32) larger than the 126 MB L2; no flush between steps",
         "step": "one rts_solve over all 4 bands and 24 rays",
         "tile_rows": TILE_ROWS,
@@ -696,7 +705,7 @@ def run_ours(args):
     line = {"metric": METRIC, "value": round(value, 4), "unit": "Gupd/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec != "fp64" else "f64", "data": "synthetic",
-            "config": _config(prec, ws), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": _config(prec, ws, st["sweep_kernel"]), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk.summary(), "gpu_launches": st["kernels_per_solve"] * args.steps,
             "phases_ms": phases,
             "wrap": {"max_warmup_planes": st["max_warmup_steps"], "mean_warmup_planes": st["mean_warmup_steps"]},
