@@ -299,9 +299,12 @@ void rts_destroy(rts_handle *h);
  * and S of every band: reverse-mode differentiation of the discrete solve.
  * The paper has no adjoint; this is the transpose of its forward operator.
  * Per chunk of adjoint_chunk_bands bands (the checkpoint):
- *   1. the forward sweep of the chunk, keeping the converged intensity of
- *      every ray (4 values per point and sweep unit); its partial sums give
- *      the chunk's J_b, F_b;
+ *   1. the forward sweep of the chunk, keeping the derivative dI/d(dtau) of
+ *      every ray's converged segment (4 values per point and sweep unit);
+ *      the intensities it produces give the chunk's J_b, F_b (on FP32
+ *      handles that run the register sweep, the register sweep's own
+ *      checkpoint form with the double-float reduction and a double-float
+ *      Q-step transpose, in both FP32 modes);
  *   2. the Q step transposed for those bands (cotangents of J_b and F_b, and
  *      the direct chi and S terms of Q_rad), then the reverse sweep: the
  *      cotangent of I along each ray, lam_p = lam0_p + sum over the downwind

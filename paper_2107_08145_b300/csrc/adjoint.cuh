@@ -142,6 +142,84 @@ __global__ void __launch_bounds__(256) qstep_adjoint_kernel(const Acc *__restric
     }
 }
 
+// The same Q-step adjoint for double-float J_b, F_b (the register sweep's
+// reduction) in FP32 arithmetic: each cancelling difference is formed from
+// the two double-float values as (hi - hi) + (lo - lo) -- the high parts of
+// neighbouring values differ by less than a factor 2 where the difference is
+// small, so their difference is exact there -- and everything else in FP32.
+// The cotangent inputs (FP64) are converted once per point, outside the band
+// loop, so the kernel does no FP64 arithmetic per band.
+__device__ __forceinline__ float df_diff(df32 a, df32 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+template <int = 0>  // a template, so that every translation unit including this header may define it
+__global__ void __launch_bounds__(256) qstep_adjoint_df_kernel(const df32 *__restrict__ JF,
+                                                                const float *__restrict__ chi,
+                                                                const float *__restrict__ S,
+                                                                const double *__restrict__ gJ,
+                                                                const double *__restrict__ gF,
+                                                                const double *__restrict__ gQ,
+                                                                const float *__restrict__ u, QAdjParams P, int b0,
+                                                                int b1, float *__restrict__ lam0,
+                                                                float *__restrict__ direct)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= P.nx || j >= P.ny) return;
+    const long long nx = P.nx, ny = P.ny, nz = P.nz, N = nx * ny * nz, pl = nx * ny;
+    const long long p = (long long)k * pl + (long long)j * nx + i;
+    const int im = i == 0 ? P.nx - 1 : i - 1, ip = i + 1 == P.nx ? 0 : i + 1;
+    const int jm = j == 0 ? P.ny - 1 : j - 1, jp = j + 1 == P.ny ? 0 : j + 1;
+    const long long pxp = p - i + ip, pxm = p - i + im;
+    const long long pyp = p + (long long)(jp - j) * nx, pym = p + (long long)(jm - j) * nx;
+    const float four_pi = 12.566370614359172954f;
+    const float thin = (float)P.thin, i2x = (float)P.inv2dx, i2y = (float)P.inv2dy;
+    // z part of div F at level k: the two levels it differences and their coefficient
+    int zq1 = k + 1, zq0 = k - 1;
+    float zc = (float)P.inv2dz;
+    if (nz == 1) zc = 0.f, zq1 = zq0 = k;
+    else if (k == 0) zq1 = 1, zq0 = 0, zc = (float)P.invdz;
+    else if (k == nz - 1) zq1 = k, zq0 = k - 1, zc = (float)P.invdz;
+    const float gq = gQ ? (float)gQ[p] : 0.f;
+    const float gJp = gJ ? (float)gJ[p] : 0.f;
+    const float gFxp = gF ? (float)gF[p] : 0.f, gFyp = gF ? (float)gF[N + p] : 0.f;
+    const float gFzp = gF ? (float)gF[2 * N + p] : 0.f;
+    for (int b = b0; b < b1; ++b) {
+        const float *cb = chi + (long long)b * N;
+        const df32 *jf = JF + (long long)b * 4 * N;
+        const float *ub = gQ ? u + (long long)(b - b0) * N : nullptr;
+        auto u_at = [&](long long q) -> float { return ub ? ub[q] : 0.f; };  // gQ (1 - om_b) at point q
+        float om, omc;
+        blend_weights(cb[p], thin, om, omc);
+        const float fpc = four_pi * cb[p];
+        float gJb = gJp, gchi = 0.f, gs = 0.f;
+        if (gQ) {  // J_b and F_b of the forward solve are read only when Q_rad enters L
+            const long long col = (long long)j * nx + i;
+            const float divz = zc == 0.f ? 0.f : df_diff(jf[3 * N + zq1 * pl + col], jf[3 * N + zq0 * pl + col]) * zc;
+            const float qf = -(df_diff(jf[N + pxp], jf[N + pxm]) * i2x + df_diff(jf[2 * N + pyp], jf[2 * N + pym]) * i2y +
+                               divz);
+            const df32 Jb = jf[p];
+            const float dJ = (Jb.hi - S[(long long)b * N + p]) + Jb.lo;  // J_b - S_b
+            const float qj = fpc * dJ;
+            gJb += gq * (om * fpc);
+            gchi = gq * (om * four_pi * dJ - thin * om * (qj - qf));
+            gs = -gq * om * fpc;
+        }
+        const float gFx = gFxp + (u_at(pxp) - u_at(pxm)) * i2x;
+        const float gFy = gFyp + (u_at(pyp) - u_at(pym)) * i2y;
+        float dTz = 0.f;  // (D_z^T u)(k) = sum_q u(q) coef_z(q, k)
+        for (int q = k - 1; q <= k + 1; ++q) {
+            if (q < 0 || q >= P.nz) continue;
+            const float cf = (float)coef_z(q, k, P);
+            if (cf != 0.f) dTz += u_at((long long)q * pl + (long long)j * nx + i) * cf;
+        }
+        st4(lam0 + ((long long)b * N + p) * 4, gJb, gFx, gFy, gFzp - dTz);
+        float *dr = direct + (long long)b * 2 * N;
+        dr[p] = gchi;
+        dr[N + p] = gs;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // 3. Reverse sweep of one tile (cotangent lam of the rays of one unit)
 // ---------------------------------------------------------------------------

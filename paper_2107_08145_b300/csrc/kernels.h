@@ -15,7 +15,8 @@ using SweepFn = void (*)(SweepArgs<T>);
 SweepFn<float> fwd_kernel_f32(int tq, int maxr, bool ckpt);
 SweepFn<double> fwd_kernel_f64(int tq, int maxr, bool ckpt);
 // register-resident FP32 forward sweep (sweep_reg.cuh)
-SweepFn<float> reg_kernel_f32(int tq, int maxr, bool seeded = false);  // seeded: the warm-start instantiation
+// seeded: the warm-start instantiation; checkpoint: the adjoint's checkpoint sweep (stores D)
+SweepFn<float> reg_kernel_f32(int tq, int maxr, bool seeded = false, bool checkpoint = false);
 // reverse (adjoint) sweep
 SweepFn<float> adj_kernel_f32(int tq, int maxr);
 SweepFn<double> adj_kernel_f64(int tq, int maxr);

@@ -20,6 +20,7 @@
 #include <mutex>
 #include <new>
 #include <numeric>
+#include <type_traits>
 #include <vector>
 
 #include "rts.h"
@@ -321,6 +322,8 @@ struct rts_handle {
     bool qf_ok = false;  // the register sweep's reduction (qfused.cuh) is used
     int reg_grid_seed = 0;       // grid and carveout of the warm-start instantiation (0: none fits)
     unsigned reg_carveout_seed = 100;
+    int reg_grid_ck = 0;         // grid and carveout of the adjoint's checkpoint instantiation (0: none fits)
+    unsigned reg_carveout_ck = 100;
     size_t qr_smem = 0;
     int qr_grid = 0, qr_max_nat = 0, qr_max_x = 0;
     rts::RedUnit *d_qfu = nullptr;  // its units: per band the x groups first
@@ -673,6 +676,37 @@ static cudaError_t launch_reg_sweep(rts_handle *h, rts::SweepArgs<float> a)
     return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
+// the register sweep's checkpoint instantiation over units u0 .. u1-1 (one
+// chunk of bands of rts_adjoint): raw slot intensities and D = dI/d(dtau)
+static cudaError_t launch_reg_ckpt(rts_handle *h, rts::SweepArgs<float> a, int u0, int u1)
+{
+    rts::SweepFn<float> kern = rts::reg_kernel_f32(h->reg_tq, h->reg_maxr, false, true);
+    if (!kern || h->reg_grid_ck < 1) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->reg_smem);
+    if (e != cudaSuccess) return e;
+    const rts::SweepUnit &U0 = h->reg_units[u0], &U1 = h->reg_units[u1 - 1];
+    a.units = h->d_reg_units;
+    a.unit_of_tile = h->d_reg_uot;
+    a.unit_base = u0;
+    a.tile_base = U0.tile0;
+    a.total_tiles = U1.tile0 + U1.ntiles - U0.tile0;
+    a.seed = nullptr;
+    a.seed_in = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(std::min(h->reg_grid_ck, a.total_tiles));
+    cfg.blockDim = dim3(h->reg_nt);
+    cfg.dynamicSmemBytes = h->reg_smem;
+    cfg.stream = h->stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs co-resident
+    attr[0].val.cooperative = 1;
+    attr[1].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+    attr[1].val.sharedMemCarveout = h->reg_carveout_ck;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 // Batched forward sweep: one cooperative launch per CTA-width class (a single
 // class is the plain launch). Each class's CTA has as many threads as its
 // widest plane needs, so narrow subdomains leave no idle warps; the ticket is
@@ -953,6 +987,16 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
                     (long long)bs * nsm >= pr.max_ntiles) {
                     h->reg_grid_seed = std::min(pr.ntiles, bs * nsm);
                     h->reg_carveout_seed = carveout_percent(bs, tr.smem, (const void *)ks);
+                }
+                cudaGetLastError();
+            }
+            if (want_adj) {  // the adjoint's checkpoint instantiation: its own residency
+                rts::SweepFn<float> kc = rts::reg_kernel_f32(tr.tq, tr.maxt, false, true);
+                int bc = 0;
+                if (kc && kernel_occupancy<float>(kc, tr.nt, tr.smem, &bc) == cudaSuccess && bc > 0 &&
+                    (long long)bc * nsm >= pr.max_ntiles) {
+                    h->reg_grid_ck = std::min(pr.ntiles, bc * nsm);
+                    h->reg_carveout_ck = carveout_percent(bc, tr.smem, (const void *)kc);
                 }
                 cudaGetLastError();
             }
@@ -1422,14 +1466,35 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
         rts_status rs = reset_sweep_state(h, st);
         if (rs) return rs;
         a.store = (T *)h->d_ckpt;
-        cudaError_t e = launch_sweep<T>(h, a);
+        // FP32 on a register-sweep handle: the register sweep's checkpoint
+        // instantiation (raw slot intensities and D), then the forward solve's
+        // double-float reduction and a double-float Q-step adjoint, in both
+        // FP32 modes (as the forward solve's register path)
+        bool regck = false;
+        if constexpr (std::is_same<T, float>::value) regck = h->use_reg && !h->batched && h->reg_grid_ck > 0;
+        cudaError_t e;
+        if constexpr (std::is_same<T, float>::value) {
+            if (regck) e = launch_reg_ckpt(h, a, u0, u1);
+            else e = launch_sweep<T>(h, a);
+        } else {
+            e = launch_sweep<T>(h, a);
+        }
         if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
         kernels += 1;
         if (gQ) {
             const dim3 rg((g.nx + 31) / 32, (g.ny + 31) / 32, (unsigned)(g.nz * nbc));
-            rts::reduce_units_kernel<T, Acc><<<rg, tb, 0, st>>>(h->d_ru, h->d_ru_begin + b0,
-                                                               (Acc *)h->d_JF + (long long)b0 * 4 * N, g.nx, g.ny,
-                                                               g.nz, 0);
+            if (regck && b0 == 0 && b1 == B && h->qf_ok) {
+                rts::qf_reduce_kernel<<<h->qr_grid, dim3(rts::QR_TI, rts::QR_RY), h->qr_smem, st>>>(
+                    h->d_qfu, h->d_qfb, g.nx, g.ny, g.nz, B, (int)h->units.size(), h->qr_max_nat, h->qr_max_x,
+                    (rts::df32 *)h->d_JF);
+            } else if (regck) {  // raw slot intensities of the chunk's units
+                rts::reduce_units_kernel<float, rts::df32><<<rg, tb, 0, st>>>(
+                    h->d_ru, h->d_ru_begin + b0, (rts::df32 *)h->d_JF + (long long)b0 * 4 * N, g.nx, g.ny, g.nz, 1);
+            } else {
+                rts::reduce_units_kernel<T, Acc><<<rg, tb, 0, st>>>(h->d_ru, h->d_ru_begin + b0,
+                                                                   (Acc *)h->d_JF + (long long)b0 * 4 * N, g.nx,
+                                                                   g.ny, g.nz, 0);
+            }
             CUDA_TRY(h, cudaGetLastError());
             kernels += 1;
         }
@@ -1447,9 +1512,20 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
                 CUDA_TRY(h, cudaGetLastError());
                 kernels += 1;
             }
-            rts::qstep_adjoint_kernel<T, Acc><<<qg, tb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi, (const T *)S,
-                                                                gJ, gF, gQ, u, QP, b0, b1, (T *)h->d_lam0,
-                                                                (T *)h->d_direct);
+            if constexpr (std::is_same<T, float>::value) {
+                if (regck)
+                    rts::qstep_adjoint_df_kernel<><<<qg, tb, 0, st>>>(
+                        (const rts::df32 *)h->d_JF, (const float *)chi, (const float *)S, gJ, gF, gQ, u, QP, b0, b1,
+                        (float *)h->d_lam0, (float *)h->d_direct);
+                else
+                    rts::qstep_adjoint_kernel<T, Acc><<<qg, tb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi,
+                                                                        (const T *)S, gJ, gF, gQ, u, QP, b0, b1,
+                                                                        (T *)h->d_lam0, (T *)h->d_direct);
+            } else {
+                rts::qstep_adjoint_kernel<T, Acc><<<qg, tb, 0, st>>>((const Acc *)h->d_JF, (const T *)chi,
+                                                                    (const T *)S, gJ, gF, gQ, u, QP, b0, b1,
+                                                                    (T *)h->d_lam0, (T *)h->d_direct);
+            }
             CUDA_TRY(h, cudaGetLastError());
             kernels += 1;
             if (h->has_x) {

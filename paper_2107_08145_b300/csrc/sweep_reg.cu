@@ -5,10 +5,12 @@
 
 namespace rts {
 
-SweepFn<float> reg_kernel_f32(int tq, int maxr, bool seeded)
+SweepFn<float> reg_kernel_f32(int tq, int maxr, bool seeded, bool checkpoint)
 {
 #define RTS_CFG(A, B)                                                                                              \
-    if (tq == A && maxr == B) return seeded ? sweep_reg_kernel<A, B, true> : sweep_reg_kernel<A, B, false>;
+    if (tq == A && maxr == B)                                                                                      \
+        return checkpoint ? sweep_reg_kernel<A, B, false, true>                                                   \
+                          : (seeded ? sweep_reg_kernel<A, B, true> : sweep_reg_kernel<A, B, false>);
     RTS_CFG(8, 255) RTS_CFG(4, 168) RTS_CFG(4, 128)
 #undef RTS_CFG
     return nullptr;

@@ -78,27 +78,57 @@ struct RegStencil {
     float2 hdn;             // -(ds/2) log2(e): y = hdn (chi_up + chi_p) = -dtau log2(e)
 };
 
+// dw_p/dx = (q - e)/x below x = 1/4: the degree-4 polynomial interpolating
+// it at the Chebyshev nodes of [0, 1/4] (the same literals as seg_dwp),
+// evaluated in y = -x log2(e) and negated, as the checkpoint uses it
+constexpr double kDwpX[5] = {0.49999999793, -0.33333291823, 0.12498666530, -0.03318270431, 0.00624265650};
+constexpr float kNDwpY[5] = {(float)-kDwpX[0], (float)(-kDwpX[1] * -kLn2), (float)(-kDwpX[2] * kLn2 * kLn2),
+                             (float)(-kDwpX[3] * -kLn2 * kLn2 * kLn2),
+                             (float)(-kDwpX[4] * kLn2 * kLn2 * kLn2 * kLn2)};
+
 // One segment for two columns: the upwind intensity, opacity and source
 // interpolated with the shared weights, dtau, e = exp(-dtau) and
 // q = (1 - e)/dtau, and the new intensity
 //   I = S_p + e (I_up - S_up) + q (S_up - S_p)
 // (the linear-in-tau formal solution, same form as seg_eq). Returns I; e
-// goes to the seed-error bound.
+// goes to the seed-error bound. WD (the adjoint's checkpoint): also the
+// segment's derivative D = dI/d(dtau) = e (S_up - I_up) + dw_p (S_p - S_up),
+// with dw_p = (q - e)/dtau the derivative of the own-point weight 1 - q.
+template <bool WD = false>
 __device__ __forceinline__ float2 seg2(const RegStencil &K, float2 i0, float2 i1, float2 i2, float2 i3, float2 x0,
                                        float2 x1, float2 x2, float2 x3, float2 s0, float2 s1, float2 s2, float2 s3,
-                                       float2 xp, float2 sp, float2 &e)
+                                       float2 xp, float2 sp, float2 &e, float2 *D = nullptr)
 {
     const float2 iup = fma2(K.b3, i3, fma2(K.b2, i2, fma2(K.b1, i1, mul2(K.b0, i0))));
     const float2 xup = fma2(K.b3, x3, fma2(K.b2, x2, fma2(K.b1, x1, mul2(K.b0, x0))));
     const float2 sup = fma2(K.b3, s3, fma2(K.b2, s2, fma2(K.b1, s1, mul2(K.b0, s0))));
     const float2 y = mul2(K.hdn, add2(xup, xp));
     e = f2(ex2_approx(y.x), ex2_approx(y.y));
-    // (1 - e)/x = (e - 1) log2(e) / y
-    const float2 qd = mul2(fma2(f2((float)kLog2e), e, f2(-(float)kLog2e)), f2(rcp_approx(y.x), rcp_approx(y.y)));
-    const float2 qs = fma2(fma2(fma2(fma2(f2(kQPolyY[4]), y, f2(kQPolyY[3])), y, f2(kQPolyY[2])), y, f2(kQPolyY[1])),
-                           y, f2(kQPolyY[0]));
-    const float2 q = f2(y.x > kYSwitch ? qs.x : qd.x, y.y > kYSwitch ? qs.y : qd.y);
-    return fma2(q, sub2(sup, sp), fma2(e, sub2(iup, sup), sp));
+    if constexpr (!WD) {
+        // (1 - e)/x = (e - 1) log2(e) / y
+        const float2 qd = mul2(fma2(f2((float)kLog2e), e, f2(-(float)kLog2e)), f2(rcp_approx(y.x), rcp_approx(y.y)));
+        const float2 qs = fma2(fma2(fma2(fma2(f2(kQPolyY[4]), y, f2(kQPolyY[3])), y, f2(kQPolyY[2])), y,
+                                    f2(kQPolyY[1])),
+                               y, f2(kQPolyY[0]));
+        const float2 q = f2(y.x > kYSwitch ? qs.x : qd.x, y.y > kYSwitch ? qs.y : qd.y);
+        return fma2(q, sub2(sup, sp), fma2(e, sub2(iup, sup), sp));
+    } else {
+        const float2 ry = f2(rcp_approx(y.x), rcp_approx(y.y));
+        const float2 qd = mul2(fma2(f2((float)kLog2e), e, f2(-(float)kLog2e)), ry);
+        const float2 qs = fma2(fma2(fma2(fma2(f2(kQPolyY[4]), y, f2(kQPolyY[3])), y, f2(kQPolyY[2])), y,
+                                    f2(kQPolyY[1])),
+                               y, f2(kQPolyY[0]));
+        const bool smx = y.x > kYSwitch, smy = y.y > kYSwitch;
+        const float2 q = f2(smx ? qs.x : qd.x, smy ? qs.y : qd.y);
+        const float2 bv = sub2(sup, sp);
+        // dw_p: (q - e)/x = (e - q) log2(e) / y above x = 1/4, else the polynomial
+        const float2 dd = mul2(mul2(sub2(e, q), f2((float)kLog2e)), ry);
+        const float2 ds = fma2(
+            fma2(fma2(fma2(f2(kNDwpY[4]), y, f2(kNDwpY[3])), y, f2(kNDwpY[2])), y, f2(kNDwpY[1])), y, f2(kNDwpY[0]));
+        const float2 ndwp = f2(smx ? ds.x : -dd.x, smy ? ds.y : -dd.y);
+        *D = fma2(ndwp, bv, mul2(e, sub2(sup, iup)));
+        return fma2(q, bv, fma2(e, sub2(iup, sup), sp));
+    }
 }
 
 // bound of the remaining seed error: g = e * sum_c beta_c g(corner c)
@@ -126,8 +156,12 @@ __device__ __forceinline__ float reg_bc(int kind, const float *arr, int udx, int
 }
 
 // SEED: the instantiation for warm-started solves (rts_boundary.wrap_seed
-// with seed_in); the plain one carries none of that code.
-template <int TQ, bool SEED>
+// with seed_in); the plain one carries none of that code. CK: the adjoint's
+// checkpoint sweep, which also stores every accumulated segment's
+// D = dI/d(dtau) (0 at set points and in empty slots) at
+// a.store + (unit - a.unit_base) * 4 N + 4 off + slot, off the point's offset
+// in the unit's layout (the layout the reverse sweep reads).
+template <int TQ, bool SEED, bool CK>
 __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restrict__ Ug, int uidx, int r, int gt,
                              unsigned char *smem)
 {
@@ -143,6 +177,8 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     const float *__restrict__ Sg = (Ug->transposed ? a.ST : a.S) + Ug->in_off;
     float *const itop = a.itop ? a.itop + Ug->top_off : nullptr;
     float *const part = (float *)Ug->partial;
+    // the adjoint's checkpoint of this unit (CK only)
+    float *const ckb = CK ? a.store + (long long)(uidx - a.unit_base) * MAXD * Ug->N : nullptr;
     // thread c owns columns c (.x of every pair) and c + H (.y)
     const int H = NP >> 1;
     const int RR = H + 2;                        // records per shared row: record c + 1 holds pair c
@@ -320,6 +356,16 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             }
         }
     };
+    // checkpoint: D of slots 2h, 2h+1 of own row k of plane m ({D(2h),
+    // D(2h+1)} of column c in lo, of column c + H in hi)
+    auto store_ck = [&](int m, int k, int h, float2 lo, float2 hi) {
+        if constexpr (CK) {
+            if (!act || k > nrows) return;
+            float4 *pp = reinterpret_cast<float4 *>(ckb) + (m * sMi + (q0 + k - 1) * sQi + c);
+            reinterpret_cast<float2 *>(pp)[h] = lo;
+            reinterpret_cast<float2 *>(pp + H)[h] = hi;
+        }
+    };
     // raw slot intensities and I_top of the own rows of an accumulated plane m
     // (held in Ip)
     auto store_rows = [&](int m) {
@@ -409,7 +455,16 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
         }
         publish_ring(tp, Ip[1][2], Ip[1][3], Gp[1][1], Ip[TQ][0], Ip[TQ][1], Gp[TQ][0]);
         publish_edges(tp);
-        if (!wrap) store_rows(m);  // z groups: the boundary plane is the first accumulated plane
+        if (!wrap) {  // z groups: the boundary plane is the first accumulated plane
+            store_rows(m);
+            if constexpr (CK) {  // set points: D = 0
+#pragma unroll
+                for (int k = 1; k <= TQ; ++k) {
+                    store_ck(m, k, 0, f2(0.f), f2(0.f));
+                    store_ck(m, k, 1, f2(0.f), f2(0.f));
+                }
+            }
+        }
     }
     __syncthreads();
     release_plane();
@@ -513,12 +568,19 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
             const float4 cc = XC[k * RR];
             const float2 xp = f2(cc.x, cc.y), sp = f2(cc.z, cc.w);
             float2 e0, e1;
+            constexpr bool WD = CK && ACC;
+            [[maybe_unused]] float2 d0, d1;
             // sP = +1 slot: corners (k, c), (k, c-1), (k2, c), (k2, c-1)
-            const float2 v0 = seg2(K, Ip[k][2 * h], NA.il, Ip[k2][2 * h], NB.il, A.x0, A.xl, B.x0, B.xl, A.s0, A.sl,
-                                   B.s0, B.sl, xp, sp, e0);
+            const float2 v0 = seg2<WD>(K, Ip[k][2 * h], NA.il, Ip[k2][2 * h], NB.il, A.x0, A.xl, B.x0, B.xl, A.s0,
+                                       A.sl, B.s0, B.sl, xp, sp, e0, &d0);
             // sP = -1 slot: corners (k, c), (k, c+1), (k2, c), (k2, c+1)
-            const float2 v1 = seg2(K, Ip[k][2 * h + 1], NA.ir, Ip[k2][2 * h + 1], NB.ir, A.x0, A.xr, B.x0, B.xr, A.s0,
-                                   A.sr, B.s0, B.sr, xp, sp, e1);
+            const float2 v1 = seg2<WD>(K, Ip[k][2 * h + 1], NA.ir, Ip[k2][2 * h + 1], NB.ir, A.x0, A.xr, B.x0, B.xr,
+                                       A.s0, A.sr, B.s0, B.sr, xp, sp, e1, &d1);
+            if constexpr (WD) {
+                // empty slots carry D = 0; a set row overwrites its slots' D later
+                const bool a0 = (actm >> (2 * h)) & 1, a1 = (actm >> (2 * h + 1)) & 1;
+                store_ck(m, k, h, f2(a0 ? d0.x : 0.f, a1 ? d1.x : 0.f), f2(a0 ? d0.y : 0.f, a1 ? d1.y : 0.f));
+            }
             if constexpr (BND) {
                 const float2 g0 = bound2(K, Gp[k][h], NA.gl, Gp[k2][h], NB.gl, e0);
                 const float2 g1 = bound2(K, Gp[k][h], NA.gr, Gp[k2][h], NB.gr, e1);
@@ -549,6 +611,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
                 Ip[k][d] = f2(v[0], v[1]);
             }
             if constexpr (BND) Gp[k][h] = f2(0.f);
+            if constexpr (CK && ACC) store_ck(m, k, h, f2(0.f), f2(0.f));
         };
 
         // ---- rising row TQ and descending row 1 (own rows only), published at once ----
@@ -859,7 +922,7 @@ __device__ void run_tile_reg(const SweepArgs<float> &a, const SweepUnit *__restr
     cp_async_wait_all();
 }
 
-template <int TQ, int MAXR, bool SEED>
+template <int TQ, int MAXR, bool SEED, bool CK = false>
 __global__ void __maxnreg__(MAXR) sweep_reg_kernel(SweepArgs<float> a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -875,7 +938,7 @@ __global__ void __maxnreg__(MAXR) sweep_reg_kernel(SweepArgs<float> a)
         if (s_tile < 0 || s_tile >= a.total_tiles) return;
         const int tile = a.tile_base + s_tile;
         const int u = a.unit_of_tile[tile];
-        run_tile_reg<TQ, SEED>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
+        run_tile_reg<TQ, SEED, CK>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
     }
 }
 

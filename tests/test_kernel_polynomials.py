@@ -112,3 +112,30 @@ def test_switch_point_continuity():
         f = {"q": _exact_q, "wu/x": _exact_wu_over_x, "wp/x": _exact_wp_over_x}[name]
         ref = f(np.array([x]))[0]
         assert abs(_horner(c, np.array([x]), np.float64)[0] - ref) / abs(ref) < 5e-9
+
+
+REG_SRC = os.path.join(os.path.dirname(SRC), "sweep_reg.cuh")
+
+
+def _reg_array(name):
+    """A `constexpr double name[5] = {...};` literal array of the register sweep."""
+    src = open(REG_SRC).read()
+    m = re.search(r"constexpr double " + name + r"\[5\] = \{([^}]*)\}", src)
+    assert m, name
+    return tuple(float(v) for v in m.group(1).split(","))
+
+
+def test_register_sweep_literals():
+    """The register sweep's q polynomial (kQPolyX) and its checkpoint's
+    dw_p/dx = w_up/x polynomial (kDwpX) interpolate their functions, and the
+    latter evaluated in y = -x log2(e) with the float32 coefficients the kernel
+    forms stays within a few float32 ulps."""
+    x = np.linspace(1e-7, 0.25, 20001)
+    cq, cd = _reg_array("kQPolyX"), _reg_array("kDwpX")
+    assert np.max(np.abs(_horner(cq, x, np.float64) - _exact_q(x)) / _exact_q(x)) < 5e-9
+    ref = _exact_wu_over_x(x)
+    assert np.max(np.abs(_horner(cd, x, np.float64) - ref) / ref) < 5e-9
+    ln2 = np.log(2.0)
+    ky = [-cd[i] * (-ln2) ** i for i in range(5)]  # negated, in y
+    y = (-x / ln2).astype(np.float32)
+    assert np.max(np.abs(-_horner(ky, y, np.float32) - ref) / ref) < 2.5e-7
