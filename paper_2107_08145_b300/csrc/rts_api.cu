@@ -294,6 +294,7 @@ struct rts_handle {
     std::vector<int> reg_unit_of_tile;
     rts::SweepUnit *d_reg_units = nullptr;
     int *d_reg_uot = nullptr;
+    int *d_reg_order = nullptr;  // tickets -> tiles of the single-grid register sweep (null: identity)
     int reg_tq = 0, reg_maxr = 0, reg_total_tiles = 0, reg_grid = 0, reg_nt = 32;
     size_t reg_smem = 0;
     unsigned reg_carveout = 100;
@@ -659,6 +660,7 @@ static cudaError_t launch_reg_sweep(rts_handle *h, rts::SweepArgs<float> a)
     if (e != cudaSuccess) return e;
     a.units = h->d_reg_units;
     a.unit_of_tile = h->d_reg_uot;
+    a.tile_order = h->d_reg_order;
     a.tile_base = 0;
     a.total_tiles = h->reg_total_tiles;
     cudaLaunchConfig_t cfg = {};
@@ -1046,7 +1048,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     const size_t o_dirw = scatter ? take(sizeof(double) * 2 * h->ndir) : 0;
     const size_t o_dsmax = scatter ? take(sizeof(unsigned) * 4) : 0;
     const size_t o_regu = h->use_reg ? take(sizeof(rts::SweepUnit) * h->reg_units.size()) : 0;
-    const size_t o_reguot = h->use_reg ? take(sizeof(int) * h->reg_unit_of_tile.size()) : 0;
+    // the register tiles' unit table and ticket order
+    const size_t o_reguot = h->use_reg ? take(2 * sizeof(int) * h->reg_unit_of_tile.size()) : 0;
     size_t o_adj[9] = {0};
     if (adjoint) {
         o_adj[7] = take(sizeof(rts::SweepUnit) * h->adj_units.size());
@@ -1118,6 +1121,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     if (h->use_reg) {
         h->d_reg_units = (rts::SweepUnit *)(base + o_regu);
         h->d_reg_uot = (int *)(base + o_reguot);
+        h->d_reg_order = h->d_reg_uot + h->reg_unit_of_tile.size();
     }
     if (adjoint) {
         h->d_adj_units = (rts::SweepUnit *)(base + o_adj[7]);
@@ -1209,6 +1213,15 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
                                cudaMemcpyHostToDevice));
         CUDA_TRY(h, cudaMemcpy(h->d_reg_uot, h->reg_unit_of_tile.data(), sizeof(int) * h->reg_unit_of_tile.size(),
                                cudaMemcpyHostToDevice));
+        // tickets: the x/y groups' tiles first (their periodic warm-up makes
+        // them the long ones), then the z groups', each unit's tiles together
+        std::vector<int> order;
+        order.reserve(h->reg_unit_of_tile.size());
+        for (int pass = 0; pass < 2; ++pass)
+            for (const rts::SweepUnit &U : h->reg_units)
+                if ((U.wrap != 0) == (pass == 0))
+                    for (int t = 0; t < U.ntiles; ++t) order.push_back(U.tile0 + t);
+        CUDA_TRY(h, cudaMemcpy(h->d_reg_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
     }
     if (adjoint) {
         for (size_t u = 0; u < h->adj_units.size(); ++u) h->adj_units[u].partial = h->units[u].partial;

@@ -87,6 +87,9 @@ template <typename T>
 struct SweepArgs {
     const SweepUnit *units;
     const int *unit_of_tile;
+    // register sweep: the tile that ticket k takes, tile_order[k] (every
+    // unit's tiles consecutive); null: tile k
+    const int *tile_order;
     int total_tiles;            // tiles of this launch: tile_base .. tile_base+total_tiles-1
     int tile_base, unit_base;   // first tile and first unit of this launch
     // optional (forward: checkpoint for the adjoint): per accumulated point
