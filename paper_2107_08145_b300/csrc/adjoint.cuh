@@ -657,7 +657,7 @@ __global__ void __maxnreg__(MAXR) sweep_adj_kernel(SweepArgs<T> a)
         }
         __syncthreads();
         if (s_tile < 0 || s_tile >= a.total_tiles) return;
-        const int tile = a.tile_base + s_tile;
+        const int tile = a.tile_base + (a.tile_order ? a.tile_order[s_tile] : s_tile);
         const int u = a.unit_of_tile[tile];
         run_tile_adj<T, TQ>(a, a.units + u, u, tile - a.units[u].tile0, tile, smem);
     }

@@ -286,6 +286,7 @@ struct rts_handle {
     std::vector<int> adj_unit_of_tile;
     rts::SweepUnit *d_adj_units = nullptr;
     int *d_adj_uot = nullptr;
+    int *d_adj_order = nullptr;  // tickets -> tiles of the reverse sweep over all units
     int adj_tq = 0, adj_maxr = 0, adj_total_tiles = 0, adj_max_ntiles = 0;
     // register-resident FP32 forward sweep (sweep_reg.cuh): its own tiling of the same units
     bool use_reg = false;
@@ -689,6 +690,7 @@ static cudaError_t launch_reg_ckpt(rts_handle *h, rts::SweepArgs<float> a, int u
     const rts::SweepUnit &U0 = h->reg_units[u0], &U1 = h->reg_units[u1 - 1];
     a.units = h->d_reg_units;
     a.unit_of_tile = h->d_reg_uot;
+    a.tile_order = (u0 == 0 && u1 == (int)h->reg_units.size()) ? h->d_reg_order : nullptr;
     a.unit_base = u0;
     a.tile_base = U0.tile0;
     a.total_tiles = U1.tile0 + U1.ntiles - U0.tile0;
@@ -1053,7 +1055,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     size_t o_adj[9] = {0};
     if (adjoint) {
         o_adj[7] = take(sizeof(rts::SweepUnit) * h->adj_units.size());
-        o_adj[8] = take(sizeof(int) * h->adj_unit_of_tile.size());
+        o_adj[8] = take(2 * sizeof(int) * h->adj_unit_of_tile.size());  // unit table and ticket order
         const size_t cu = (size_t)h->chunk_units;
         o_adj[0] = take((size_t)nbands * 4 * h->N * es);
         o_adj[1] = h->has_x ? take((size_t)nbands * 4 * h->N * es) : 0;
@@ -1126,6 +1128,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
     if (adjoint) {
         h->d_adj_units = (rts::SweepUnit *)(base + o_adj[7]);
         h->d_adj_uot = (int *)(base + o_adj[8]);
+        h->d_adj_order = h->d_adj_uot + h->adj_unit_of_tile.size();
         h->d_lam0 = base + o_adj[0];
         h->d_lam0T = h->has_x ? base + o_adj[1] : nullptr;
         h->d_direct = base + o_adj[2];
@@ -1229,6 +1232,14 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
                                cudaMemcpyHostToDevice));
         CUDA_TRY(h, cudaMemcpy(h->d_adj_uot, h->adj_unit_of_tile.data(), sizeof(int) * h->adj_unit_of_tile.size(),
                                cudaMemcpyHostToDevice));
+        // as the forward's: the x/y groups' tiles first (used when a chunk covers every unit)
+        std::vector<int> order;
+        order.reserve(h->adj_unit_of_tile.size());
+        for (int pass = 0; pass < 2; ++pass)
+            for (const rts::SweepUnit &U : h->adj_units)
+                if ((U.wrap != 0) == (pass == 0))
+                    for (int t = 0; t < U.ntiles; ++t) order.push_back(U.tile0 + t);
+        CUDA_TRY(h, cudaMemcpy(h->d_adj_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
     }
     // a status word and warm-up record that read as "nothing ran yet"
     CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(int) * 4));
@@ -1558,6 +1569,7 @@ static rts_status adjoint_impl(rts_handle *h, const void *chi, const void *S, co
         const rts::SweepUnit &A0 = h->adj_units[u0], &A1 = h->adj_units[u1 - 1];
         a.units = h->d_adj_units;
         a.unit_of_tile = h->d_adj_uot;
+        a.tile_order = (u0 == 0 && u1 == (int)h->units.size()) ? h->d_adj_order : nullptr;
         a.tile_base = A0.tile0;
         a.total_tiles = A1.tile0 + A1.ntiles - A0.tile0;
         a.store = (T *)h->d_grad;
