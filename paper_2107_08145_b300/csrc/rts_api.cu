@@ -587,6 +587,22 @@ static bool reg_eligible(const std::vector<rts::SweepUnit> &units)
     return true;
 }
 
+// Ticket order of a persistent sweep launch: units by decreasing planes
+// per tile (a periodic x/y unit counted twice for its warm-up), each unit's
+// tiles together -- the long tiles start first and the short ones fill the
+// end of the launch.
+static std::vector<int> ticket_order(const std::vector<rts::SweepUnit> &units)
+{
+    std::vector<int> idx(units.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    auto key = [&](int u) { return (long long)units[u].NM * (units[u].wrap ? 2 : 1); };
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return key(a) > key(b); });
+    std::vector<int> order;
+    for (int u : idx)
+        for (int t = 0; t < units[u].ntiles; ++t) order.push_back(units[u].tile0 + t);
+    return order;
+}
+
 struct RegCfg {
     int tq, maxr;
 };
@@ -1216,14 +1232,7 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
                                cudaMemcpyHostToDevice));
         CUDA_TRY(h, cudaMemcpy(h->d_reg_uot, h->reg_unit_of_tile.data(), sizeof(int) * h->reg_unit_of_tile.size(),
                                cudaMemcpyHostToDevice));
-        // tickets: the x/y groups' tiles first (their periodic warm-up makes
-        // them the long ones), then the z groups', each unit's tiles together
-        std::vector<int> order;
-        order.reserve(h->reg_unit_of_tile.size());
-        for (int pass = 0; pass < 2; ++pass)
-            for (const rts::SweepUnit &U : h->reg_units)
-                if ((U.wrap != 0) == (pass == 0))
-                    for (int t = 0; t < U.ntiles; ++t) order.push_back(U.tile0 + t);
+        const std::vector<int> order = ticket_order(h->reg_units);
         CUDA_TRY(h, cudaMemcpy(h->d_reg_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
     }
     if (adjoint) {
@@ -1232,13 +1241,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
                                cudaMemcpyHostToDevice));
         CUDA_TRY(h, cudaMemcpy(h->d_adj_uot, h->adj_unit_of_tile.data(), sizeof(int) * h->adj_unit_of_tile.size(),
                                cudaMemcpyHostToDevice));
-        // as the forward's: the x/y groups' tiles first (used when a chunk covers every unit)
-        std::vector<int> order;
-        order.reserve(h->adj_unit_of_tile.size());
-        for (int pass = 0; pass < 2; ++pass)
-            for (const rts::SweepUnit &U : h->adj_units)
-                if ((U.wrap != 0) == (pass == 0))
-                    for (int t = 0; t < U.ntiles; ++t) order.push_back(U.tile0 + t);
+        // as the forward's (used when a chunk covers every unit)
+        const std::vector<int> order = ticket_order(h->adj_units);
         CUDA_TRY(h, cudaMemcpy(h->d_adj_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
     }
     // a status word and warm-up record that read as "nothing ran yet"
@@ -2444,7 +2448,7 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     const size_t o_units = take(sizeof(rts::SweepUnit) * nunits);
     const size_t o_uot = take(sizeof(int) * h->unit_of_tile.size());
     const size_t o_regu = h->use_reg ? take(sizeof(rts::SweepUnit) * nunits) : 0;
-    const size_t o_reguot = h->use_reg ? take(sizeof(int) * h->reg_unit_of_tile.size()) : 0;
+    const size_t o_reguot = h->use_reg ? take(2 * sizeof(int) * h->reg_unit_of_tile.size()) : 0;  // and the ticket order
     const size_t o_part = take((size_t)part_elems * es);
     const size_t o_chiT = h->has_x ? take((size_t)h->in_total * es) : 0;
     const size_t o_ST = h->has_x ? take((size_t)h->in_total * es) : 0;
@@ -2495,11 +2499,14 @@ extern "C" rts_status rts_create_batched(rts_handle **out, int nsub, const rts_g
     if (h->use_reg) {
         h->d_reg_units = (rts::SweepUnit *)(base + o_regu);
         h->d_reg_uot = (int *)(base + o_reguot);
+        h->d_reg_order = h->d_reg_uot + h->reg_unit_of_tile.size();
         for (int k = 0; k < nunits; ++k) h->reg_units[k].partial = h->units[k].partial;
         CUDA_TRY(h, cudaMemcpy(h->d_reg_units, h->reg_units.data(), sizeof(rts::SweepUnit) * nunits,
                                cudaMemcpyHostToDevice));
         CUDA_TRY(h, cudaMemcpy(h->d_reg_uot, h->reg_unit_of_tile.data(), sizeof(int) * h->reg_unit_of_tile.size(),
                                cudaMemcpyHostToDevice));
+        const std::vector<int> order = ticket_order(h->reg_units);
+        CUDA_TRY(h, cudaMemcpy(h->d_reg_order, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice));
     }
     h->band_unit.assign(1, 0);
     CUDA_TRY(h, cudaMemset(h->d_status, 0, sizeof(int) * 4));
