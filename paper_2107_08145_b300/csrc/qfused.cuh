@@ -252,7 +252,7 @@ struct Acc2Const {
         thin = (float)P.thin;
     }
 };
-__global__ void __launch_bounds__(256, 3) qstep_df2_kernel(const df32 *__restrict__ JF, const float *__restrict__ chi,
+__global__ void __launch_bounds__(256, 4) qstep_df2_kernel(const df32 *__restrict__ JF, const float *__restrict__ chi,
                                                         const float *__restrict__ S, QParams P,
                                                         double *__restrict__ J, double *__restrict__ F,
                                                         double *__restrict__ Q)
