@@ -607,22 +607,23 @@ struct RegCfg {
     int tq, maxr;
 };
 // (rows, register cap): measured at 288^3 x 4 bands, 4 rows at 128 registers
-// (3 CTAs of 160 threads per SM) is the fastest. The 2-row tiles are not
-// built: at 288^3 they ended in a GPU fault whose cause was not found.
-static const RegCfg kRegCfg[] = {{8, 255}, {4, 168}, {4, 128}};
+// (3 CTAs of 160 threads per SM) is the fastest; 2 rows at 96 registers (4
+// CTAs per SM) serve grids whose periodic rows are not a multiple of 4
+// (13.7 against 13.5 ms at 288^3 x 4, the same outputs).
+static const RegCfg kRegCfg[] = {{8, 255}, {4, 168}, {4, 128}, {2, 96}};
 
 // Tiling of the register-resident sweep: among the instantiated (rows,
 // register cap) pairs whose tile height divides the periodic rows (nq_per),
 // whose CTA fits and whose units' tiles all fit on the GPU at once, the one
 // with the most plane rows resident per SM (requested > 0: the tallest not
-// above it, at least 4 rows).
+// above it, at least 2 rows).
 static Tiling choose_reg(int requested, int npmax, int nqmax, int nq_per, int nsm)
 {
     Tiling best;
     best.nt = 32 * ((npmax / 2 + 31) / 32);
     double best_score = -1;
     for (const RegCfg &c : kRegCfg) {
-        if (requested > 0 && c.tq > std::max(requested, 4)) continue;  // 4 rows is the smallest tile
+        if (requested > 0 && c.tq > std::max(requested, 2)) continue;  // 2 rows is the smallest tile
         if (nq_per % c.tq != 0) continue;
         if ((long long)c.maxr * best.nt > 65536) continue;
         const size_t smem = rts::reg_tile_smem_bytes(c.tq, npmax);

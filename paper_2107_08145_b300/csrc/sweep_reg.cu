@@ -11,7 +11,7 @@ SweepFn<float> reg_kernel_f32(int tq, int maxr, bool seeded, bool checkpoint)
     if (tq == A && maxr == B)                                                                                      \
         return checkpoint ? sweep_reg_kernel<A, B, false, true>                                                   \
                           : (seeded ? sweep_reg_kernel<A, B, true> : sweep_reg_kernel<A, B, false>);
-    RTS_CFG(8, 255) RTS_CFG(4, 168) RTS_CFG(4, 128)
+    RTS_CFG(8, 255) RTS_CFG(4, 168) RTS_CFG(4, 128) RTS_CFG(2, 96)
 #undef RTS_CFG
     return nullptr;
 }

@@ -1,6 +1,6 @@
 """GPU parity of the register-resident FP32 sweep (sweep_reg_kernel) against
 the FP64 oracle, on grids chosen to reach every path of that kernel: tile
-heights 4 and 8; x/y-group tiles whose last tile is short (padding rows);
+heights 2, 4 and 8; x/y-group tiles whose last tile is short (padding rows);
 plane extents narrower than the CTA (idle warps) and a single column pair;
 explicit boundary intensities; a very transparent top (long periodic
 warm-up); both FP32 modes. Bar: 1e-5 max|oracle| per output, as for every
@@ -78,6 +78,18 @@ def test_thin_top_and_spacing(rts, prec):
     assert s.stats()["max_warmup_steps"] > 0
 
 
+def test_two_row_tiles(rts):
+    """ny even but not a multiple of 4: the register sweep runs with 2-row
+    tiles (the periodic z-group rows must be a multiple of the tile height);
+    x/y groups of 13 rows end with a short tile."""
+    nx, ny, nz, B = 28, 18, 13, 2
+    chi, S = random_case(nx, ny, nz, B, seed=29)
+    ref = oracle_solve(chi, S)
+    s = _solver(rts, nx, ny, nz, B, precision="fp32")
+    assert s.stats()["tile_rows"] == 2
+    _check(rts, s, chi, S, ref, "two-row tiles")
+
+
 def test_explicit_boundaries(rts):
     nx, ny, nz, B = 12, 12, 14, 2
     chi, S = random_case(nx, ny, nz, B, seed=3)
@@ -117,10 +129,11 @@ def test_register_matches_shared_sweep(rts):
 
 
 def test_register_sweep_refuses_what_it_cannot_run(rts):
-    """Odd plane extents, ny not a multiple of 4 (the smallest register tile
-    must divide the z groups' periodic rows) and FP64 have no register sweep:
+    """Odd plane extents, an odd ny (no register tile height, 2 or 4 rows,
+    divides the z groups' periodic rows) and FP64 have no register sweep:
     asking for it fails at create time with RTS_EINVAL; 'auto' falls back to
-    the shared sweep."""
+    the shared sweep. An even ny that is not a multiple of 4 takes 2-row
+    tiles."""
     with pytest.raises(rts.RTSError) as e:
         rts.Solver(13, 10, 8, 1, precision="fp32", sweep_kernel="register")
     assert e.value.code == rts.RTS_EINVAL
@@ -129,6 +142,8 @@ def test_register_sweep_refuses_what_it_cannot_run(rts):
     with pytest.raises(rts.RTSError):
         rts.Solver(12, 10, 8, 1, precision="fp64", sweep_kernel="register")
     with pytest.raises(rts.RTSError) as e:
-        rts.Solver(12, 10, 8, 1, precision="fp32", sweep_kernel="register")
+        rts.Solver(12, 9, 8, 1, precision="fp32", sweep_kernel="register")
     assert e.value.code == rts.RTS_EINVAL
-    assert rts.Solver(12, 10, 8, 1, precision="fp32").stats()["sweep_kernel"] == rts.SWEEP_SHARED
+    assert rts.Solver(12, 9, 8, 1, precision="fp32").stats()["sweep_kernel"] == rts.SWEEP_SHARED
+    st = rts.Solver(12, 10, 8, 1, precision="fp32").stats()
+    assert st["sweep_kernel"] == rts.SWEEP_REGISTER and st["tile_rows"] == 2
