@@ -211,6 +211,45 @@ def _traffic_from_profile(prec, grid, tile_rows, kernel):
         return None
 
 
+def _solve_bytes(prec, ms_step, sweep_traffic):
+    """Bytes of one whole FP32 solve of the bench workload (register path):
+    the compulsory floor (chi, S read once, J, F, Q written once: 72 B per
+    point at 4 bands), the streaming model of the method (744 B per point at
+    4 bands: each of the 6 groups streams every band's chi and S, its J/F
+    partials leave and return once, and the Q step reads chi, S and writes
+    J, F, Q), the
+    algorithmic bytes of the four kernels as built (x transpose, sweep,
+    reduction, Q step), and the DRAM bytes ncu measured for the sweep, the
+    reduction and the Q step (profiles/sweep_reg_rts288x4_dram.md, only while
+    their sources are unchanged) plus the transpose's algorithmic bytes."""
+    if prec == "fp64":
+        return None
+    n = NX * NY * NZ
+    alg = {"transpose": 4 * NB * n * 4,             # chi, S read and written once
+           "sweep": sweep_algorithmic_bytes(prec),
+           "reduction": NB * (NDIR // 4) * n * 16 + NB * 4 * n * 8,  # raw slots in, double-float J_b, F_b out
+           "q_step": NB * 4 * n * 8 + 2 * NB * n * 4 + 5 * n * 8}    # J_b, F_b and chi, S in; J, F, Q out
+    out = {"floor_bytes": (8 * NB + 40) * n, "streaming_model_bytes": (6 * 8 * NB + 6 * 2 * 40 + 8 * NB + 40) * n,
+           "algorithmic_bytes": sum(alg.values()), "algorithmic_by_kernel": alg}
+    rec = {}
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "sweep_reg_rts288x4_dram.md")):
+            if line.startswith("- ") and ":" in line:
+                k, v = line[2:].split(":", 1)
+                rec[k.strip()] = v.strip()
+    except OSError:
+        rec = {}
+    q = os.path.join(ROOT, "paper_2107_08145_b300", "csrc", "qfused.cuh")
+    if sweep_traffic and rec.get("qfused_source_sha256_16") == hashlib.sha256(open(q, "rb").read()).hexdigest()[:16]:
+        try:
+            dram = sweep_traffic + int(rec["qf_reduce_dram_bytes"]) + int(rec["qstep_df2_dram_bytes"]) + alg["transpose"]
+            out["dram_bytes"] = dram
+            out["dram_gbs"] = round(dram / (ms_step * 1e-3) / 1e9, 1)
+        except (KeyError, ValueError):
+            pass
+    return out
+
+
 FP64_PEAK_GFLOPS = 1250.0  # nominal B300 FP64 rate; no measured FP64 peak is on record
 
 
@@ -256,8 +295,9 @@ def _fp64_roofline(st):
 
 def sweep_algorithmic_bytes(prec, nb=NB, ndir=NDIR):
     """Per launch: every sweep unit (band x group of 4 rays) reads its band's
-    chi and S once and writes its 4 partial sums (J, Fx, Fy, Fz) once; plus
-    the upward intensities at the top."""
+    chi and S once and writes 4 values per point once (its raw slot
+    intensities, or its partial sums J, Fx, Fy, Fz); plus the upward
+    intensities at the top."""
     es = 8 if prec == "fp64" else 4
     n = NX * NY * NZ
     units = nb * (ndir // 4)
@@ -597,6 +637,8 @@ def run_ours(args):
                 "traffic": _traffic_from_profile(prec, (NX, NY, NZ), TILE_ROWS, st["sweep_kernel"]),
                 "algorithmic_bytes_per_launch": alg,
                 "sweep_ms_mean": round(sweep_ms, 4), "launches_timed": st["timed_solves"]}
+    if roofline["traffic"]:  # the same fraction from the DRAM bytes ncu measured
+        roofline["frac_dram"] = round(roofline["traffic"] / (sweep_ms * 1e-3) / 1e9 / roofline["peak"], 5)
     phases = {k: round(st[k], 4) for k in ("ms_transpose", "ms_sweep", "ms_reduce", "ms_qstep")}
 
     extra = {}
@@ -708,6 +750,8 @@ def run_ours(args):
             "config": _config(prec, ws, st["sweep_kernel"]), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clk.summary(), "gpu_launches": st["kernels_per_solve"] * args.steps,
             "phases_ms": phases,
+            "solve_bytes": (_solve_bytes(prec, ms, roofline["traffic"])
+                            if (NX, NY, NZ) == (288, 288, 288) and st["sweep_kernel"] == 2 else None),
             "wrap": {"max_warmup_planes": st["max_warmup_steps"], "mean_warmup_planes": st["mean_warmup_steps"]},
             "adjoint_over_forward": ratio, "adjoint": adj, "batched": batched, "large": large,
             "sequence": sequence}
