@@ -130,14 +130,23 @@ def test_adjoint_fp64_explicit_boundaries(rts):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_compensated"])
-def test_adjoint_fp32_vs_oracle(rts, precision):
+@pytest.mark.parametrize("sweep,chunk", [("auto", 0), ("auto", 1), ("shared", 0)])
+def test_adjoint_fp32_vs_oracle(rts, precision, sweep, chunk):
+    """Both FP32 adjoint paths: on the register sweep (its checkpoint
+    instantiation, the double-float reduction and Q-step transpose; with one
+    band per checkpoint also the general reduction over a chunk's units) and
+    on the shared-memory sweep."""
     nx, ny, nz, B = 24, 20, 18, 2
     chi, S = random_case(nx, ny, nz, B, seed=8)
-    s = rts.Solver(nx, ny, nz, B, precision=precision, adjoint=True)
+    s = rts.Solver(nx, ny, nz, B, precision=precision, adjoint=True, adjoint_chunk_bands=chunk, sweep_kernel=sweep)
+    st = s.stats()
+    assert st["sweep_kernel"] == (rts.SWEEP_SHARED if sweep == "shared" else rts.SWEEP_REGISTER)
+    if chunk:
+        assert st["adjoint_chunk_bands"] == chunk
     cot = _cotangents(B, s.n_up, nx, ny, nz, seed=12)
     got = _gpu_adjoint(s, chi, S, cot)
     ref = _oracle_adjoint(chi, S, cot)
-    _check(got, ref, FP32_TOL, precision)
+    _check(got, ref, FP32_TOL, (precision, sweep, chunk))
 
 
 def test_adjoint_null_gq_equals_zero_gq(rts):
