@@ -521,6 +521,57 @@ def _large_timing(rts, torch):
     return r
 
 
+def _extensions_timing(rts, torch, chi, S, solve_ms, peak):
+    """The solver's extensions on the bench workload (FP32): the spatial
+    decomposition into 4 slabs of levels iterated on their boundary
+    intensities (against the undecomposed solve's outputs and time), the
+    scattering source iteration S = (1 - eps) J + eps B (eps = 0.3, from
+    S = B), and the MHD -> RTS input step (trilinear interpolation of ln T,
+    ln rho and the band table lookup) with its bytes against HBM. CUDA
+    events on the current stream."""
+    import numpy as np
+    from workloads.opacity import mhd_fields, synthetic_table
+
+    def timed(fn, n=3):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n, r
+
+    res = {}
+    ref = rts.Solver(NX, NY, NZ, NB, precision="fp32").solve(chi, S)
+    dsol = rts.DecomposedSolver(NX, NY, NZ, NB, nblocks=4, precision="fp32")
+    ms, (out, iters) = timed(lambda: dsol.solve(chi, S))
+    dq = float((out["Q"] - ref["Q"]).abs().max() / ref["Q"].abs().max())
+    res["decomposition"] = {"slabs": 4, "ms": round(ms, 2), "iterations": iters, "over_undecomposed": round(ms / solve_ms, 2),
+                            "q_rad_max_diff_rel_to_max": dq}
+    del dsol, out
+    ssol = rts.Solver(NX, NY, NZ, NB, precision="fp32", scatter=True)
+    eps = torch.full_like(S, 0.3)
+    ms, (S_new, out, iters) = timed(lambda: ssol.scatter_solve(chi, S, eps), n=1)
+    res["scattering"] = {"eps": 0.3, "ms": round(ms, 2), "iterations": iters, "ms_per_iteration": round(ms / max(iters, 1), 2)}
+    del ssol, S_new, out, eps
+    T, rho = mhd_fields(NX, NY, NZ, seed=0)
+    tab = synthetic_table(nb=NB)
+    Td = torch.tensor(T, dtype=torch.float32, device="cuda")
+    rd = torch.tensor(rho, dtype=torch.float32, device="cuda")
+    tab = dict(tab, ln_kappa=torch.tensor(tab["ln_kappa"], dtype=torch.float32, device="cuda"),
+               ln_B=torch.tensor(tab["ln_B"], dtype=torch.float32, device="cuda"))
+    fe_out = (torch.empty((NB, NZ, NY, NX), device="cuda"), torch.empty((NB, NZ, NY, NX), device="cuda"))
+    ms, _ = timed(lambda: rts.front_end(Td, rd, tab, precision="fp32", out=fe_out), n=20)
+    nbytes = (2 + 2 * NB) * 4 * NX * NY * NZ  # T, rho read; chi_b, S_b written
+    res["front_end"] = {"ms": round(ms, 3), "algorithmic_bytes": nbytes, "achieved_gbs": round(nbytes / (ms * 1e-3) / 1e9, 1),
+                        "frac_of_hbm": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}
+    del Td, rd, fe_out
+    torch.cuda.empty_cache()
+    return res
+
+
 def _sequence_timing(rts, torch, s, chi, S, stream, steps=6):
     """Cold solves and warm-started solves of a slowly changing atmosphere:
     ms per solve (library phase timer: sweep) and the planes each x/y group
@@ -730,6 +781,12 @@ def run_ours(args):
     if not args.skip_sequence and prec != "fp64" and ws == 1:
         sequence = _sequence_timing(rts, torch, s, chi, S, stream)
 
+    # the extensions on the same workload: spatial decomposition, scattering
+    # iteration, MHD -> RTS input step
+    extensions = None
+    if not args.skip_extensions and prec != "fp64" and ws == 1:
+        extensions = _extensions_timing(rts, torch, chi, S, ms, hbm if hbm else 6400.0)
+
     batched = None
     if not args.skip_batched:
         batched = _batched_timing(rts, torch, max(3, min(args.steps, 10)))
@@ -754,7 +811,7 @@ def run_ours(args):
                             if (NX, NY, NZ) == (288, 288, 288) and st["sweep_kernel"] == 2 else None),
             "wrap": {"max_warmup_planes": st["max_warmup_steps"], "mean_warmup_planes": st["mean_warmup_steps"]},
             "adjoint_over_forward": ratio, "adjoint": adj, "batched": batched, "large": large,
-            "sequence": sequence}
+            "sequence": sequence, "extensions": extensions}
     line.update(extra)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -847,6 +904,7 @@ def main():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-large", action="store_true")
     ap.add_argument("--skip-sequence", action="store_true")
+    ap.add_argument("--skip-extensions", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--grid", default="288,288,288",
                     help="NX,NY,NZ override (profiling of smaller cases); the metric is quoted at 288^3")

@@ -437,7 +437,8 @@ typedef struct {
     double lnR0, dlnR;     /* ln rho of table row 0, step (> 0) */
     const void *ln_kappa;  /* [nbands][nR][nT] ln of the opacity per unit density */
     const void *ln_B;      /* [nbands][nT] ln of the band source function */
-    double shift[3];       /* RTS point (0,0,0) on the MHD grid, in cells */
+    double shift[3];       /* RTS point (0,0,0) on the MHD grid, in cells;
+                              finite, |shift| <= 2^20, else RTS_EINVAL */
 } rts_front_table;
 rts_status rts_front_end(const rts_grid *g, const rts_front_table *tab, rts_precision prec,
                          const void *T_mhd, const void *rho_mhd, void *chi, void *S, void *stream,

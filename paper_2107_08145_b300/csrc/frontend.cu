@@ -8,8 +8,9 @@
 //                                 x, y; clamped to the first / last layer in z)
 //   ln kappa_b                    bilinear in the (ln T, ln rho) table
 //   chi_b = exp(ln kappa_b) rho,  S_b = exp(ln B_b(ln T)), ln B_b linear in ln T
-// Table coordinates outside the table are clamped to its edge. One thread per
-// RTS point; the tables are read through the read-only cache.
+// Table coordinates outside the table are clamped to its edge. FP64: one
+// thread per RTS point. FP32: tiled, ln T and ln rho taken once per MHD cell
+// in shared memory. The tables are read through the read-only cache.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -87,57 +88,111 @@ __global__ void __launch_bounds__(256) front_end_kernel(FrontArgs A, const T *__
     }
 }
 
-// FP32: the same steps in float (logs and exps of the FP32 library)
-__global__ void __launch_bounds__(256) front_end_f32_kernel(FrontArgs A, const float *__restrict__ Tm,
-                                                              const float *__restrict__ rho,
-                                                              const float *__restrict__ lnk,
-                                                              const float *__restrict__ lnB, float *__restrict__ chi,
-                                                              float *__restrict__ S)
+// FP32: the same steps in float, tiled. A CTA covers kFX x kFY points of one
+// RTS level. The stagger is the same for every point, so the 8 MHD cells of
+// a point are (i, j, z0) + (fx, fy, 0) + {0, 1}^3 with fixed weights (wx, wy)
+// and the level's clamped (z0, wz): the CTA takes ln T and ln rho once per
+// MHD cell of its (kFX + 1) x (kFY + 1) x 2 footprint into shared memory
+// (4.3 logarithms per point instead of 16) and interpolates from there.
+constexpr int kFX = 96, kFY = 16, kFThreads = 2 * kFX;
+
+struct FrontArgsF {
+    int nx, ny, nz, nb, nT, nR;
+    int fx, fy, fz;                  // floor of the shift
+    float wx, wy, wz;                // shift - floor(shift)
+    float lnT0, idlnT, lnR0, idlnR;  // table origin and 1 / step
+};
+
+// node_weight in float; x > 0 makes the truncation a floor
+__device__ __forceinline__ void node_weight_f(float x, int n, int &i0, float &w)
 {
-    const long long nxy = (long long)A.nx * A.ny, N = nxy * A.nz;
-    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= N) return;
-    const int i = (int)(p % A.nx), j = (int)((p / A.nx) % A.ny), k = (int)(p / nxy);
-    const float ux = (float)(i + A.sx), uy = (float)(j + A.sy);
-    const double uz = k + A.sz;
-    const float fx = floorf(ux), fy = floorf(uy);
-    const float wx = ux - fx, wy = uy - fy;
-    int x0 = (int)fx % A.nx, y0 = (int)fy % A.ny;
-    if (x0 < 0) x0 += A.nx;
-    if (y0 < 0) y0 += A.ny;
-    const int x1 = x0 + 1 == A.nx ? 0 : x0 + 1, y1 = y0 + 1 == A.ny ? 0 : y0 + 1;
-    int z0;
-    double wzd;
-    node_weight(uz, A.nz, z0, wzd);
-    const float wz = (float)wzd;
-    const int z1 = A.nz > 1 ? z0 + 1 : z0;
-    const int xs[2] = {x0, x1}, ys[2] = {y0, y1}, zs[2] = {z0, z1};
-    const float wxs[2] = {1.f - wx, wx}, wys[2] = {1.f - wy, wy}, wzs[2] = {1.f - wz, wz};
-    float lt = 0.f, lr = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const long long q = (long long)zs[c >> 2] * nxy + (long long)ys[(c >> 1) & 1] * A.nx + xs[c & 1];
-        const float w = wzs[c >> 2] * wys[(c >> 1) & 1] * wxs[c & 1];
-        lt = fmaf(w, logf(Tm[q]), lt);
-        lr = fmaf(w, logf(rho[q]), lr);
+    if (!(x > 0.f)) { i0 = 0; w = 0.f; return; }
+    if (x >= (float)(n - 1)) { i0 = n > 1 ? n - 2 : 0; w = n > 1 ? 1.f : 0.f; return; }
+    i0 = (int)x;
+    w = x - (float)i0;
+}
+
+__global__ void __launch_bounds__(kFThreads) front_end_f32_kernel(FrontArgsF A, const float *__restrict__ Tm,
+                                                                  const float *__restrict__ rho,
+                                                                  const float *__restrict__ lnk,
+                                                                  const float *__restrict__ lnB,
+                                                                  float *__restrict__ chi, float *__restrict__ S)
+{
+    __shared__ float sT[2][kFY + 1][kFX + 1], sR[2][kFY + 1][kFX + 1];
+    const int ntx = (A.nx + kFX - 1) / kFX, nty = (A.ny + kFY - 1) / kFY;
+    const int k = blockIdx.x / (ntx * nty), t = blockIdx.x - k * (ntx * nty);
+    const int i0 = (t % ntx) * kFX, j0 = (t / ntx) * kFY;
+    // the level's two MHD layers (the clamp of node_weight on z = k + shift_z)
+    int z0 = k + A.fz;
+    float wz = A.wz;
+    if (z0 < 0) {
+        z0 = 0;
+        wz = 0.f;
+    } else if (z0 >= A.nz - 1) {
+        z0 = A.nz > 1 ? A.nz - 2 : 0;
+        wz = A.nz > 1 ? 1.f : 0.f;
     }
-    const float rh = expf(lr);
-    int it, ir;
-    double atd, ard;
-    node_weight(((double)lt - A.lnT0) / A.dlnT, A.nT, it, atd);
-    node_weight(((double)lr - A.lnR0) / A.dlnR, A.nR, ir, ard);
-    const float at = (float)atd, ar = (float)ard;
-    const int it1 = A.nT > 1 ? it + 1 : it, ir1 = A.nR > 1 ? ir + 1 : ir;
-    for (int b = 0; b < A.nb; ++b) {
-        const float *kb = lnk + (long long)b * A.nR * A.nT;
-        const float lk = (1.f - ar) * ((1.f - at) * __ldg(kb + (long long)ir * A.nT + it) +
-                                       at * __ldg(kb + (long long)ir * A.nT + it1)) +
-                         ar * ((1.f - at) * __ldg(kb + (long long)ir1 * A.nT + it) +
-                               at * __ldg(kb + (long long)ir1 * A.nT + it1));
-        const float *bb = lnB + (long long)b * A.nT;
-        const float lb = (1.f - at) * __ldg(bb + it) + at * __ldg(bb + it1);
-        chi[(long long)b * N + p] = expf(lk) * rh;
-        S[(long long)b * N + p] = expf(lb);
+    const int z1 = A.nz > 1 ? z0 + 1 : z0;
+    const long long nxy = (long long)A.nx * A.ny, N = nxy * A.nz;
+    int xb = (i0 + A.fx) % A.nx, yb = (j0 + A.fy) % A.ny;
+    if (xb < 0) xb += A.nx;
+    if (yb < 0) yb += A.ny;
+    // footprint: thread (c, h) loads column c of rows h, h + 2, ..; the last
+    // column (kFX) goes to threads 0 .. 2 (kFY + 1) - 1
+    const int c = threadIdx.x % kFX, h = threadIdx.x / kFX;
+    const int gx = (xb + c) % A.nx;
+#pragma unroll
+    for (int zz = 0; zz < 2; ++zz) {
+        const float *tz = Tm + (long long)(zz ? z1 : z0) * nxy, *rz = rho + (long long)(zz ? z1 : z0) * nxy;
+        int gy = (yb + h) % A.ny;
+#pragma unroll
+        for (int rr = h; rr <= kFY; rr += kFThreads / kFX) {
+            const long long q = (long long)gy * A.nx + gx;
+            sT[zz][rr][c] = logf(__ldg(tz + q));
+            sR[zz][rr][c] = logf(__ldg(rz + q));
+            gy += kFThreads / kFX;
+            if (gy >= A.ny) gy -= A.ny;
+            if (gy >= A.ny) gy -= A.ny;
+        }
+    }
+    if (threadIdx.x < 2 * (kFY + 1)) {
+        const int zz = threadIdx.x / (kFY + 1), rr = threadIdx.x - zz * (kFY + 1);
+        const long long q = (long long)(zz ? z1 : z0) * nxy + (long long)((yb + rr) % A.ny) * A.nx + (xb + kFX) % A.nx;
+        sT[zz][rr][kFX] = logf(__ldg(Tm + q));
+        sR[zz][rr][kFX] = logf(__ldg(rho + q));
+    }
+    __syncthreads();
+    const int i = i0 + c;
+    if (i >= A.nx) return;
+    const float wx1 = A.wx, wx0 = 1.f - A.wx, wy1 = A.wy, wy0 = 1.f - A.wy, wz0 = 1.f - wz;
+    for (int r = threadIdx.x / kFX; r < kFY && j0 + r < A.ny; r += kFThreads / kFX) {
+        float lt = 0.f, lr = 0.f;
+#pragma unroll
+        for (int zz = 0; zz < 2; ++zz) {
+            const float w = zz ? wz : wz0;
+            const float t0 = fmaf(wx1, sT[zz][r][c + 1], wx0 * sT[zz][r][c]);
+            const float t1 = fmaf(wx1, sT[zz][r + 1][c + 1], wx0 * sT[zz][r + 1][c]);
+            const float r0 = fmaf(wx1, sR[zz][r][c + 1], wx0 * sR[zz][r][c]);
+            const float r1 = fmaf(wx1, sR[zz][r + 1][c + 1], wx0 * sR[zz][r + 1][c]);
+            lt = fmaf(w, fmaf(wy1, t1, wy0 * t0), lt);
+            lr = fmaf(w, fmaf(wy1, r1, wy0 * r0), lr);
+        }
+        const float rh = expf(lr);
+        int it, ir;
+        float at, ar;
+        node_weight_f((lt - A.lnT0) * A.idlnT, A.nT, it, at);
+        node_weight_f((lr - A.lnR0) * A.idlnR, A.nR, ir, ar);
+        const int it1 = A.nT > 1 ? it + 1 : it, ir1 = A.nR > 1 ? ir + 1 : ir;
+        const long long p = (long long)k * nxy + (long long)(j0 + r) * A.nx + i;
+        for (int b = 0; b < A.nb; ++b) {
+            const float *kb = lnk + (long long)b * A.nR * A.nT;
+            const float lk = (1.f - ar) * ((1.f - at) * __ldg(kb + ir * A.nT + it) + at * __ldg(kb + ir * A.nT + it1)) +
+                             ar * ((1.f - at) * __ldg(kb + ir1 * A.nT + it) + at * __ldg(kb + ir1 * A.nT + it1));
+            const float *bb = lnB + (long long)b * A.nT;
+            const float lb = (1.f - at) * __ldg(bb + it) + at * __ldg(bb + it1);
+            chi[(long long)b * N + p] = expf(lk) * rh;
+            S[(long long)b * N + p] = expf(lb);
+        }
     }
 }
 
@@ -155,6 +210,8 @@ extern "C" rts_status rts_front_end(const rts_grid *g, const rts_front_table *ta
         return msg("table needs nbands, nT, nR >= 1 and positive steps"), RTS_EINVAL;
     if (!T_mhd || !rho_mhd || !chi || !S || !tab->ln_kappa || !tab->ln_B)
         return msg("NULL array"), RTS_EINVAL;
+    for (int d = 0; d < 3; ++d)
+        if (!(fabs(tab->shift[d]) <= 1048576.0)) return msg("shift must be finite, |shift| <= 2^20"), RTS_EINVAL;
     if (prec != RTS_FP64 && prec != RTS_FP32_MIXED && prec != RTS_FP32_COMPENSATED)
         return msg("unknown precision"), RTS_EINVAL;
     FrontArgs A;
@@ -162,16 +219,26 @@ extern "C" rts_status rts_front_end(const rts_grid *g, const rts_front_table *ta
     A.sx = tab->shift[0]; A.sy = tab->shift[1]; A.sz = tab->shift[2];
     A.lnT0 = tab->lnT0; A.dlnT = tab->dlnT; A.lnR0 = tab->lnR0; A.dlnR = tab->dlnR;
     const long long N = (long long)g->nx * g->ny * g->nz;
-    const unsigned blocks = (unsigned)((N + 255) / 256);
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == RTS_FP64)
+    if (prec == RTS_FP64) {
+        const unsigned blocks = (unsigned)((N + 255) / 256);
         front_end_kernel<double><<<blocks, 256, 0, st>>>(A, (const double *)T_mhd, (const double *)rho_mhd,
                                                          (const double *)tab->ln_kappa, (const double *)tab->ln_B,
                                                          (double *)chi, (double *)S);
-    else
-        front_end_f32_kernel<<<blocks, 256, 0, st>>>(A, (const float *)T_mhd, (const float *)rho_mhd,
-                                                            (const float *)tab->ln_kappa, (const float *)tab->ln_B,
-                                                            (float *)chi, (float *)S);
+    } else {
+        FrontArgsF F;
+        F.nx = A.nx; F.ny = A.ny; F.nz = A.nz; F.nb = A.nb; F.nT = A.nT; F.nR = A.nR;
+        const double *sh = tab->shift;
+        F.fx = (int)floor(sh[0]); F.fy = (int)floor(sh[1]); F.fz = (int)floor(sh[2]);
+        F.wx = (float)(sh[0] - floor(sh[0])); F.wy = (float)(sh[1] - floor(sh[1])); F.wz = (float)(sh[2] - floor(sh[2]));
+        F.lnT0 = (float)tab->lnT0; F.idlnT = (float)(1.0 / tab->dlnT);
+        F.lnR0 = (float)tab->lnR0; F.idlnR = (float)(1.0 / tab->dlnR);
+        const long long tiles = (long long)((g->nx + kFX - 1) / kFX) * ((g->ny + kFY - 1) / kFY) * g->nz;
+        if (tiles > 0x7fffffffLL) return msg("grid too large for the FP32 input step"), RTS_EINVAL;
+        front_end_f32_kernel<<<(unsigned)tiles, kFThreads, 0, st>>>(F, (const float *)T_mhd, (const float *)rho_mhd,
+                                                                    (const float *)tab->ln_kappa,
+                                                                    (const float *)tab->ln_B, (float *)chi, (float *)S);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return msg(cudaGetErrorString(e)), RTS_ECUDA;
     msg("ok");

@@ -48,20 +48,32 @@ __global__ void __launch_bounds__(256) exp_kernel(const T *__restrict__ in, T *_
 // taken here with dtau_d = ds_d chi_p / 2, a lower bound (chi_up >= 0), so
 // that L* never exceeds the true diagonal (1 - q grows with dtau): a larger
 // L* over-corrects and the iteration can diverge. Only the preconditioner:
-// the fixed point does not depend on it.
+// the fixed point does not depend on it. dirw lists each distinct segment
+// length once with the summed weight of its directions.
 template <typename T>
 __global__ void __launch_bounds__(256) lambda_star_kernel(const T *__restrict__ chi, const double *__restrict__ dirw,
                                                            int ndir, long long n, T *__restrict__ lstar)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const double c = (double)chi[i];
-        double l = 0.0;
-        for (int d = 0; d < ndir; ++d) {
-            const double x = 0.5 * dirw[2 * d] * c;
-            const double q = x < 1e-4 ? 1.0 - 0.5 * x + x * x / 6.0 : -expm1(-x) / x;
-            l += dirw[2 * d + 1] * (1.0 - q);
+        if constexpr (sizeof(T) == 4) {  // FP32 inputs: the preconditioner in float
+            const float cf = chi[i];
+            float lf = 0.f;
+            for (int d = 0; d < ndir; ++d) {
+                const float x = 0.5f * (float)dirw[2 * d] * cf;  // 1 - q: its series below x = 0.03
+                const float om = x < 0.03f ? x * (0.5f - x * (1.f / 6.f - x * (1.f / 24.f))) : 1.f + expm1f(-x) / x;
+                lf = fmaf((float)dirw[2 * d + 1], om, lf);
+            }
+            lstar[i] = lf;
+        } else {
+            const double c = (double)chi[i];
+            double l = 0.0;
+            for (int d = 0; d < ndir; ++d) {
+                const double x = 0.5 * dirw[2 * d] * c;
+                const double q = x < 1e-4 ? 1.0 - 0.5 * x + x * x / 6.0 : -expm1(-x) / x;
+                l += dirw[2 * d + 1] * (1.0 - q);
+            }
+            lstar[i] = (T)l;
         }
-        lstar[i] = (T)l;
     }
 }
 
@@ -87,11 +99,20 @@ __global__ void __launch_bounds__(256) scatter_update_kernel(const Acc *__restri
         const long long b = i / N, p = i - b * N;
         const double J = acc_val(JF[b * 4 * N + p]);
         const double e = (double)eps[i], s = (double)S[i];
-        const double ds = ((1.0 - e) * J + e * (double)Bp[i] - s) / (1.0 - (1.0 - e) * (double)lstar[i]);
-        const T sn = (T)(s + ds);
-        S[i] = sn;
-        const double den = fabs((double)sn);
-        m = fmaxf(m, (float)(den > 0.0 ? fabs(ds) / den : (ds != 0.0 ? 1.0 : 0.0)));
+        const double num = (1.0 - e) * J + e * (double)Bp[i] - s;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 S: the residual in double (it cancels), the rest in float
+            const float ds = (float)num / (1.f - (1.f - eps[i]) * lstar[i]);
+            const float sn = S[i] + ds, den = fabsf(sn);
+            S[i] = sn;
+            m = fmaxf(m, den > 0.f ? fabsf(ds) / den : (ds != 0.f ? 1.f : 0.f));
+        } else {
+            const double ds = num / (1.0 - (1.0 - e) * (double)lstar[i]);
+            const T sn = (T)(s + ds);
+            S[i] = sn;
+            const double den = fabs((double)sn);
+            m = fmaxf(m, (float)(den > 0.0 ? fabs(ds) / den : (ds != 0.0 ? 1.0 : 0.0)));
+        }
     }
     for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(dsmax, __float_as_uint(m));
@@ -311,7 +332,8 @@ struct rts_handle {
     // per-direction path lengths and weights it is formed from, the iteration's
     // largest relative change of S
     void *d_lstar = nullptr;
-    double *d_dirw = nullptr;     // [ndir][2]: ds_d, w_d
+    double *d_dirw = nullptr;     // [n_lsd][2]: a segment length ds and the summed weight of its directions
+    int n_lsd = 0;
     unsigned *d_dsmax = nullptr;
     rts::SweepUnit *d_units = nullptr;
     int *d_unit_of_tile = nullptr;
@@ -1130,11 +1152,16 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         h->d_lstar = base + o_lstar;
         h->d_dirw = (double *)(base + o_dirw);
         h->d_dsmax = (unsigned *)(base + o_dsmax);
-        std::vector<double> dw(2 * h->ndir);
+        // (ds_d, w_d) with the weights of directions of equal segment length
+        // summed (S4: 3 lengths for 24 directions)
+        std::vector<double> dw;
         for (int d = 0; d < h->ndir; ++d) {
-            dw[2 * d] = geo[d].ds;
-            dw[2 * d + 1] = h->w[d];
+            size_t e = 0;
+            while (e < dw.size() && dw[e] != geo[d].ds) e += 2;
+            if (e == dw.size()) dw.insert(dw.end(), {geo[d].ds, 0.0});
+            dw[e + 1] += h->w[d];
         }
+        h->n_lsd = (int)(dw.size() / 2);
         CUDA_TRY(h, cudaMemcpy(h->d_dirw, dw.data(), sizeof(double) * dw.size(), cudaMemcpyHostToDevice));
     }
     if (h->use_reg) {
@@ -1369,7 +1396,7 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
     if (e != cudaSuccess) return fail(h, RTS_ECUDA, "sweep launch: %s", cudaGetErrorString(e));
     kernels += 1;
     if (ev) CUDA_TRY(h, cudaEventRecord(ev[2], st));
-    if (reg && h->qf_ok && !reduce_only && (J || F || Q)) {
+    if (reg && h->qf_ok && (reduce_only || J || F || Q)) {
         // the register sweep's raw partials: the streaming reduction into
         // double-float J_b, F_b, then the double-float Q step (both FP32 modes)
         rts::QParams P;
@@ -1381,10 +1408,13 @@ static rts_status solve_impl(rts_handle *h, const void *chi, const void *S, cons
             h->d_qfu, h->d_qfb, g.nx, g.ny, g.nz, B, (int)h->units.size(), h->qr_max_nat, h->qr_max_x, jf);
         CUDA_TRY(h, cudaGetLastError());
         if (ev) CUDA_TRY(h, cudaEventRecord(ev[3], st));
-        dim3 rb(32, 8), qg((g.nx + 31) / 32, (g.ny + rts::QS_TJ - 1) / rts::QS_TJ, (unsigned)g.nz);
-        rts::qstep_df2_kernel<<<qg, rb, 0, st>>>(jf, (const float *)chi, (const float *)S, P, J, F, Q);
-        CUDA_TRY(h, cudaGetLastError());
-        kernels += 2;
+        kernels += 1;
+        if (!reduce_only) {  // else the per-band J_b, F_b (double-float) stay in the handle's JF array
+            dim3 rb(32, 8), qg((g.nx + 31) / 32, (g.ny + rts::QS_TJ - 1) / rts::QS_TJ, (unsigned)g.nz);
+            rts::qstep_df2_kernel<<<qg, rb, 0, st>>>(jf, (const float *)chi, (const float *)S, P, J, F, Q);
+            CUDA_TRY(h, cudaGetLastError());
+            kernels += 1;
+        }
     } else if (J || F || Q || reduce_only) {
         dim3 rb(32, 8);
         rts::QParams P;
@@ -1749,7 +1779,7 @@ static rts_status scatter_impl(rts_handle *h, const void *chi, const void *Bp, c
     int dummy = 0;
     const void *c = chi;
     if (rts_status fs = form_chi<T>(h, c, dummy)) return fs;
-    lambda_star_kernel<T><<<cb, 256, 0, st>>>((const T *)c, h->d_dirw, h->ndir, n, (T *)h->d_lstar);
+    lambda_star_kernel<T><<<cb, 256, 0, st>>>((const T *)c, h->d_dirw, h->n_lsd, n, (T *)h->d_lstar);
     CUDA_TRY(h, cudaGetLastError());
     int it = 0;
     bool conv = false;
@@ -1757,8 +1787,13 @@ static rts_status scatter_impl(rts_handle *h, const void *chi, const void *Bp, c
         rts_status rs = solve_impl<T, Acc>(h, chi, S, bc, nullptr, nullptr, nullptr, nullptr, true);
         if (rs) return rs;
         CUDA_TRY(h, cudaMemsetAsync(h->d_dsmax, 0, sizeof(unsigned), st));
-        scatter_update_kernel<T, Acc><<<cb, 256, 0, st>>>((const Acc *)h->d_JF, (const T *)eps, (const T *)Bp,
-                                                          (const T *)h->d_lstar, (T *)S, h->N, h->B, h->d_dsmax);
+        if (h->use_reg && h->qf_ok && sizeof(T) == 4)  // the register sweep's reduction left double-float J_b
+            scatter_update_kernel<T, rts::df32><<<cb, 256, 0, st>>>((const rts::df32 *)h->d_JF, (const T *)eps,
+                                                                    (const T *)Bp, (const T *)h->d_lstar, (T *)S,
+                                                                    h->N, h->B, h->d_dsmax);
+        else
+            scatter_update_kernel<T, Acc><<<cb, 256, 0, st>>>((const Acc *)h->d_JF, (const T *)eps, (const T *)Bp,
+                                                              (const T *)h->d_lstar, (T *)S, h->N, h->B, h->d_dsmax);
         CUDA_TRY(h, cudaGetLastError());
         unsigned bits = 0;
         CUDA_TRY(h, cudaMemcpyAsync(&bits, h->d_dsmax, sizeof(unsigned), cudaMemcpyDeviceToHost, st));

@@ -6,7 +6,9 @@ v = exp(ln v) is formed from FP32 logarithms, each rounded relative to its
 own size, and the table's ln kappa carries ln T with slope up to ~3 (chi and
 S are positive).
 Grids with a ragged last CTA, several staggers, a table that the
-atmosphere overruns (clamping), and the 288^3 x 4 band case."""
+atmosphere overruns (clamping), and the 288^3 x 4 band case; for the tiled
+FP32 kernel also a single level, a 1 x 1 plane and shifts of several
+periods (the footprint wraps more than once)."""
 import numpy as np
 import pytest
 
@@ -60,6 +62,26 @@ def test_front_end_matches_oracle(rts, shape, shift, nb, prec, tol):
     for got, ref in ((chi, rchi), (S, rS)):
         g = got.double().cpu().numpy()
         assert (_rel(g, ref) <= tol) if tol else _fp32_ok(g, ref, lnT, lnR), _rel(g, ref)
+
+
+@pytest.mark.parametrize("shape,shift", [((100, 9, 1), (-0.5, -0.5, -0.5)), ((1, 1, 2), (3.5, -7.25, 1.5)),
+                                         ((97, 17, 4), (-200.5, 33.75, 2.0))])
+def test_front_end_fp32_edges(rts, shape, shift):
+    import torch
+
+    nx, ny, nz = shape
+    rng = np.random.default_rng(nx + ny)
+    T = (0.5 + rng.random((nz, ny, nx))).astype(np.float32)
+    rho = np.exp(rng.normal(size=(nz, ny, nx))).astype(np.float32)
+    tab = synthetic_table(nb=2, nT=40, nR=30, lnR_range=(-4.0, 2.0))
+    tab32 = dict(tab, ln_kappa=tab["ln_kappa"].astype(np.float32), ln_B=tab["ln_B"].astype(np.float32))
+    chi, S = rts.front_end(torch.tensor(T, device="cuda"), torch.tensor(rho, device="cuda"), tab, precision="fp32",
+                           shift=shift)
+    rchi, rS = oracle_front_end(T, rho, tab32, shift)
+    lnT, lnR = trilinear_log(T, shift), trilinear_log(rho, shift)
+    for got, ref in ((chi, rchi), (S, rS)):
+        g = got.double().cpu().numpy()
+        assert _fp32_ok(g, ref, lnT, lnR), _rel(g, ref)
 
 
 def test_front_end_288x4(rts):

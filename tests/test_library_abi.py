@@ -94,6 +94,26 @@ def test_create_rejects_too_many_levels_times_bands_without_gpu():
     L.rts_destroy(h)
 
 
+def test_front_end_rejects_bad_arguments_without_gpu():
+    """rts_front_end validates its table and the stagger shift (finite,
+    |shift| <= 2^20) before it launches anything; the array pointers are
+    never dereferenced on these paths."""
+    L = rts.load()
+    g = rts.Grid(8, 8, 8, 1.0, 1.0, 1.0)
+    err = ctypes.create_string_buffer(128)
+    fake = ctypes.c_void_p(16)
+
+    def call(shift=(-0.5, -0.5, -0.5), nT=4, dlnT=0.1):
+        tab = rts.FrontTable(2, nT, 3, 0.0, dlnT, 0.0, 0.1, fake, fake, (ctypes.c_double * 3)(*shift))
+        return L.rts_front_end(ctypes.byref(g), ctypes.byref(tab), rts.FP32_MIXED, fake, fake, fake, fake, None, err, 128)
+
+    assert call(shift=(float("nan"), 0.0, 0.0)) == rts.RTS_EINVAL and b"shift" in err.value
+    assert call(shift=(0.0, 2.0 ** 21, 0.0)) == rts.RTS_EINVAL and b"shift" in err.value
+    assert call(shift=(0.0, 0.0, float("inf"))) == rts.RTS_EINVAL
+    assert call(nT=0) == rts.RTS_EINVAL and b"table" in err.value
+    assert call(dlnT=0.0) == rts.RTS_EINVAL
+
+
 def test_product_path_does_not_import_oracle():
     """The library and its binding never reach the CPU oracle."""
     pkg = os.path.join(ROOT, "paper_2107_08145_b300")
