@@ -240,8 +240,11 @@ rts_status rts_solve_host_async(rts_handle *h, const void *chi, const void *S, c
  * lower bound of each segment's optical depth, so L* stays below the true
  * diagonal and the iteration stable): it only preconditions the iteration
  * (an accelerated Lambda iteration); the converged S solves the equation
- * above. The paper's alternative, a
- * Gauss-Seidel update along each ray, is not used: see the design notes.
+ * above. The paper's alternative, a Gauss-Seidel update along each ray, does
+ * not fit the direction-group sweep (the x/y groups advance their rays
+ * plane by plane across the horizontal), so every point is updated at once.
+ * In the FP32 modes L* and the update are taken in float, the residual
+ * (1 - eps) J + eps B - S in double.
  * Arguments: chi, B_src (the thermal source) and eps (photon destruction
  * probability, 0 < eps <= 1) are [B][Nz][Ny][Nx] device arrays of the sweep
  * precision; S (same layout) is the initial guess on entry and the converged

@@ -8,8 +8,7 @@ Bars (the FP64 path is the plain solve, the FP32 paths carry FP32 intensities):
          4 pi J for F, 4 pi sum_b (chi_b S_b + J_b / h) for Q_rad;
   FP32 (sweep in FP32, FP64 or double-float accumulation and Q step):
          max |gpu - oracle| <= 1e-5 max |oracle| per output.
-Each test prints its per-output table (pytest -s); the tables in the
-design notes come from these runs.
+Each test prints its per-output table (pytest -s).
 
 Configurations: the 288^3 x 4-band workload (FP64 and both FP32 modes,
 one oracle solve), one full band of the 512 x 512 x 256 x 16-band workload in
