@@ -9,8 +9,9 @@
 //   ln kappa_b                    bilinear in the (ln T, ln rho) table
 //   chi_b = exp(ln kappa_b) rho,  S_b = exp(ln B_b(ln T)), ln B_b linear in ln T
 // Table coordinates outside the table are clamped to its edge. FP64: one
-// thread per RTS point. FP32: tiled, ln T and ln rho taken once per MHD cell
-// in shared memory. The tables are read through the read-only cache.
+// thread per RTS point. FP32: tiled, the logarithms of T and rho taken once
+// per MHD cell in shared memory, in base 2. The tables are read through the
+// read-only cache.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -91,16 +92,20 @@ __global__ void __launch_bounds__(256) front_end_kernel(FrontArgs A, const T *__
 // FP32: the same steps in float, tiled. A CTA covers kFX x kFY points of one
 // RTS level. The stagger is the same for every point, so the 8 MHD cells of
 // a point are (i, j, z0) + (fx, fy, 0) + {0, 1}^3 with fixed weights (wx, wy)
-// and the level's clamped (z0, wz): the CTA takes ln T and ln rho once per
-// MHD cell of its (kFX + 1) x (kFY + 1) x 2 footprint into shared memory
+// and the level's clamped (z0, wz): the CTA takes log2 T and log2 rho once
+// per MHD cell of its (kFX + 1) x (kFY + 1) x 2 footprint into shared memory
 // (4.3 logarithms per point instead of 16) and interpolates from there.
+// Base-2 logarithms: interpolating log2 x is interpolating ln x scaled by
+// 1 / ln 2, the table position takes the scale into its step, and
+// chi_b = 2^(ln kappa_b / ln 2 + log2 rho), S_b = 2^(ln B_b / ln 2).
 constexpr int kFX = 96, kFY = 16, kFThreads = 2 * kFX;
+constexpr float kLog2e = 1.44269504088896340736f;  // 1 / ln 2
 
 struct FrontArgsF {
     int nx, ny, nz, nb, nT, nR;
     int fx, fy, fz;                  // floor of the shift
     float wx, wy, wz;                // shift - floor(shift)
-    float lnT0, idlnT, lnR0, idlnR;  // table origin and 1 / step
+    float pT, oT, pR, oR;            // table position = log2(x) p - o (ln 2 / step, origin / step)
 };
 
 // node_weight in float; x > 0 makes the truncation a floor
@@ -148,8 +153,8 @@ __global__ void __launch_bounds__(kFThreads) front_end_f32_kernel(FrontArgsF A, 
 #pragma unroll
         for (int rr = h; rr <= kFY; rr += kFThreads / kFX) {
             const long long q = (long long)gy * A.nx + gx;
-            sT[zz][rr][c] = logf(__ldg(tz + q));
-            sR[zz][rr][c] = logf(__ldg(rz + q));
+            sT[zz][rr][c] = log2f(__ldg(tz + q));
+            sR[zz][rr][c] = log2f(__ldg(rz + q));
             gy += kFThreads / kFX;
             if (gy >= A.ny) gy -= A.ny;
             if (gy >= A.ny) gy -= A.ny;
@@ -158,8 +163,8 @@ __global__ void __launch_bounds__(kFThreads) front_end_f32_kernel(FrontArgsF A, 
     if (threadIdx.x < 2 * (kFY + 1)) {
         const int zz = threadIdx.x / (kFY + 1), rr = threadIdx.x - zz * (kFY + 1);
         const long long q = (long long)(zz ? z1 : z0) * nxy + (long long)((yb + rr) % A.ny) * A.nx + (xb + kFX) % A.nx;
-        sT[zz][rr][kFX] = logf(__ldg(Tm + q));
-        sR[zz][rr][kFX] = logf(__ldg(rho + q));
+        sT[zz][rr][kFX] = log2f(__ldg(Tm + q));
+        sR[zz][rr][kFX] = log2f(__ldg(rho + q));
     }
     __syncthreads();
     const int i = i0 + c;
@@ -177,21 +182,23 @@ __global__ void __launch_bounds__(kFThreads) front_end_f32_kernel(FrontArgsF A, 
             lt = fmaf(w, fmaf(wy1, t1, wy0 * t0), lt);
             lr = fmaf(w, fmaf(wy1, r1, wy0 * r0), lr);
         }
-        const float rh = expf(lr);
         int it, ir;
         float at, ar;
-        node_weight_f((lt - A.lnT0) * A.idlnT, A.nT, it, at);
-        node_weight_f((lr - A.lnR0) * A.idlnR, A.nR, ir, ar);
-        const int it1 = A.nT > 1 ? it + 1 : it, ir1 = A.nR > 1 ? ir + 1 : ir;
-        const long long p = (long long)k * nxy + (long long)(j0 + r) * A.nx + i;
+        node_weight_f(fmaf(lt, A.pT, -A.oT), A.nT, it, at);
+        node_weight_f(fmaf(lr, A.pR, -A.oR), A.nR, ir, ar);
+        const int dt = A.nT > 1 ? 1 : 0, dr = A.nR > 1 ? A.nT : 0;
+        const float *kb = lnk + ir * A.nT + it, *bb = lnB + it;
+        float *cp = chi + (long long)k * nxy + (long long)(j0 + r) * A.nx + i, *sp = S + (cp - chi);
         for (int b = 0; b < A.nb; ++b) {
-            const float *kb = lnk + (long long)b * A.nR * A.nT;
-            const float lk = (1.f - ar) * ((1.f - at) * __ldg(kb + ir * A.nT + it) + at * __ldg(kb + ir * A.nT + it1)) +
-                             ar * ((1.f - at) * __ldg(kb + ir1 * A.nT + it) + at * __ldg(kb + ir1 * A.nT + it1));
-            const float *bb = lnB + (long long)b * A.nT;
-            const float lb = (1.f - at) * __ldg(bb + it) + at * __ldg(bb + it1);
-            chi[(long long)b * N + p] = expf(lk) * rh;
-            S[(long long)b * N + p] = expf(lb);
+            const float lk = (1.f - ar) * ((1.f - at) * __ldg(kb) + at * __ldg(kb + dt)) +
+                             ar * ((1.f - at) * __ldg(kb + dr) + at * __ldg(kb + dr + dt));
+            const float lb = (1.f - at) * __ldg(bb) + at * __ldg(bb + dt);
+            *cp = exp2f(fmaf(lk, kLog2e, lr));  // kappa rho = 2^(log2 kappa + log2 rho)
+            *sp = exp2f(lb * kLog2e);
+            kb += A.nR * A.nT;
+            bb += A.nT;
+            cp += N;
+            sp += N;
         }
     }
 }
@@ -231,8 +238,8 @@ extern "C" rts_status rts_front_end(const rts_grid *g, const rts_front_table *ta
         const double *sh = tab->shift;
         F.fx = (int)floor(sh[0]); F.fy = (int)floor(sh[1]); F.fz = (int)floor(sh[2]);
         F.wx = (float)(sh[0] - floor(sh[0])); F.wy = (float)(sh[1] - floor(sh[1])); F.wz = (float)(sh[2] - floor(sh[2]));
-        F.lnT0 = (float)tab->lnT0; F.idlnT = (float)(1.0 / tab->dlnT);
-        F.lnR0 = (float)tab->lnR0; F.idlnR = (float)(1.0 / tab->dlnR);
+        F.pT = (float)(M_LN2 / tab->dlnT); F.oT = (float)(tab->lnT0 / tab->dlnT);
+        F.pR = (float)(M_LN2 / tab->dlnR); F.oR = (float)(tab->lnR0 / tab->dlnR);
         const long long tiles = (long long)((g->nx + kFX - 1) / kFX) * ((g->ny + kFY - 1) / kFY) * g->nz;
         if (tiles > 0x7fffffffLL) return msg("grid too large for the FP32 input step"), RTS_EINVAL;
         front_end_f32_kernel<<<(unsigned)tiles, kFThreads, 0, st>>>(F, (const float *)T_mhd, (const float *)rho_mhd,
