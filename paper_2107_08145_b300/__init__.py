@@ -169,6 +169,34 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _need(name, t, shape, dtype, device, contiguous=False):
+    """t unchanged if it is a CUDA tensor of this shape and dtype on this
+    device (and contiguous: arrays the library writes through their
+    pointer); else ValueError. The library trusts its pointers' extents, so
+    a short or misplaced array would be read or written out of bounds."""
+    ok = (getattr(t, "is_cuda", False) and t.dtype == dtype and tuple(t.shape) == tuple(shape)
+          and t.device == device and (not contiguous or t.is_contiguous()))
+    if not ok:
+        got = f"{getattr(t, 'dtype', type(t).__name__)} {tuple(getattr(t, 'shape', ()))} on {getattr(t, 'device', 'host')}"
+        raise ValueError(f"{name} must be a {'contiguous ' if contiguous else ''}CUDA {dtype} tensor "
+                         f"{tuple(shape)} on {device}, got {got}")
+    return t
+
+
+def _need_host(name, a, shape, dtype, writable=False):
+    """The host-array form of _need: a C-contiguous numpy array of this shape
+    and dtype (writable for outputs)."""
+    import numpy as np
+
+    ok = (isinstance(a, np.ndarray) and a.dtype == dtype and a.shape == tuple(shape) and a.flags.c_contiguous
+          and (not writable or a.flags.writeable))
+    if not ok:
+        got = f"{getattr(a, 'dtype', type(a).__name__)} {tuple(getattr(a, 'shape', ()))}"
+        raise ValueError(f"{name} must be a C-contiguous{' writable' if writable else ''} {np.dtype(dtype)} array "
+                         f"{tuple(shape)}, got {got}")
+    return a
+
+
 class Solver:
     """One grid + band count; owns the device scratch of the CUDA library.
 
@@ -184,7 +212,9 @@ class Solver:
 
         L = load()
         self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())  # the device rts_create works on
         self.nx, self.ny, self.nz, self.nbands = nx, ny, nz, nbands
+        self.ndir = 24 if n is None else len(w)
         self.precision = precision
         self.prec = _PREC[precision]
         self.dtype = torch.float64 if self.prec == FP64 else torch.float32
@@ -245,12 +275,35 @@ class Solver:
             if isinstance(v, str):
                 setattr(b, side, _BC[v])
             else:
-                t = v.contiguous()
-                assert t.dtype == self.dtype and t.is_cuda
+                nr = self.n_up if side == "bottom" else self.ndir - self.n_up
+                t = _need(side, v, (self.nbands, nr, self.ny, self.nx), self.dtype, self.device).contiguous()
                 keep.append(t)
                 setattr(b, side, BC_EXPLICIT)
                 setattr(b, side + "_I", t.data_ptr())
         return b, keep
+
+    def _inputs(self, *named):
+        """(name, tensor) pairs of [B, nz, ny, nx] inputs -> contiguous tensors."""
+        shape = (self.nbands, self.nz, self.ny, self.nx)
+        return [_need(n, t, shape, self.dtype, self.device).contiguous() for n, t in named]
+
+    def _out_shapes(self):
+        f64 = self.torch.float64
+        return dict(I_top=((self.nbands, self.n_up, self.ny, self.nx), self.dtype), J=((self.nz, self.ny, self.nx), f64),
+                    F=((3, self.nz, self.ny, self.nx), f64), Q=((self.nz, self.ny, self.nx), f64))
+
+    def _outputs(self, out):
+        """The caller's output dict checked (absent or None entries are not
+        written), or a new one."""
+        shapes = self._out_shapes()
+        if out is None:
+            return {k: self.torch.empty(shp, dtype=dt, device=self.device) for k, (shp, dt) in shapes.items()}
+        for k, v in out.items():
+            if k not in shapes:
+                raise ValueError(f"unknown output {k!r}; expected some of {sorted(shapes)}")
+            if v is not None:
+                _need(f"out[{k!r}]", v, shapes[k][0], shapes[k][1], self.device, contiguous=True)
+        return out
 
     def wrap_seed_elems(self):
         """Floats of the warm-start buffer (rts_wrap_seed_elems)."""
@@ -265,21 +318,12 @@ class Solver:
         as the warm start (rts_boundary.wrap_seed).
         Returns dict(I_top [B,n_up,ny,nx], J [nz,ny,nx], F [3,nz,ny,nx], Q [nz,ny,nx])."""
         torch = self.torch
-        shape = (self.nbands, self.nz, self.ny, self.nx)
-        assert tuple(chi.shape) == shape and tuple(S.shape) == shape, (chi.shape, shape)
-        assert chi.dtype == self.dtype and S.dtype == self.dtype and chi.is_cuda and S.is_cuda
-        chi = chi.contiguous()
-        S = S.contiguous()
-        if out is None:
-            dev = chi.device
-            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=self.dtype, device=dev),
-                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        chi, S = self._inputs(("chi", chi), ("S", S))
+        out = self._outputs(out)
         b, keep = self._bc(bottom, top)
         if wrap_seed is not None:
             if (not wrap_seed.is_cuda or wrap_seed.dtype != torch.float32 or not wrap_seed.is_contiguous()
-                    or wrap_seed.numel() != self.wrap_seed_elems()):
+                    or wrap_seed.numel() != self.wrap_seed_elems() or wrap_seed.device != self.device):
                 raise ValueError(f"wrap_seed must be a contiguous CUDA float32 tensor of {self.wrap_seed_elems()}")
             b.wrap_seed = wrap_seed.data_ptr()
             b.seed_in = 1 if seed_in else 0
@@ -297,23 +341,14 @@ class Solver:
         (iterated on the GPU from S, default B). chi, B, eps: CUDA tensors
         [B, nz, ny, nx] in the solver dtype. Returns (S, outputs, iterations).
         Needs Solver(..., scatter=True)."""
-        torch = self.torch
-        shape = (self.nbands, self.nz, self.ny, self.nx)
-        for name, t in (("chi", chi), ("B", B), ("eps", eps)):
-            if tuple(t.shape) != shape or t.dtype != self.dtype or not t.is_cuda:
-                raise ValueError(f"{name} must be a CUDA {self.dtype} tensor {shape}")
-        S = (B.clone() if S is None else S.clone()).contiguous()
+        chi, B, eps = self._inputs(("chi", chi), ("B", B), ("eps", eps))
+        S = (B.clone() if S is None else self._inputs(("S", S))[0].clone()).contiguous()
         if tol is None:
             tol = 1e-12 if self.prec == FP64 else 2e-6
-        if out is None:
-            dev = chi.device
-            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=self.dtype, device=dev),
-                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        out = self._outputs(out)
         b, keep = self._bc(bottom, top)
         it = C.c_int(0)
-        rc = self._L.rts_scatter_solve(self._h, _ptr(chi.contiguous()), _ptr(B.contiguous()), _ptr(eps.contiguous()),
+        rc = self._L.rts_scatter_solve(self._h, _ptr(chi), _ptr(B), _ptr(eps),
                                        _ptr(S), C.byref(b), max_iter, tol, C.byref(it), _ptr(out.get("I_top")),
                                        _ptr(out.get("J")), _ptr(out.get("F")), _ptr(out.get("Q")))
         self._err(rc)
@@ -328,25 +363,19 @@ class Solver:
         the solver dtype, gJ/gF/gQ float64. Returns (g_logchi, g_S), each
         [B, nz, ny, nx] in the solver dtype. Needs Solver(..., adjoint=True)."""
         torch = self.torch
-        shape = (self.nbands, self.nz, self.ny, self.nx)
-        assert tuple(chi.shape) == shape and tuple(S.shape) == shape, (chi.shape, shape)
-        assert chi.dtype == self.dtype and S.dtype == self.dtype and chi.is_cuda and S.is_cuda
-        chi = chi.contiguous()
-        S = S.contiguous()
-
-        def cot(t, shp, dt):
-            if t is None:
-                return None
-            assert tuple(t.shape) == shp, (t.shape, shp)
-            assert t.dtype == dt and t.is_cuda
-            return t.contiguous()
-
-        gI_top = cot(gI_top, (self.nbands, self.n_up, self.ny, self.nx), self.dtype)
-        gJ = cot(gJ, (self.nz, self.ny, self.nx), torch.float64)
-        gF = cot(gF, (3, self.nz, self.ny, self.nx), torch.float64)
-        gQ = cot(gQ, (self.nz, self.ny, self.nx), torch.float64)
+        chi, S = self._inputs(("chi", chi), ("S", S))
+        shp = self._out_shapes()
+        gI_top, gJ, gF, gQ = (None if t is None else _need(n, t, *shp[k], self.device).contiguous()
+                              for n, k, t in (("gI_top", "I_top", gI_top), ("gJ", "J", gJ), ("gF", "F", gF),
+                                              ("gQ", "Q", gQ)))
         if out is None:
             out = (torch.empty_like(chi), torch.empty_like(S))
+        else:
+            if len(out) != 2:
+                raise ValueError("out must be a pair (g_logchi, g_S)")
+            shape = (self.nbands, self.nz, self.ny, self.nx)
+            for n, t in zip(("out[0]", "out[1]"), out):
+                _need(n, t, shape, self.dtype, self.device, contiguous=True)
         b, keep = self._bc(bottom, top)
         rc = self._L.rts_adjoint(self._h, _ptr(chi), _ptr(S), C.byref(b), _ptr(gI_top), _ptr(gJ), _ptr(gF),
                                  _ptr(gQ), _ptr(out[0]), _ptr(out[1]))
@@ -360,27 +389,20 @@ class Solver:
         """Capture one solve with these tensors in a CUDA graph (rts_graph_create).
         The solver's stream must not be the legacy default stream. Returns
         (Graph, out); Graph.launch() replays it."""
-        torch = self.torch
-        if out is None:
-            dev = chi.device
-            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=self.dtype, device=dev),
-                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        chi, S = self._inputs(("chi", chi), ("S", S))
+        out = self._outputs(out)
         b, keep = self._bc(bottom, top)
-        return Graph(self, self._L.rts_graph_create, (chi.contiguous(), S.contiguous()), b, out, keep), out
+        return Graph(self, self._L.rts_graph_create, (chi, S), b, out, keep), out
 
     def solve_host(self, chi, S, bottom="equal_s", top="zero", out=None):
         """Host (numpy) inputs and outputs; the library copies both ways."""
         import numpy as np
 
         npdt = np.float64 if self.prec == FP64 else np.float32
-        chi = np.ascontiguousarray(chi, dtype=npdt)
-        S = np.ascontiguousarray(S, dtype=npdt)
-        if out is None:
-            out = dict(I_top=np.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=npdt),
-                       J=np.empty((self.nz, self.ny, self.nx)), F=np.empty((3, self.nz, self.ny, self.nx)),
-                       Q=np.empty((self.nz, self.ny, self.nx)))
+        shape = (self.nbands, self.nz, self.ny, self.nx)
+        chi = _need_host("chi", np.ascontiguousarray(chi, dtype=npdt), shape, npdt)
+        S = _need_host("S", np.ascontiguousarray(S, dtype=npdt), shape, npdt)
+        out = self._host_outputs(out)
         b = Boundary(_BC[bottom], _BC[top], None, None)
         p = lambda a: None if a is None else C.c_void_p(a.ctypes.data)  # noqa: E731
         rc = self._L.rts_solve_host(self._h, p(chi), p(S), C.byref(b), p(out.get("I_top")), p(out.get("J")),
@@ -392,11 +414,35 @@ class Solver:
         """Enqueue a solve on host (numpy, preferably pinned) buffers and return
         at once (rts_solve_host_async); `out` as returned by solve_host. Call
         host_wait() before reading the outputs."""
+        import numpy as np
+
+        npdt = np.float64 if self.prec == FP64 else np.float32
+        shape = (self.nbands, self.nz, self.ny, self.nx)
+        _need_host("chi", chi, shape, npdt)
+        _need_host("S", S, shape, npdt)
+        if out is None:
+            raise ValueError("solve_host_async needs the output arrays (out)")
+        out = self._host_outputs(out)
         p = lambda a: None if a is None else C.c_void_p(a.ctypes.data)  # noqa: E731
         b = Boundary(_BC[bottom], _BC[top], None, None)
         rc = self._L.rts_solve_host_async(self._h, p(chi), p(S), C.byref(b), p(out.get("I_top")), p(out.get("J")),
                                           p(out.get("F")), p(out.get("Q")))
         self._err(rc)
+        return out
+
+    def _host_outputs(self, out):
+        """The host form of _outputs: numpy arrays (float64 for J, F, Q)."""
+        import numpy as np
+
+        shapes = {k: (shp, np.float64 if dt == self.torch.float64 else np.float32)
+                  for k, (shp, dt) in self._out_shapes().items()}
+        if out is None:
+            return {k: np.empty(shp, dtype=dt) for k, (shp, dt) in shapes.items()}
+        for k, v in out.items():
+            if k not in shapes:
+                raise ValueError(f"unknown output {k!r}; expected some of {sorted(shapes)}")
+            if v is not None:
+                _need_host(f"out[{k!r}]", v, shapes[k][0], shapes[k][1], writable=True)
         return out
 
     def host_wait(self):
@@ -460,6 +506,7 @@ class BatchedSolver(Solver):
 
         L = load()
         self.torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self.shapes = [tuple(int(v) for v in s) for s in shapes]
         self.nbands = nbands
         self.precision = precision
@@ -520,14 +567,35 @@ class BatchedSolver(Solver):
                     F=torch.empty(3 * self.totals[2], dtype=torch.float64, device=device),
                     Q=torch.empty(self.totals[2], dtype=torch.float64, device=device))
 
+    def _bc(self, bottom, top):
+        if not (isinstance(bottom, str) and isinstance(top, str)):
+            raise ValueError("batched solves take the boundary kinds 'zero' and 'equal_s' only")
+        return super()._bc(bottom, top)
+
+    def _packed_inputs(self, chi, S):
+        n = self.totals[0]
+        return [_need(nm, t.reshape(-1) if getattr(t, "numel", lambda: -1)() == n else t, (n,), self.dtype,
+                      self.device).contiguous() for nm, t in (("chi", chi), ("S", S))]
+
+    def _packed_outputs(self, out):
+        if out is None:
+            return self.empty_outputs(self.device)
+        f64 = self.torch.float64
+        shapes = dict(I_top=(self.totals[1], self.dtype), J=(self.totals[2], f64), F=(3 * self.totals[2], f64),
+                      Q=(self.totals[2], f64))
+        for k, v in out.items():
+            if k not in shapes:
+                raise ValueError(f"unknown output {k!r}; expected some of {sorted(shapes)}")
+            if v is not None:
+                _need(f"out[{k!r}]", v, (shapes[k][0],), shapes[k][1], self.device, contiguous=True)
+        return out
+
     def solve(self, chi, S, bottom="equal_s", top="zero", check=True, out=None):
         """chi, S: packed CUDA tensors of totals[0] elements. Returns packed outputs."""
-        assert chi.numel() == self.totals[0] and S.numel() == self.totals[0], (chi.numel(), self.totals)
-        assert chi.dtype == self.dtype and S.dtype == self.dtype and chi.is_cuda and S.is_cuda
-        if out is None:
-            out = self.empty_outputs(chi.device)
+        chi, S = self._packed_inputs(chi, S)
+        out = self._packed_outputs(out)
         b, keep = self._bc(bottom, top)
-        rc = self._L.rts_solve_batched(self._h, _ptr(chi.contiguous()), _ptr(S.contiguous()), C.byref(b),
+        rc = self._L.rts_solve_batched(self._h, _ptr(chi), _ptr(S), C.byref(b),
                                        _ptr(out.get("I_top")), _ptr(out.get("J")), _ptr(out.get("F")),
                                        _ptr(out.get("Q")))
         self._err(rc)
@@ -537,10 +605,10 @@ class BatchedSolver(Solver):
         return out
 
     def graph(self, chi, S, bottom="equal_s", top="zero", out=None):
-        if out is None:
-            out = self.empty_outputs(chi.device)
+        chi, S = self._packed_inputs(chi, S)
+        out = self._packed_outputs(out)
         b, keep = self._bc(bottom, top)
-        return Graph(self, self._L.rts_graph_create, (chi.contiguous(), S.contiguous()), b, out, keep), out
+        return Graph(self, self._L.rts_graph_create, (chi, S), b, out, keep), out
 
 
 def autotune(shapes, nbands, chi, S, precision="fp32", spacing=None, repeats=3, stream=None, **opts):
@@ -635,6 +703,8 @@ def front_end(T, rho, table, precision="fp32", shift=(-0.5, -0.5, -0.5), out=Non
             raise ValueError(f"{name} must be a CUDA tensor of {dt}")
     nz, ny, nx = T.shape
     dev = T.device
+    if rho.device != dev:
+        raise ValueError(f"T and rho must be on the same device, got {T.device} and {rho.device}")
     lnk = torch.as_tensor(table["ln_kappa"], dtype=dt, device=dev).contiguous()
     lnB = torch.as_tensor(table["ln_B"], dtype=dt, device=dev).contiguous()
     nb, nR, nT = lnk.shape
@@ -644,6 +714,11 @@ def front_end(T, rho, table, precision="fp32", shift=(-0.5, -0.5, -0.5), out=Non
                      lnB.data_ptr(), (C.c_double * 3)(*shift))
     if out is None:
         out = (torch.empty((nb, nz, ny, nx), dtype=dt, device=dev), torch.empty((nb, nz, ny, nx), dtype=dt, device=dev))
+    elif len(out) != 2:
+        raise ValueError("out must be a pair (chi, S)")
+    else:
+        for n, t in zip(("out[0]", "out[1]"), out):
+            _need(n, t, (nb, nz, ny, nx), dt, dev, contiguous=True)
     if stream is None:
         stream = torch.cuda.current_stream(dev)
     err = C.create_string_buffer(256)
@@ -670,6 +745,7 @@ class DecomposedSolver:
         self.torch = torch
         self._L = L
         self._h = C.c_void_p()
+        self.device = torch.device("cuda", torch.cuda.current_device())
         self.nx, self.ny, self.nz, self.nbands, self.nblocks = nx, ny, nz, nbands, nblocks
         self.prec = _PREC[precision]
         self.dtype = torch.float32
@@ -705,19 +781,8 @@ class DecomposedSolver:
     def solve(self, chi, S, tol=1e-6, max_iter=32, out=None):
         """chi, S: float32 CUDA tensors [B, nz, ny, nx]. Returns (outputs,
         iterations), outputs as Solver.solve."""
-        torch = self.torch
-        shape = (self.nbands, self.nz, self.ny, self.nx)
-        for name, t in (("chi", chi), ("S", S)):
-            if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_cuda:
-                raise ValueError(f"{name} must be a CUDA float32 tensor {shape}")
-        chi = chi.contiguous()
-        S = S.contiguous()
-        if out is None:
-            dev = chi.device
-            out = dict(I_top=torch.empty((self.nbands, self.n_up, self.ny, self.nx), dtype=torch.float32, device=dev),
-                       J=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       F=torch.empty((3, self.nz, self.ny, self.nx), dtype=torch.float64, device=dev),
-                       Q=torch.empty((self.nz, self.ny, self.nx), dtype=torch.float64, device=dev))
+        chi, S = self._inputs(("chi", chi), ("S", S))
+        out = self._outputs(out)
         it = C.c_int(0)
         rc = self._L.rts_solve_decomposed(self._h, _ptr(chi), _ptr(S), None, tol, max_iter, C.byref(it),
                                           _ptr(out.get("I_top")), _ptr(out.get("J")), _ptr(out.get("F")),
@@ -725,3 +790,7 @@ class DecomposedSolver:
         if rc != RTS_OK:
             raise RTSError(rc, self._L.rts_decomposed_last_error(self._h).decode())
         return out, it.value
+
+    _inputs = Solver._inputs
+    _out_shapes = Solver._out_shapes
+    _outputs = Solver._outputs
