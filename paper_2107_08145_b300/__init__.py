@@ -568,9 +568,19 @@ class BatchedSolver(Solver):
                     Q=torch.empty(self.totals[2], dtype=torch.float64, device=device))
 
     def _bc(self, bottom, top):
-        if not (isinstance(bottom, str) and isinstance(top, str)):
-            raise ValueError("batched solves take the boundary kinds 'zero' and 'equal_s' only")
-        return super()._bc(bottom, top)
+        # explicit boundary arrays go to the library, which refuses them for
+        # batched handles (RTS_EINVAL) without reading them
+        b = Boundary()
+        keep = []
+        for side, v in (("bottom", bottom), ("top", top)):
+            if isinstance(v, str):
+                setattr(b, side, _BC[v])
+            else:
+                t = v.contiguous()
+                keep.append(t)
+                setattr(b, side, BC_EXPLICIT)
+                setattr(b, side + "_I", t.data_ptr())
+        return b, keep
 
     def _packed_inputs(self, chi, S):
         n = self.totals[0]
@@ -625,6 +635,12 @@ def autotune(shapes, nbands, chi, S, precision="fp32", spacing=None, repeats=3, 
     if stream is None:
         stream = torch.cuda.current_stream()
     o.stream = C.c_void_p(stream.cuda_stream)
+    # chi, S packed as for BatchedSolver: nbands x the points of every grid
+    n = nbands * sum(int(a) * int(b) * int(c) for a, b, c in shapes)
+    dt = torch.float64 if o.prec == FP64 else torch.float32
+    dev = torch.device("cuda", torch.cuda.current_device())
+    chi, S = (_need(nm, t.reshape(-1) if getattr(t, "numel", lambda: -1)() == n else t, (n,), dt, dev).contiguous()
+              for nm, t in (("chi", chi), ("S", S)))
     gr = _grids([tuple(s) for s in shapes], spacing)
     best, n = C.c_int(), C.c_int()
     rows = (C.c_int * 8)()

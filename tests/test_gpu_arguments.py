@@ -2,7 +2,8 @@
 library would read or write out of bounds or on the wrong device: inputs of
 the wrong shape, dtype or placement, caller-supplied outputs that are short,
 strided or of the wrong dtype, explicit boundaries of the wrong ray count,
-batched arrays of the wrong length. Valid arrays are still accepted after
+batched arrays of the wrong length (explicit boundaries on a batched handle
+are refused by the library itself). Valid arrays are still accepted after
 the refusals (the handle is unchanged by them)."""
 import numpy as np
 import pytest
@@ -80,12 +81,14 @@ def test_batched_arguments(rts):
     S = torch.ones(n, device="cuda")
     with pytest.raises(ValueError):
         bs.solve(chi[:-1], S)
-    with pytest.raises(ValueError):
+    with pytest.raises(rts.RTSError):  # the library refuses explicit boundaries on batched handles
         bs.solve(chi, S, bottom=torch.ones(10, device="cuda"))
     out = bs.solve(chi, S)
     with pytest.raises(ValueError):
         bs.solve(chi, S, out=dict(out, Q=out["Q"][:-1]))
     assert bs.solve(chi, S, out=out) is out
+    with pytest.raises(ValueError):
+        rts.autotune([(12, 10, 9), (16, 16, 12)], 1, chi[:-1], S, precision="fp32")
 
 
 def test_host_arguments(rts):
