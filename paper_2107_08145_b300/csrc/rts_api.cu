@@ -1153,7 +1153,8 @@ rts_status rts_create(rts_handle **out, const rts_grid *g, int nbands, const rts
         h->d_dirw = (double *)(base + o_dirw);
         h->d_dsmax = (unsigned *)(base + o_dsmax);
         // (ds_d, w_d) with the weights of directions of equal segment length
-        // summed (S4: 3 lengths for 24 directions)
+        // summed (the 24 S4 directions share their dominant cosine: one
+        // length per axis, one in all on a grid of cubic cells)
         std::vector<double> dw;
         for (int d = 0; d < h->ndir; ++d) {
             size_t e = 0;
